@@ -1,0 +1,21 @@
+"""FP64 CPU oracle for the streaming-collision LB scheme with the kinetic
+diffuse-reflection wall (Meng & Zhang, arXiv:1209.5201).
+
+TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and the CPU-baseline
+leg of bench.py may import, call, link or run anything in this package.  The
+CUDA library never does, and this package never imports the library: the two
+share no kernels, headers, helpers or table generators.  The oracle follows
+the paper's push / ghost-layer description step by step in plain C (FP64,
+no FMA contraction) and derives its own lattice tables in numpy.
+
+Parity status per function (what pins it, see tests/test_oracle_pins.py):
+  lattice.*                 pinned: Gaussian moment isotropy, closed forms
+  orc_equilibrium           pinned: Maxwellian moments through the kept order
+  orc_collide               pinned: exact conservation of rho, rho u (, energy)
+  orc_run (stream + wall)   pinned: rest / uniform-flow fixed points, per-step
+                            zero net wall mass flux, slot bookkeeping,
+                            positivity, Couette antisymmetry, NS slip limit
+                            (Eq. (13)), NS temperature profile (Eq. (14), read
+                            with U_w^2), second-order grid convergence
+  orc_run_to_residual       pinned through the steady Couette profiles above
+"""

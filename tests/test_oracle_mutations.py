@@ -1,0 +1,82 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case copies oracle/lbm_oracle.c to a temporary directory, plants one
+mistake by a textual substitution, compiles the copy, and runs one pin from
+test_oracle_pins.py against it: the pin must fail.  The committed oracle is
+never modified.
+"""
+import importlib.util
+import subprocess
+
+import pytest
+
+import test_oracle_pins as pins
+
+MUTATIONS = {
+    # dropped (T-1)^2/8 term of Eq. (4)
+    "drop_theta2_term": (
+        "g += th * th / 8.0 * (c2 * c2 - 2.0 * (D + 2.0) * c2 + D * (D + 2.0));", "",
+        lambda o: pins.test_equilibrium_maxwellian_moments(o, "D2Q37", 4, True)),
+    # wrong sign inside the third-order bracket of Eq. (4)
+    "sign_third_order": (
+        "(cu * cu - 3.0 * u2 + 3.0 * th", "(cu * cu + 3.0 * u2 + 3.0 * th",
+        lambda o: pins.test_equilibrium_maxwellian_moments(o, "D2Q37", 3, True)),
+    # normaliser of Eq. (11)-(12) counting each outgoing velocity once
+    "normaliser_once_per_velocity": (
+        "if (nsgn * L->ey[a] > l) den += gw[a];", "if (nsgn * L->ey[a] > 0 && l == 0) den += gw[a];",
+        lambda o: pins.test_wall_zero_net_mass_flux_and_bookkeeping(o, "D2Q37")),
+    # incoming criterion of Sec. III off by one layer
+    "incoming_off_by_one": (
+        "if (nsgn * L->ey[a] < -l)", "if (nsgn * L->ey[a] < -l - 1)",
+        lambda o: pins.test_wall_zero_net_mass_flux_and_bookkeeping(o, "D2Q25")),
+    # ghost row of the top wall mirrored the wrong way
+    "top_ghost_row": (
+        "int grow = wall == 0 ? -1 - l : Ny + l;\n                for (int a = 0; a < Q; ++a)\n"
+        "                    if (nsgn",
+        "int grow = wall == 0 ? -1 - l : Ny + N - 1 - l;\n                for (int a = 0; a < Q; ++a)\n"
+        "                    if (nsgn",
+        lambda o: pins.test_wall_zero_net_mass_flux_and_bookkeeping(o, "D2Q17")),
+    # relaxation factor of Eq. (5) without the dt/2 shift
+    "omega_without_half_dt": (
+        "return dt / (tau + 0.5 * dt);", "return dt / tau;",
+        lambda o: pins.test_ns_slip_limit(o, "D2Q25")),
+    # x-momentum moment with the wrong velocity component
+    "moment_transposed": (
+        "sx += L->r * L->ex[a] * v;", "sx += L->r * L->ey[a] * v;",
+        lambda o: pins.test_moments_recover_fields(o)),
+    # temperature moment without the peculiar velocity
+    "temperature_not_peculiar": (
+        "double Cx = L->r * L->ex[a] - u, Cy = L->r * L->ey[a] - v;",
+        "double Cx = L->r * L->ex[a], Cy = L->r * L->ey[a];",
+        lambda o: pins.test_moments_recover_fields(o)),
+    # wall distribution evaluated at the wrong wall's velocity
+    "wall_velocity_swapped": (
+        "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[wall], 0.0, Tw, gw);",
+        "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[1 - wall], 0.0, Tw, gw);",
+        lambda o: pins.test_couette_antisymmetry(o)),
+}
+
+
+def _mutant(tmp_path, old, new):
+    from oracle import oracle as base
+    src = open(base._SRC).read()
+    assert old in src, "mutation anchor not found in the oracle source"
+    path = tmp_path / "lbm_oracle_mut.c"
+    path.write_text(src.replace(old, new, 1))
+    so = str(tmp_path / "liblbm_oracle_mut.so")
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                           "-shared", "-o", so, str(path), "-lm"])
+    spec = importlib.util.find_spec("oracle.oracle")
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build = lambda force=False: so
+    mod._lib = None
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new, pin = MUTATIONS[name]
+    mod = _mutant(tmp_path, old, new)
+    with pytest.raises((AssertionError, RuntimeError)):
+        pin(mod)

@@ -1,0 +1,334 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: Gaussian
+moments, closed-form quadrature solutions, Maxwellian moments, conservation
+laws, fixed points, exact symmetries, and the Navier-Stokes slip / jump
+solutions the paper compares with (Eq. (13)-(14)).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import lattice as olat
+
+LATS = ["D2Q17", "D2Q25", "D2Q25b", "D2Q37"]
+DEGREE = {"D2Q17": 7, "D2Q25": 7, "D2Q25b": 7, "D2Q37": 9}
+
+
+def _dfact(n):
+    return 1 if n <= 0 else n * _dfact(n - 2)
+
+
+def gauss_moment(px, py):
+    """Moment E[c_x^px c_y^py] of the unit 2-D Gaussian."""
+    if px % 2 or py % 2:
+        return 0.0
+    return float(_dfact(px - 1) * _dfact(py - 1))
+
+
+def maxwell_moment(px, py, ux, uy, T):
+    """E[c_x^px c_y^py] of the Maxwellian with mean (ux, uy) and temperature T."""
+    def m1(p, u):
+        return sum(math.comb(p, k) * u ** (p - k) * T ** (k / 2) * _dfact(k - 1)
+                   for k in range(0, p + 1, 2))
+    return m1(px, ux) * m1(py, uy)
+
+
+# --------------------------------------------------------------------------
+# Lattices: the velocity set xi of Sec. II must integrate the Gaussian exactly
+# through the degree that Eq. (4) needs.
+
+@pytest.mark.parametrize("name", LATS)
+def test_lattice_isotropy(name):
+    L = olat.get(name)
+    c = L.r * L.e.astype(np.float64)
+    assert np.all(L.w > 0)
+    deg = DEGREE[name]
+    for n in range(deg + 1):
+        for px in range(n + 1):
+            py = n - px
+            m = float(np.sum(L.w * c[:, 0] ** px * c[:, 1] ** py))
+            assert abs(m - gauss_moment(px, py)) <= 2e-13 * max(1.0, gauss_moment(px, py)), \
+                (name, px, py, m)
+    # and it is not exact one even degree further (the set is no better than claimed)
+    worst = max(abs(float(np.sum(L.w * c[:, 0] ** px * c[:, 1] ** (deg + 1 - px)))
+                    - gauss_moment(px, deg + 1 - px)) for px in range(deg + 2))
+    assert worst > 1e-3
+
+
+def test_d2q17_closed_form():
+    # Shan, Yuan & Chen (2006) D2Q17: the degree-7 system has the algebraic solution
+    # r^2 = (125 + 5 sqrt 193)/72 with these shell weights (positive root).
+    L = olat.get("D2Q17")
+    s = math.sqrt(193.0)
+    assert abs(L.r ** 2 - (125 + 5 * s) / 72) < 1e-13
+    expect = {(0, 0): (575 + 193 * s) / 8100, (1, 0): (3355 - 91 * s) / 18000,
+              (1, 1): (655 + 17 * s) / 27000, (2, 2): (685 - 49 * s) / 54000,
+              (3, 0): (1445 - 101 * s) / 162000}
+    for (ex, ey), w in zip(L.e.tolist(), L.w):
+        key = tuple(sorted((abs(ex), abs(ey)), reverse=True))
+        assert abs(w - expect[key]) < 1e-15, (ex, ey)
+
+
+def test_d2q25_is_d1q5_tensor_product():
+    # D1Q5 {0,+-1,+-3}: 3 s^2 - 10 s + 5 = 0 for s = r^2; both roots are valid
+    for name, s in (("D2Q25", (5 + math.sqrt(10)) / 3), ("D2Q25b", (5 - math.sqrt(10)) / 3)):
+        L = olat.get(name)
+        assert abs(L.r ** 2 - s) < 1e-14
+        assert abs(3 * s * s - 10 * s + 5) < 1e-13
+        # 1-D marginal moments m0..m8 of the x-axis
+        c = L.r * L.e[:, 0]
+        for k, ref in ((0, 1), (2, 1), (4, 3), (6, 15)):
+            assert abs(np.sum(L.w * c ** k) - ref) < 1e-12 * ref
+
+
+def test_d2q37_matches_published_table():
+    # Degree-9 D2V37 table of the paper's cited lattice solution (Shan 2010,
+    # Phys. Rev. E 81, 036702), stored under tests/golden with its citation.
+    rows = {}
+    with open(__file__.replace("test_oracle_pins.py", "golden/d2q37_shan2010.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()
+            rows[k] = float(v)
+    L = olat.get("D2Q37")
+    assert abs(L.r - rows["r"]) < 1e-13
+    for (ex, ey), w in zip(L.e.tolist(), L.w):
+        a, b = sorted((abs(ex), abs(ey)), reverse=True)
+        assert abs(w - rows[f"w{a}{b}"]) < 1e-13 * max(w, 1e-3), (ex, ey)
+
+
+# --------------------------------------------------------------------------
+# Equilibrium, Eq. (4): the truncated Maxwellian reproduces the Maxwellian's
+# moments through the kept Hermite order.
+
+@pytest.mark.parametrize("name,order,thermal", [
+    ("D2Q37", 4, True), ("D2Q37", 3, True), ("D2Q37", 2, False),
+    ("D2Q17", 2, False), ("D2Q25", 2, False), ("D2Q25b", 2, False)])
+def test_equilibrium_maxwellian_moments(oracle, name, order, thermal):
+    p = oracle.Problem(lattice=name, eq_order=order, thermal=thermal)
+    c = p.lat.r * p.lat.e.astype(np.float64)
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        rho = 0.7 + 0.6 * rng.random()
+        ux, uy = 0.4 * rng.random(2) - 0.2
+        T = (0.85 + 0.3 * rng.random()) if thermal else 1.0
+        f = oracle.equilibrium(p, rho, ux, uy, T)
+        for n in range(order + 1):
+            for px in range(n + 1):
+                py = n - px
+                m = float(np.sum(f * c[:, 0] ** px * c[:, 1] ** py))
+                ref = rho * maxwell_moment(px, py, ux, uy, T)
+                assert abs(m - ref) <= 1e-13 * max(1.0, abs(ref)), (n, px, py, m, ref)
+        # one order further the truncation shows (the expansion is really order `order`)
+        n = order + 1
+        err = max(abs(float(np.sum(f * c[:, 0] ** px * c[:, 1] ** (n - px)))
+                      - rho * maxwell_moment(px, n - px, ux, uy, T)) for px in range(n + 1))
+        assert err > 1e-6
+
+
+def test_moments_recover_fields(oracle):
+    p = oracle.Problem(lattice="D2Q37", eq_order=4, thermal=True)
+    f = oracle.equilibrium(p, 1.13, 0.07, -0.04, 1.05)
+    rho, ux, uy, T = oracle.moments(p, f)
+    assert abs(rho - 1.13) < 1e-14 and abs(ux - 0.07) < 1e-15
+    assert abs(uy + 0.04) < 1e-15 and abs(T - 1.05) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Collision, Eq. (5) right-hand side: conserves mass, momentum (and energy when
+# thermal) exactly; relaxes toward f^eq by the factor dt/(tau + dt/2).
+
+@pytest.mark.parametrize("name,order,thermal", [("D2Q37", 4, True), ("D2Q25", 2, False),
+                                                ("D2Q17", 2, False)])
+def test_collision_conserves(oracle, name, order, thermal):
+    p = oracle.Problem(lattice=name, Nx=5, Ny=7, eq_order=order, thermal=thermal, Kn=0.03)
+    rng = np.random.default_rng(5)
+    f = oracle.init_fields(p, 1 + 0.05 * rng.random((7, 5)), 0.1 * rng.random((7, 5)),
+                           0.1 * rng.random((7, 5)) - 0.05,
+                           1 + (0.05 * rng.random((7, 5)) if thermal else 0))
+    f *= 1 + 0.1 * rng.random(f.shape)        # leave equilibrium
+    g = oracle.collide(p, f)
+    c = p.lat.r * p.lat.e.astype(np.float64)
+    for w in (np.ones(p.Q), c[:, 0], c[:, 1]) + ((np.sum(c * c, 1),) if thermal else ()):
+        a = np.tensordot(w, f, 1)
+        b = np.tensordot(w, g, 1)
+        assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a)) + 1e-16
+    assert np.all(np.abs(g - f) > 0)
+
+
+def test_collision_relaxation_factor(oracle):
+    # constant tau: f* - f^eq = (1 - dt/(tau + dt/2)) (f - f^eq), dt = 1/(r Ny)
+    p = oracle.Problem(lattice="D2Q25", Nx=1, Ny=10, tau=0.02)
+    f = oracle.init_fields(p, np.ones((10, 1)), 0.05)
+    f[:, :, :] *= 1 + 0.01 * np.arange(p.Q)[:, None, None] / p.Q
+    g = oracle.collide(p, f)
+    rho, ux, uy, T = oracle.macros(p, f)
+    feq = oracle.equilibrium(p, rho[3, 0], ux[3, 0], uy[3, 0], 1.0)
+    dt = 1 / (p.lat.r * 10)
+    om = dt / (0.02 + dt / 2)
+    assert np.allclose(g[:, 3, 0] - feq, (1 - om) * (f[:, 3, 0] - feq), rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Stream + diffuse wall, Eq. (5) shift and Eq. (12).
+
+@pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
+def test_rest_state_is_fixed_point(oracle, name):
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    p = oracle.Problem(lattice=name, Nx=3, Ny=8, eq_order=order, thermal=thermal,
+                       Kn=0.1, u_wall=(0.0, 0.0))
+    f = oracle.init_fields(p, np.ones((8, 3)))
+    f0 = f.copy()
+    oracle.run(p, f, 200)
+    assert np.max(np.abs(f - f0)) < 1e-13 * f0.max()
+    assert np.allclose(f0[:, 0, 0], p.lat.w, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
+def test_uniform_flow_is_fixed_point(oracle, name):
+    # both walls move with the gas: the diffuse wall re-emits exactly g^eq(U, T_w)
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    U = 0.15
+    p = oracle.Problem(lattice=name, Nx=2, Ny=6, eq_order=order, thermal=thermal,
+                       Kn=0.05, u_wall=(U, U))
+    f = oracle.init_fields(p, np.ones((6, 2)), U)
+    f0 = f.copy()
+    oracle.run(p, f, 150)
+    assert np.max(np.abs(f - f0)) < 1e-13 * f0.max()
+
+
+@pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
+def test_wall_zero_net_mass_flux_and_bookkeeping(oracle, name):
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    Nx, Ny = 9, 12
+    p = oracle.Problem(lattice=name, Nx=Nx, Ny=Ny, eq_order=order, thermal=thermal, Kn=0.05,
+                       u_wall=(-0.2, 0.25), T_wall=(1.04, 0.97))
+    f = oracle.init_fields(p, inputs.rho_field(Nx, Ny, 0.05, seed=3))
+    m0 = f.sum()
+    for _ in range(5):
+        st = oracle.run(p, f, 7, stats=True)
+        assert st["holes_unfilled"] == 0 and st["slots_doubled"] == 0
+        for wall in (0, 1):
+            assert abs(st["m_in"][wall] - st["m_out"][wall]) <= 1e-14 * st["m_in"][wall]
+            assert st["m_in"][wall] > 0
+    assert abs(f.sum() - m0) <= 1e-13 * m0
+
+
+def test_wall_normaliser_is_half_range_flux(oracle):
+    # Eq. (11): the double sum over layers l < N and velocities with e.n > l counts
+    # each outgoing velocity once per layer it crosses: sum_{e.n>0} |e.n| g^w.
+    p = oracle.Problem(lattice="D2Q37", eq_order=4, thermal=True, u_wall=(-0.3, 0.2),
+                       T_wall=(1.1, 0.9))
+    for wall, sgn in ((0, 1), (1, -1)):
+        gw, den = oracle.wall_distribution(p, wall)
+        ey = p.lat.e[:, 1] * sgn
+        assert abs(den - np.sum(np.where(ey > 0, ey, 0) * gw)) < 1e-15
+        # and by the lattice's reflection symmetry it equals the incoming count of g^w
+        assert abs(den - np.sum(np.where(ey < 0, -ey, 0) * gw)) < 1e-15
+
+
+def test_global_mass_drift_long_run(oracle):
+    Nx, Ny = 4, 16
+    p = oracle.Problem(lattice="D2Q25", Nx=Nx, Ny=Ny, Kn=0.1, u_wall=(-0.1, 0.1))
+    f = oracle.init_fields(p, inputs.rho_field(Nx, Ny, 1e-3, seed=7))
+    m0 = f.sum()
+    oracle.run(p, f, 4000)
+    assert abs(f.sum() - m0) / m0 < 1e-13
+
+
+@pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
+def test_positivity(oracle, name):
+    # Sec. I: the kinetic wall keeps f >= 0 given a positive bulk and g^w >= 0
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    p = oracle.Problem(lattice=name, Nx=1, Ny=24, eq_order=order, thermal=thermal, Kn=0.5,
+                       u_wall=(-0.3, 0.3), T_wall=(1.1, 0.9))
+    f = oracle.init_fields(p, np.ones((24, 1)))
+    for _ in range(10):
+        oracle.run(p, f, 50)
+        assert f.min() > 0
+    for wall in (0, 1):
+        assert oracle.wall_distribution(p, wall)[0].min() > 0
+
+
+def test_couette_antisymmetry(oracle):
+    # D2Q25, Nx=1 x Ny=64, walls -+0.1, Kn=0.1, uniform start, FP64
+    p = oracle.Problem(lattice="D2Q25", Nx=1, Ny=64, Kn=0.1, u_wall=(-0.1, 0.1))
+    f = oracle.init_fields(p, np.ones((64, 1)))
+    oracle.run(p, f, 2000)
+    rho, ux, uy, T = oracle.macros(p, f)
+    assert np.max(np.abs(ux[:, 0] + ux[::-1, 0])) < 1e-14
+    assert np.max(np.abs(rho[:, 0] - rho[::-1, 0])) < 1e-14
+    assert np.max(np.abs(uy)) < 1e-14
+    assert ux[-1, 0] > 0 > ux[0, 0]
+
+
+@pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
+def test_ns_slip_limit(oracle, name):
+    # Eq. (13): U_NS = (2y - 1) U_w / (2 Kn + 1) in the slip regime
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    Ny, Uw = 32, 0.05
+    errs = []
+    for Kn in (0.01, 0.02):
+        p = oracle.Problem(lattice=name, Nx=1, Ny=Ny, eq_order=order, thermal=thermal, Kn=Kn,
+                           u_wall=(-Uw, Uw))
+        f = oracle.init_fields(p, np.ones((Ny, 1)))
+        ok, _, _ = oracle.run_to_residual(p, f, 1e-11, 300000, 100)
+        assert ok
+        ux = oracle.macros(p, f)[1][:, 0]
+        y = (np.arange(Ny) + 0.5) / Ny
+        errs.append(np.max(np.abs(ux - (2 * y - 1) * Uw / (2 * Kn + 1))) / Uw)
+    assert errs[1] < 0.02
+    assert errs[0] < errs[1]                   # closer to NS as Kn -> 0
+
+
+def test_ns_temperature_jump(oracle):
+    # Eq. (14) read with U_w^2 and the 2-D gas of the thermal lattice:
+    # C_p = (D+2)/2 = 2, gamma = 2, Pr = 1 (BGK), jump coefficient 4 gamma/(gamma+1).
+    Ny, Uw, Kn = 32, 0.3, 0.02
+    p = oracle.Problem(lattice="D2Q37", Nx=1, Ny=Ny, eq_order=4, thermal=True, Kn=Kn,
+                       u_wall=(-Uw, Uw))
+    f = oracle.init_fields(p, np.ones((Ny, 1)))
+    ok, _, _ = oracle.run_to_residual(p, f, 1e-11, 300000, 100)
+    assert ok
+    T = oracle.macros(p, f)[3][:, 0]
+    y = (np.arange(Ny) + 0.5) / Ny
+    Cp, g, Pr = 2.0, 2.0, 1.0
+    d = (1 + 2 * Kn) ** 2
+    Tns = 1 + 4 * g / (g + 1) * Kn * Uw ** 2 / (Cp * d) + 2 * Pr * Uw ** 2 * y * (1 - y) / (Cp * d)
+    assert np.max(np.abs(T - Tns)) < 0.05 * np.max(Tns - 1)
+    assert abs(T[Ny // 2] - Tns[Ny // 2]) < 0.02 * (Tns[Ny // 2] - 1)
+    assert np.max(np.abs(T - T[::-1])) < 1e-13
+
+
+@pytest.mark.slow
+def test_second_order_grid_convergence(oracle):
+    # Sec. IV convergence study at the paper's setting (thermal, Kn = 0.01):
+    # E_U and E_T (Eq. (16)-(17)) of coarse grids against a fine-grid reference
+    # fall at second order in the grid size.
+    Kn, Uw, ref = 0.01, 0.2, 256
+    sols = {}
+    for Ny in (16, 32, 64, ref):
+        p = oracle.Problem(lattice="D2Q37", Nx=1, Ny=Ny, eq_order=4, thermal=True, Kn=Kn,
+                           u_wall=(-Uw, Uw))
+        f = oracle.init_fields(p, np.ones((Ny, 1)))
+        ok, _, _ = oracle.run_to_residual(p, f, 1e-12, 3000000, 500)
+        assert ok
+        _, ux, _, T = oracle.macros(p, f)
+        sols[Ny] = ((np.arange(Ny) + 0.5) / Ny, ux[:, 0], T[:, 0])
+    yf, uf, Tf = sols[ref]
+    EU, ET = [], []
+    for Ny in (16, 32, 64):
+        y, u, T = sols[Ny]
+        ur = np.interp(y, yf, uf)
+        Tr = np.interp(y, yf, Tf)
+        EU.append(math.sqrt(np.sum((u - ur) ** 2) / np.sum(ur ** 2)))
+        ET.append(math.sqrt(np.sum((T - Tr) ** 2) / np.sum((Tr - 1.0) ** 2)))
+    sU = np.polyfit(np.log([16, 32, 64]), np.log(EU), 1)[0]
+    sT = np.polyfit(np.log([16, 32, 64]), np.log(ET), 1)[0]
+    assert -2.3 < sU < -1.7, (EU, sU)
+    assert -2.3 < sT < -1.6, (ET, sT)
