@@ -63,27 +63,30 @@ def _dfact(n: int) -> int:
 def _newton_shell_system(shells, conds, guess):
     """Solve sum_k w_k S_pq(k) s^(p+q) = (2p-1)!!(2q-1)!! for (w, s).
 
-    S_pq(k) = sum over shell k of e_x^(2p) e_y^(2q); analytic Jacobian.
+    S_pq(k) = sum over shell k of e_x^(2p) e_y^(2q); analytic Jacobian.  The
+    residual is evaluated in numpy's extended precision and the float64 Newton
+    correction is applied to the extended-precision iterate (iterative
+    refinement), so the result is correctly rounded to float64.
     """
+    ld = np.longdouble
     pts = [_shell(*s) for s in shells]
     S = np.array([[sum(ex ** (2 * p) * ey ** (2 * q) for ex, ey in pk) for pk in pts]
-                  for (p, q) in conds], dtype=np.float64)
-    deg = np.array([p + q for (p, q) in conds], dtype=np.float64)
-    rhs = np.array([_dfact(2 * p - 1) * _dfact(2 * q - 1) for (p, q) in conds],
-                   dtype=np.float64)
-    x = np.array(guess, dtype=np.float64)
+                  for (p, q) in conds], dtype=ld)
+    deg = np.array([p + q for (p, q) in conds], dtype=ld)
+    rhs = np.array([_dfact(2 * p - 1) * _dfact(2 * q - 1) for (p, q) in conds], dtype=ld)
+    x = np.array(guess, dtype=ld)
     for _ in range(200):
         w, s = x[:-1], x[-1]
         sp = s ** deg
         F = (S @ w) * sp - rhs
         J = np.empty((len(conds), len(x)))
-        J[:, :-1] = S * sp[:, None]
-        J[:, -1] = (S @ w) * deg * s ** (deg - 1)
-        dx = np.linalg.solve(J, -F)
-        x = x + dx
-        if np.max(np.abs(dx)) < 1e-16 * max(1.0, np.max(np.abs(x))):
+        J[:, :-1] = (S * sp[:, None]).astype(np.float64)
+        J[:, -1] = ((S @ w) * deg * s ** (deg - 1)).astype(np.float64)
+        dx = np.linalg.solve(J, -F.astype(np.float64))
+        x = x + dx.astype(ld)
+        if np.max(np.abs(dx)) < 1e-19 * max(1.0, float(np.max(np.abs(x)))):
             break
-    return x[:-1], x[-1], pts
+    return x[:-1].astype(np.float64), x[-1], pts
 
 
 def _from_shells(name, shells, w_shell, s):
@@ -93,7 +96,7 @@ def _from_shells(name, shells, w_shell, s):
             e.append(p)
             w.append(w_shell[k])
     return OracleLattice(name, np.array(e, dtype=np.int32),
-                         np.array(w, dtype=np.float64), math.sqrt(s))
+                         np.array(w, dtype=np.float64), float(np.sqrt(np.longdouble(s))))
 
 
 def d2q17() -> OracleLattice:
@@ -116,19 +119,22 @@ def d2q37() -> OracleLattice:
 
 
 def d2q25(root: int = 0) -> OracleLattice:
-    s = (5.0 + math.sqrt(10.0)) / 3.0 if root == 0 else (5.0 - math.sqrt(10.0)) / 3.0
-    w3 = (3.0 - s) / (144.0 * s * s)
-    w1 = 1.0 / (2.0 * s) - 9.0 * w3
-    w0 = 1.0 - 2.0 * w1 - 2.0 * w3
+    # closed form evaluated in extended precision, then rounded
+    ld = np.longdouble
+    r10 = np.sqrt(ld(10))
+    s = (ld(5) + r10) / ld(3) if root == 0 else (ld(5) - r10) / ld(3)
+    w3 = (ld(3) - s) / (ld(144) * s * s)
+    w1 = ld(1) / (ld(2) * s) - ld(9) * w3
+    w0 = ld(1) - ld(2) * w1 - ld(2) * w3
     w1d = {0: w0, 1: w1, 3: w3}
     e, w = [], []
     for ex in (0, 1, -1, 3, -3):
         for ey in (0, 1, -1, 3, -3):
             e.append((ex, ey))
-            w.append(w1d[abs(ex)] * w1d[abs(ey)])
+            w.append(float(w1d[abs(ex)] * w1d[abs(ey)]))
     return OracleLattice("D2Q25" if root == 0 else "D2Q25b",
                          np.array(e, dtype=np.int32), np.array(w, dtype=np.float64),
-                         math.sqrt(s))
+                         float(np.sqrt(s)))
 
 
 def get(name: str) -> OracleLattice:
