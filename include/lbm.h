@@ -1,0 +1,206 @@
+/*
+ * lbm.h - C ABI of a GB300 (sm_103a) library for the streaming-collision
+ * lattice Boltzmann scheme of Meng & Zhang, "Kinetic diffuse boundary
+ * condition for high-order lattice Boltzmann model with streaming-collision
+ * mechanism" (arXiv:1209.5201).
+ *
+ * What the library computes (one time step, every fluid cell x, velocity a):
+ *   pull   f_in(x, a) = f~*(x - e_a, a)                      Eq. (5), left side
+ *          or, where x - e_a lies beyond a wall, the diffuse re-emission
+ *          M_in * g_a^eq(u_w, T_w) / sum_l sum_out g^eq(u_w, T_w)     Eq. (12)
+ *   moments rho, u, T of f_in                                  Eq. (3)
+ *   relax   f~* = f_in - dt/(tau + dt/2) (f_in - rho g^eq(u, T))  Eq. (4)-(5)
+ * The stored state is the post-collision transformed distribution f~*.
+ *
+ * Conventions shared by every call:
+ *  - Units are the paper's non-dimensional ones (Sec. II, Eq. (2)): speeds in
+ *    sqrt(R T0), lengths in the channel height (= 1), time in L/sqrt(R T0).
+ *  - Lattice velocities are c_a = r e_a with integer e_a, |e_a,y| <= 3; one
+ *    step dt = 1/(r Ny) moves a population by e_a cells (Sec. II, after Eq. (5)).
+ *  - Grid: Nx periodic columns x, Ny fluid rows j at y = (j + 1/2)/Ny; the
+ *    walls sit half a cell outside rows 0 and Ny-1 (Sec. III).  The bottom
+ *    wall (y = 0) moves with u_wall[0], the top one (y = 1) with u_wall[1],
+ *    both tangentially (along x).
+ *  - Host arrays of per-cell fields are row-major [Ny][Nx] FP64.  Host arrays
+ *    of distributions are [Q][Ny][Nx] FP64 in the library's velocity order
+ *    (query it with lbm_lattice_tables).
+ *  - Every call returns an int status (LBM_OK = 0).  No C++ exception crosses
+ *    the ABI.  On failure the thread-local message of lbm_last_error says why.
+ *  - Handles are opaque and not thread-safe: one host thread at a time per
+ *    handle.  Device work is enqueued on the caller's CUDA stream, given as a
+ *    cudaStream_t cast to void* (NULL = the legacy default stream).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LBM_OK             0
+#define LBM_EINVAL         1   /* bad argument, size or parameter            */
+#define LBM_ENOMEM         2   /* host or device allocation failed           */
+#define LBM_EBUDGET        3   /* request can never fit the memory budget    */
+#define LBM_ENOTCONVERGED  4   /* max_steps reached, or residual stagnated   */
+#define LBM_ENONFINITE     5   /* NaN / Inf met in a residual or state       */
+#define LBM_ETIMEOUT       6   /* a bounded device or host wait ran out      */
+#define LBM_ECUDA          7   /* a CUDA runtime call failed                 */
+#define LBM_EBUSY          8   /* queue or slot table full; retry later      */
+
+/* Text of a status code (static storage). */
+const char *lbm_status_string(int status);
+/* Copy the calling thread's last error message (NUL-terminated, truncated to
+ * n bytes).  Returns LBM_OK. */
+int lbm_last_error(char *buf, size_t n);
+/* Library version. */
+int lbm_version(int *major, int *minor);
+
+/* ---- lattices: xi = {c_a, w_a} (Sec. II, after Eq. (3)) ---------------- */
+#define LBM_LATTICE_D2Q17   17  /* Shan-Yuan-Chen D2Q17, degree 7 (Sec. IV)  */
+#define LBM_LATTICE_D2Q25   25  /* D1Q5 {0,+-1,+-3}^2, root r^2=(5+sqrt10)/3 */
+#define LBM_LATTICE_D2Q25B  26  /* same set, other root r^2=(5-sqrt10)/3     */
+#define LBM_LATTICE_D2Q37   37  /* degree-9 D2Q37 (the paper's cited set)   */
+
+typedef struct lbm_lattice lbm_lattice;
+
+/* Build a lattice: the library solves the Gaussian moment conditions for the
+ * weights and the scale r in extended precision (Sec. II: "the discrete
+ * velocity set may be determined through several ways").  *out is owned by
+ * the caller and released with lbm_lattice_destroy.
+ * Errors: LBM_EINVAL (unknown kind), LBM_ENOMEM. */
+int lbm_lattice_create(int kind, lbm_lattice **out);
+int lbm_lattice_destroy(lbm_lattice *lat);
+/* Q, scale r, ghost depth N = max |e_y| (Sec. III) and isotropy degree. */
+int lbm_lattice_info(const lbm_lattice *lat, int *Q, double *r, int *ghost_depth,
+                     int *degree);
+/* Copy the tables: e (Q x 2 int8, x then y) and w (Q doubles); either may be
+ * NULL.  Order is the library's velocity order used by every [Q] array. */
+int lbm_lattice_tables(const lbm_lattice *lat, int8_t *e, double *w);
+/* Largest |sum_a w_a c_ax^p c_ay^q - E[c_x^p c_y^q]| over p + q <= degree,
+ * E the unit Gaussian moment (the isotropy the quadrature must satisfy for
+ * Eq. (4)).  Errors: LBM_EINVAL if degree < 0 or > 16. */
+int lbm_lattice_verify(const lbm_lattice *lat, int degree, double *max_err);
+
+/* ---- solver parameters -------------------------------------------------- */
+#define LBM_FP64     0   /* FP64 storage and arithmetic                        */
+#define LBM_FP32     1   /* FP32 storage and arithmetic                        */
+#define LBM_BF16DEV  2   /* BF16 storage of d_a = f~*_a - w_a rho, FP32 rho
+                            plane, FP32 arithmetic                            */
+
+#define LBM_KERNEL_AUTO     0   /* library picks                             */
+#define LBM_KERNEL_DIRECT   1   /* one-pass pull kernel, global loads         */
+#define LBM_KERNEL_STAGED   2   /* TMA-staged tile kernel (shared memory)     */
+
+typedef struct lbm_params {
+    int32_t Nx;          /* periodic columns, >= 1                            */
+    int32_t Ny;          /* fluid rows between the walls, >= 2 * ghost depth  */
+    int32_t eq_order;    /* Hermite orders kept in Eq. (4): 2, 3 or 4         */
+    int32_t thermal;     /* 0: T = 1 in the collision (isothermal, Sec. II)   */
+    double Kn;           /* Knudsen number of Eq. (15); tau = sqrt(2/pi) Kn
+                            mu/(rho T) with mu = T^mu_exp (Sec. II)            */
+    double tau;          /* > 0 overrides Kn with a constant tau (units of t)  */
+    double mu_exp;       /* viscosity law exponent, default 1                  */
+    double u_wall[2];    /* x-velocity of bottom and top wall                  */
+    double T_wall[2];    /* wall temperatures; isothermal runs use 1           */
+    int32_t precision;   /* LBM_FP64 / LBM_FP32 / LBM_BF16DEV                  */
+    int32_t kernel;      /* LBM_KERNEL_*                                       */
+    double rho0;         /* initial density of lbm_solver_init                 */
+    double noise_amp;    /* initial rho = rho0 (1 + noise_amp (2U - 1))        */
+    uint64_t seed;       /* U = SplitMix64 draw at counter j*Nx + x            */
+} lbm_params;
+
+/* Defaults: Nx = 1, Ny = 64, eq_order 2, isothermal, Kn 0.1, tau 0, mu_exp 1,
+ * walls -0.1 / +0.1 at T 1, FP64, AUTO kernel, rho0 1, no noise, seed 7. */
+void lbm_params_default(lbm_params *p);
+
+/* ---- single-domain solver ----------------------------------------------- */
+typedef struct lbm_solver lbm_solver;
+
+/* Device bytes a solver needs (two state buffers plus reduction space). */
+int lbm_solver_required_bytes(const lbm_lattice *lat, const lbm_params *p,
+                              size_t *bytes);
+
+/* Create a solver.  If device_mem is non-NULL it must point to at least
+ * lbm_solver_required_bytes bytes of device memory, 256-byte aligned, that the
+ * caller owns and keeps alive until lbm_solver_destroy (the Python binding
+ * passes a torch allocation); if NULL the library allocates (and frees) its
+ * own with cudaMallocAsync on `stream`.  The lattice may be destroyed after
+ * this call.  Errors: LBM_EINVAL (parameters; Ny < 2 N, eq_order, precision),
+ * LBM_ENOMEM, LBM_ECUDA. */
+int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
+                      void *device_mem, size_t device_bytes, lbm_solver **out);
+int lbm_solver_destroy(lbm_solver *s);
+
+/* f~* = rho g^eq(0, 1) with rho = rho0 (1 + noise_amp (2U - 1)); U is the
+ * SplitMix64 draw (Steele, Lea & Flood 2014) of counter j*Nx + x under seed:
+ * first output of the stream seeded with seed XOR counter, top 53 bits.
+ * Asynchronous on the solver's stream; resets the step counter. */
+int lbm_solver_init(lbm_solver *s);
+/* f~* = rho g^eq(u, T) (Eq. (4)) from host fields [Ny][Nx]; ux, uy, T may be
+ * NULL (0, 0, 1).  Synchronous.  Resets the step counter. */
+int lbm_solver_init_fields(lbm_solver *s, const double *rho, const double *ux,
+                           const double *uy, const double *T);
+
+/* Enqueue n >= 0 time steps on the stream (asynchronous; no host round trip
+ * inside).  Errors: LBM_EINVAL, LBM_ECUDA (launch failure). */
+int lbm_solver_step(lbm_solver *s, int64_t n);
+/* Wait for the solver's stream.  Errors: LBM_ECUDA. */
+int lbm_solver_sync(lbm_solver *s);
+
+/* Copy the post-collision state f~* to / from host FP64 [Q][Ny][Nx]
+ * (converted from / to the storage precision).  Synchronous. */
+int lbm_solver_get_f(lbm_solver *s, double *f);
+int lbm_solver_set_f(lbm_solver *s, const double *f);
+
+/* Macroscopic fields of Eq. (3) of the current state, host FP64 [Ny][Nx]
+ * each; any pointer may be NULL.  T is the kinetic temperature
+ * sum f |c - u|^2 / (D rho) even for isothermal runs.  Synchronous. */
+int lbm_solver_macros(lbm_solver *s, double *rho, double *ux, double *uy,
+                      double *T);
+
+/* Checkpoint: the exact stored bytes plus the step counter.  get_state
+ * writes state_bytes bytes to host memory; set_state restores them; a resumed
+ * run is bit-identical to an uninterrupted one.  Errors: LBM_EINVAL if bytes
+ * is smaller than the size (get) or differs from it (set). */
+int lbm_solver_state_bytes(lbm_solver *s, size_t *bytes);
+int lbm_solver_get_state(lbm_solver *s, void *buf, size_t bytes);
+int lbm_solver_set_state(lbm_solver *s, const void *buf, size_t bytes);
+
+/* Steady-state driver (the paper's Couette solutions are steady, Sec. IV):
+ * run chunks of check_every steps; after each chunk
+ *   res = max( ||u_x - u_x'||_2 / ||u_x||_2 ,
+ *              thermal: ||T - T'||_2 / ||T - T_ref||_2 )
+ * over all cells, primes = previous check, T_ref = mean wall temperature,
+ * reductions in FP64 on the device.  Returns LBM_OK when res <= tol,
+ * LBM_ENOTCONVERGED after max_steps or when res has not decreased over 50
+ * consecutive checks, LBM_ENONFINITE on a NaN/Inf.  *steps and *res receive
+ * the steps run by this call and the last residual. */
+int lbm_solver_run_to_residual(lbm_solver *s, double tol, int64_t max_steps,
+                               int32_t check_every, int64_t *steps, double *res);
+
+typedef struct lbm_stats {
+    int64_t steps;        /* steps since the last init                        */
+    double mass0;         /* sum of rho at init                               */
+    double mass;          /* sum of rho now                                   */
+    double mass_drift;    /* |mass - mass0| / mass0                           */
+    double residual;      /* last residual of run_to_residual (or -1)        */
+    double wall_in[2];    /* sum over columns of M_in of the last step,
+                             bottom / top (numerator of Eq. (12))             */
+} lbm_stats;
+/* Synchronous (one reduction over the state). */
+int lbm_solver_stats(lbm_solver *s, lbm_stats *st);
+
+/* Diffuse-wall incoming mass per ghost column (numerator of Eq. (12)) of the
+ * current state: m_in[2][Nx] host FP64, bottom row then top row.  M_in(x) sums
+ * the post-collision populations that stream into ghost column x through all
+ * N ghost layers (Sec. III).  Synchronous. */
+int lbm_solver_wall_mass(lbm_solver *s, double *m_in);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

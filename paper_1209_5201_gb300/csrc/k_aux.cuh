@@ -1,0 +1,256 @@
+// Auxiliary kernels of a solver: initial state, conversions between the
+// storage format and FP64 host planes, Eq. (3) macroscopic fields, the wall
+// incoming mass of Eq. (12), and FP64 reductions.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kAuxThreads = 256;
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): first output of the stream
+// seeded with seed XOR counter; top 53 bits as a double in [0, 1).
+__device__ __forceinline__ double splitmix_u01(uint64_t seed, uint64_t k) {
+    uint64_t z = (seed ^ k) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// Equilibrium f~* = rho g^eq(u, T) (Eq. (4)) of every velocity.
+template <int Q, class C>
+__device__ __forceinline__ void equilibrium_all(C rho, C ux, C uy, C T, const KConsts<C> &k,
+                                                C (&o)[Q]) {
+    // A collision with omega = 1 from f = 0 leaves exactly rho g^eq.
+    using L = Lat<Q>;
+    Collision<Q, C> col;
+    const C u2 = ux * ux + uy * uy;
+    const C th = T - C(1);
+    col.omc = C(0);
+    col.sx = k.r * ux;
+    col.sy = k.r * uy;
+    col.rho = rho;
+    col.A3 = k.eq_order >= 3 ? C(1) / C(6) : C(0);
+    col.A4 = k.eq_order >= 4 ? C(1) / C(24) : C(0);
+#pragma unroll
+    for (int s = 0; s < L::NSH; ++s) {
+        const C c2 = k.r2 * C(L::shell_e2(s));
+        C a0 = C(1) - C(0.5) * u2 + C(0.5) * th * (c2 - C(2));
+        C a1 = C(1), a2 = C(0.5);
+        if (k.eq_order >= 3) a1 += C(-0.5) * u2 + C(0.5) * th * (c2 - C(4));
+        if (k.eq_order >= 4) {
+            a0 += C(0.125) * u2 * u2 - C(0.25) * th * (c2 - C(4)) * u2 +
+                  C(0.125) * th * th * (c2 * c2 - C(8) * c2 + C(8));
+            a2 += C(-0.25) * u2 + C(0.25) * th * (c2 - C(6));
+        }
+        col.A0[s] = a0; col.A1[s] = a1; col.A2[s] = a2;
+        col.cw[s] = rho * k.wsh[s];
+    }
+    o[0] = col.rest(C(0));
+    PairLoop<1, Q>::run([&](auto ic) {
+        constexpr int A = decltype(ic)::value;
+        col.template pair<A>(C(0), C(0), o[A], o[A + 1]);
+    });
+}
+
+template <int Q, int PREC>
+__device__ __forceinline__ void store_cell(typename Store<PREC>::S *f, float *rplane,
+                                           const KConsts<typename Store<PREC>::C> &k, int x,
+                                           int j, const typename Store<PREC>::C (&o)[Q],
+                                           typename Store<PREC>::C rho) {
+    using S = typename Store<PREC>::S;
+    using C = typename Store<PREC>::C;
+    const long long roff = (long long)j * k.pitch;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        C v = o[a];
+        if constexpr (Store<PREC>::dev) v -= k.w[a] * rho;
+        store_with_images<S>(f + (long long)a * k.plane + roff, x, k.Nx, from_c<S>(v));
+    }
+    if constexpr (Store<PREC>::dev) store_with_images<float>(rplane + roff, x, k.Nx, (float)rho);
+}
+
+// f~* = rho0 (1 + amp (2U - 1)) g^eq(0, 1) = rho w_a.
+template <int Q, int PREC>
+__global__ void k_init_rest(typename Store<PREC>::S *f, float *rplane,
+                            const __grid_constant__ KConsts<typename Store<PREC>::C> k,
+                            double rho0, double amp, uint64_t seed) {
+    using C = typename Store<PREC>::C;
+    const long long n = (long long)k.Nx * k.Ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
+        double rho = rho0;
+        if (amp != 0.0) rho = rho0 * (1.0 + amp * (2.0 * splitmix_u01(seed, (uint64_t)c) - 1.0));
+        C o[Q];
+        equilibrium_all<Q, C>((C)rho, C(0), C(0), C(1), k, o);
+        store_cell<Q, PREC>(f, rplane, k, x, j, o, (C)rho);
+    }
+}
+
+// f~* = rho g^eq(u, T) from FP64 device planes [Ny][Nx] (NULL: u = 0, T = 1).
+template <int Q, int PREC>
+__global__ void k_init_fields(typename Store<PREC>::S *f, float *rplane,
+                              const __grid_constant__ KConsts<typename Store<PREC>::C> k,
+                              const double *rho, const double *ux, const double *uy,
+                              const double *T) {
+    using C = typename Store<PREC>::C;
+    const long long n = (long long)k.Nx * k.Ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
+        C o[Q];
+        equilibrium_all<Q, C>((C)rho[c], ux ? (C)ux[c] : C(0), uy ? (C)uy[c] : C(0),
+                              T ? (C)T[c] : C(1), k, o);
+        store_cell<Q, PREC>(f, rplane, k, x, j, o, (C)rho[c]);
+    }
+}
+
+// Velocity plane a of the stored state -> FP64 logical plane [Ny][Nx].
+template <int Q, int PREC>
+__global__ void k_plane_to_f64(const typename Store<PREC>::S *f, const float *rplane,
+                               const __grid_constant__ KConsts<typename Store<PREC>::C> k,
+                               int a, double *out) {
+    const long long n = (long long)k.Nx * k.Ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
+        const long long r = (long long)j * k.pitch + x + kPadL;
+        auto v = to_c(f[(long long)a * k.plane + r]);
+        if constexpr (Store<PREC>::dev) v += k.w[a] * rplane[r];
+        out[c] = (double)v;
+    }
+}
+
+// FP64 logical plane -> velocity plane a of the stored state (with images).
+// BF16DEV needs the density plane written first (launch_rho_plane).
+template <int Q, int PREC>
+__global__ void k_plane_from_f64(typename Store<PREC>::S *f, const float *rplane,
+                                 const __grid_constant__ KConsts<typename Store<PREC>::C> k,
+                                 int a, const double *in) {
+    using S = typename Store<PREC>::S;
+    using C = typename Store<PREC>::C;
+    const long long n = (long long)k.Nx * k.Ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
+        C v = (C)in[c];
+        if constexpr (Store<PREC>::dev) v -= k.w[a] * rplane[(long long)j * k.pitch + x + kPadL];
+        store_with_images<S>(f + (long long)a * k.plane + (long long)j * k.pitch, x, k.Nx,
+                             from_c<S>(v));
+    }
+}
+
+// Eq. (3) fields of every cell of the stored state; T is the kinetic
+// temperature sum f |c - u|^2 / (2 rho).  Any output may be NULL.
+template <int Q, int PREC>
+__global__ void k_macros(const typename Store<PREC>::S *f, const float *rplane,
+                         const __grid_constant__ KConsts<typename Store<PREC>::C> k,
+                         double *rho, double *ux, double *uy, double *T) {
+    using L = Lat<Q>;
+    const long long n = (long long)k.Nx * k.Ny;
+    const double r = (double)k.r;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
+        const long long ro = (long long)j * k.pitch + x + kPadL;
+        double fv[Q];
+        double s0 = 0, sx = 0, sy = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            auto v = to_c(f[(long long)a * k.plane + ro]);
+            if constexpr (Store<PREC>::dev) v += k.w[a] * rplane[ro];
+            fv[a] = (double)v;
+            s0 += fv[a];
+            sx += L::ex(a) * fv[a];
+            sy += L::ey(a) * fv[a];
+        }
+        const double u = r * sx / s0, v = r * sy / s0;
+        double e = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const double Cx = r * L::ex(a) - u, Cy = r * L::ey(a) - v;
+            e += fv[a] * (Cx * Cx + Cy * Cy);
+        }
+        if (rho) rho[c] = s0;
+        if (ux) ux[c] = u;
+        if (uy) uy[c] = v;
+        if (T) T[c] = e / (2.0 * s0);
+    }
+}
+
+// Numerator of Eq. (12) for every ghost column of both walls: m_in[w*Nx + x].
+template <int Q, int PREC>
+__global__ void k_wall_mass(const typename Store<PREC>::S *f, const float *rplane,
+                            const __grid_constant__ KConsts<typename Store<PREC>::C> k,
+                            double *m_in) {
+    using L = Lat<Q>;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * k.Nx;
+         t += gridDim.x * blockDim.x) {
+        const int wall = t / k.Nx, xw = t % k.Nx;
+        double m = 0.0;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const int eyb = L::ey(b);
+            if (wall == 0 ? !(eyb < 0) : !(eyb > 0)) continue;
+            const int xs = wrap(xw - L::ex(b), k.Nx) + kPadL;
+            const int depth = eyb < 0 ? -eyb : eyb;
+            for (int kk = 0; kk < depth; ++kk) {
+                const int row = wall == 0 ? kk : k.Ny - 1 - kk;
+                double v = (double)to_c(f[(long long)b * k.plane + (long long)row * k.pitch + xs]);
+                if constexpr (Store<PREC>::dev)
+                    v += (double)k.w[b] * (double)rplane[(long long)row * k.pitch + xs];
+                m += v;
+            }
+        }
+        m_in[t] = m;
+    }
+}
+
+// Block-level FP64 sum of NV values per thread (warp shuffle, then shared).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
+    __shared__ double sh[32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    if (lane == 0)
+        for (int i = 0; i < NV; ++i) sh[wid][i] = v[i];
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < NV; ++i) {
+            double s = lane < nw ? sh[lane][i] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) out[i] = s;
+        }
+    }
+}
+
+// Sum of rho over all cells: per-block partials (fixed grid, fixed order).
+template <int Q, int PREC>
+__global__ void k_mass_partials(const typename Store<PREC>::S *f, const float *rplane,
+                                const __grid_constant__ KConsts<typename Store<PREC>::C> k,
+                                double *partials) {
+    const long long n = (long long)k.Nx * k.Ny;
+    double acc[1] = {0.0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
+        const long long ro = (long long)j * k.pitch + x + kPadL;
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            auto v = to_c(f[(long long)a * k.plane + ro]);
+            if constexpr (Store<PREC>::dev) v += k.w[a] * rplane[ro];
+            s += (double)v;
+        }
+        acc[0] += s;
+    }
+    block_sum<1>(acc, partials + blockIdx.x);
+}
+
+}  // namespace lbm

@@ -1,0 +1,117 @@
+// One-pass pull kernel of a full time step (Eq. (5) with the Eq. (12) wall).
+//
+// One thread per fluid cell (x, j); a block covers BX consecutive columns of
+// one row.  Every population is read once, straight from global memory at the
+// source cell (x - e_ax, j - e_ay): SoA rows are contiguous in x, so a warp's
+// 32 loads of one velocity plane are one contiguous (possibly 4..12-byte
+// shifted) segment.  Periodic images in the padded row remove the modulo in x.
+// Blocks of the N rows next to a wall first sum the incoming mass M_in of the
+// BX + 6 ghost columns their fill populations come from (FP64, fixed order).
+#pragma once
+
+#include <type_traits>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// M_in(x') for x' = x0 - 3 + t, t in [0, BX + 6): post-collision populations
+// of the N rows next to `wall` that stream into ghost column x' (Sec. III:
+// incoming at layer l when e.n < -l; summed over all layers, Eq. (12)).
+template <int Q, int PREC, int BX>
+__device__ __forceinline__ void wall_prologue(const typename Store<PREC>::S *__restrict__ fin,
+                                              const float *__restrict__ rin,
+                                              const KConsts<typename Store<PREC>::C> &k,
+                                              int wall, int x0, double *s_min) {
+    using L = Lat<Q>;
+    for (int t = threadIdx.x; t < BX + 6; t += BX) {
+        const int xw = wrap(x0 - 3 + t, k.Nx);
+        double m = 0.0;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const int eyb = L::ey(b);
+            const bool incoming = wall == 0 ? (eyb < 0) : (eyb > 0);
+            if (!incoming) continue;
+            const int xs = wrap(xw - L::ex(b), k.Nx) + kPadL;
+            const int depth = eyb < 0 ? -eyb : eyb;
+            for (int kk = 0; kk < depth; ++kk) {
+                const int row = wall == 0 ? kk : k.Ny - 1 - kk;
+                const long long idx = (long long)b * k.plane + (long long)row * k.pitch + xs;
+                double v = (double)to_c(fin[idx]);
+                if constexpr (Store<PREC>::dev)
+                    v += (double)k.w[b] * (double)rin[(long long)row * k.pitch + xs];
+                m += v;
+            }
+        }
+        s_min[t] = m;
+    }
+}
+
+template <int Q, int PREC, bool WALL>
+__device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__ fin,
+                                     const float *__restrict__ rin,
+                                     const KConsts<typename Store<PREC>::C> &k, int x, int j,
+                                     const double *s_min, typename Store<PREC>::C (&f)[Q]) {
+    using L = Lat<Q>;
+    using C = typename Store<PREC>::C;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int sj = j - L::ey(a);
+        const int sx = x - L::ex(a) + kPadL;
+        if (WALL && sj < 0) {
+            f[a] = (C)(s_min[threadIdx.x + 3 - L::ex(a)] * k.wcoef[0][a]);
+        } else if (WALL && sj >= k.Ny) {
+            f[a] = (C)(s_min[threadIdx.x + 3 - L::ex(a)] * k.wcoef[1][a]);
+        } else {
+            const long long ridx = (long long)sj * k.pitch + sx;
+            C v = to_c(fin[(long long)a * k.plane + ridx]);
+            if constexpr (Store<PREC>::dev) v += k.w[a] * rin[ridx];
+            f[a] = v;
+        }
+    }
+}
+
+template <int Q, int PREC, int BX>
+__global__ void __launch_bounds__(BX)
+k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
+              typename Store<PREC>::S *__restrict__ fout, const float *__restrict__ rin,
+              float *__restrict__ rout,
+              const __grid_constant__ KConsts<typename Store<PREC>::C> k) {
+    using L = Lat<Q>;
+    using S = typename Store<PREC>::S;
+    using C = typename Store<PREC>::C;
+    __shared__ double s_min[BX + 6];
+    const int j = blockIdx.y;
+    const int x0 = blockIdx.x * BX;
+    const int x = x0 + threadIdx.x;
+    const bool bot = j < L::N, top = j >= k.Ny - L::N;
+    if (bot || top) {
+        wall_prologue<Q, PREC, BX>(fin, rin, k, bot ? 0 : 1, x0, s_min);
+        __syncthreads();
+    }
+    if (x >= k.Nx) return;
+
+    C f[Q];
+    if (bot || top) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, f);
+    else pull<Q, PREC, false>(fin, rin, k, x, j, s_min, f);
+
+    Collision<Q, C> col;
+    col.setup(f, k);
+    C o[Q];
+    o[0] = col.rest(f[0]);
+    PairLoop<1, Q>::run([&](auto ic) {
+        constexpr int A = decltype(ic)::value;
+        col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
+    });
+
+    const long long roff = (long long)j * k.pitch;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        C v = o[a];
+        if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
+        store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx, from_c<S>(v));
+    }
+    if constexpr (Store<PREC>::dev) store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);
+}
+
+}  // namespace lbm

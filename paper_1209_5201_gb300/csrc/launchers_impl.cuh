@@ -1,0 +1,120 @@
+// Definitions of Launch<PREC>: lattice dispatch and launch geometry.
+#pragma once
+
+#include "k_aux.cuh"
+#include "k_step_direct.cuh"
+#include "launchers.h"
+
+namespace lbm {
+
+template <int PREC>
+struct Consts;
+template <> struct Consts<LBM_FP64> {
+    static const KConsts<double> &get(const SolverImpl &s) { return s.kd; }
+};
+template <> struct Consts<LBM_FP32> {
+    static const KConsts<float> &get(const SolverImpl &s) { return s.kf; }
+};
+template <> struct Consts<LBM_BF16DEV> {
+    static const KConsts<float> &get(const SolverImpl &s) { return s.kf; }
+};
+
+inline int aux_blocks(long long n) {
+    long long b = (n + kAuxThreads - 1) / kAuxThreads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+#define LBM_DISPATCH_Q(Q_, ...)                                 \
+    switch (Q_) {                                               \
+    case 17: { constexpr int QQ = 17; __VA_ARGS__; } break;     \
+    case 25: { constexpr int QQ = 25; __VA_ARGS__; } break;     \
+    case 37: { constexpr int QQ = 37; __VA_ARGS__; } break;     \
+    default: return (int)cudaErrorInvalidValue;                 \
+    }
+
+template <int PREC>
+int Launch<PREC>::step(SolverImpl &s, int src, int dst) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    constexpr int BX = 128;
+    dim3 grid((s.p.Nx + BX - 1) / BX, s.p.Ny);
+    const S *fin = (const S *)s.f[src];
+    S *fout = (S *)s.f[dst];
+    LBM_DISPATCH_Q(s.L.Q, (k_step_direct<QQ, PREC, BX><<<grid, BX, 0, s.stream>>>(
+                               fin, fout, s.rho[src], s.rho[dst], k)));
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::init_rest(SolverImpl &s) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    const long long n = (long long)s.p.Nx * s.p.Ny;
+    LBM_DISPATCH_Q(s.L.Q, (k_init_rest<QQ, PREC><<<aux_blocks(n), kAuxThreads, 0, s.stream>>>(
+                               (S *)s.f[s.cur], s.rho[s.cur], k, s.p.rho0, s.p.noise_amp,
+                               s.p.seed)));
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::init_fields(SolverImpl &s, const double *rho, const double *ux,
+                              const double *uy, const double *T) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    const long long n = (long long)s.p.Nx * s.p.Ny;
+    LBM_DISPATCH_Q(s.L.Q, (k_init_fields<QQ, PREC><<<aux_blocks(n), kAuxThreads, 0, s.stream>>>(
+                               (S *)s.f[s.cur], s.rho[s.cur], k, rho, ux, uy, T)));
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::plane_to_f64(SolverImpl &s, int a, double *out) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    const long long n = (long long)s.p.Nx * s.p.Ny;
+    LBM_DISPATCH_Q(s.L.Q, (k_plane_to_f64<QQ, PREC><<<aux_blocks(n), kAuxThreads, 0, s.stream>>>(
+                               (const S *)s.f[s.cur], s.rho[s.cur], k, a, out)));
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::plane_from_f64(SolverImpl &s, int a, const double *in) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    const long long n = (long long)s.p.Nx * s.p.Ny;
+    LBM_DISPATCH_Q(s.L.Q, (k_plane_from_f64<QQ, PREC><<<aux_blocks(n), kAuxThreads, 0, s.stream>>>(
+                               (S *)s.f[s.cur], s.rho[s.cur], k, a, in)));
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::macros(SolverImpl &s, double *rho, double *ux, double *uy, double *T) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    const long long n = (long long)s.p.Nx * s.p.Ny;
+    LBM_DISPATCH_Q(s.L.Q, (k_macros<QQ, PREC><<<aux_blocks(n), kAuxThreads, 0, s.stream>>>(
+                               (const S *)s.f[s.cur], s.rho[s.cur], k, rho, ux, uy, T)));
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::wall_mass(SolverImpl &s, double *m_in) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    LBM_DISPATCH_Q(s.L.Q, (k_wall_mass<QQ, PREC><<<aux_blocks(2LL * s.p.Nx), kAuxThreads, 0,
+                                                   s.stream>>>((const S *)s.f[s.cur],
+                                                               s.rho[s.cur], k, m_in)));
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::mass_partials(SolverImpl &s, double *partials, int nblocks) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    LBM_DISPATCH_Q(s.L.Q, (k_mass_partials<QQ, PREC><<<nblocks, kAuxThreads, 0, s.stream>>>(
+                               (const S *)s.f[s.cur], s.rho[s.cur], k, partials)));
+    return (int)cudaGetLastError();
+}
+
+}  // namespace lbm

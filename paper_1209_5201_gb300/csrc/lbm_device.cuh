@@ -1,0 +1,174 @@
+// Device-side building blocks of the step kernels: compile-time lattice
+// descriptors, storage formats, Eq. (3) moments, Eq. (4) equilibrium in the
+// per-shell polynomial form, Eq. (5) relaxation and the Eq. (12) wall fill.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lattice_tables.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---- compile-time lattice descriptors --------------------------------------
+template <int Q> struct Lat;
+
+#define LBM_DEFINE_LAT(QQ, NSHELL, EX, EY, SH)                                        \
+    template <> struct Lat<QQ> {                                                      \
+        static constexpr int Q = QQ, NSH = NSHELL, N = 3;                             \
+        __host__ __device__ static constexpr int ex(int a) { constexpr int t[] = EX; return t[a]; } \
+        __host__ __device__ static constexpr int ey(int a) { constexpr int t[] = EY; return t[a]; } \
+        __host__ __device__ static constexpr int sh(int a) { constexpr int t[] = SH; return t[a]; } \
+        __host__ __device__ static constexpr int e2(int a) { return ex(a) * ex(a) + ey(a) * ey(a); } \
+        /* |e|^2 of shell s: that of its first member */                              \
+        __host__ __device__ static constexpr int shell_e2(int s) {                     \
+            for (int a = 0; a < Q; ++a) if (sh(a) == s) return e2(a);                  \
+            return 0;                                                                   \
+        }                                                                               \
+    };
+
+LBM_DEFINE_LAT(17, 5, LBM_Q17_EX, LBM_Q17_EY, LBM_Q17_SH)
+LBM_DEFINE_LAT(25, 6, LBM_Q25_EX, LBM_Q25_EY, LBM_Q25_SH)
+LBM_DEFINE_LAT(37, 8, LBM_Q37_EX, LBM_Q37_EY, LBM_Q37_SH)
+
+// ---- storage formats ---------------------------------------------------------
+template <int PREC> struct Store;
+template <> struct Store<LBM_FP64> {
+    using S = double; using C = double;
+    static constexpr bool dev = false;
+};
+template <> struct Store<LBM_FP32> {
+    using S = float; using C = float;
+    static constexpr bool dev = false;
+};
+// d_a = f~*_a - w_a rho in BF16, rho in an FP32 plane, FP32 arithmetic.
+template <> struct Store<LBM_BF16DEV> {
+    using S = __nv_bfloat16; using C = float;
+    static constexpr bool dev = true;
+};
+
+__device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ double to_c(double v) { return v; }
+
+template <class S> __device__ __forceinline__ S from_c(float v);
+template <> __device__ __forceinline__ float from_c<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <class S> __device__ __forceinline__ S from_c(double v);
+template <> __device__ __forceinline__ double from_c<double>(double v) { return v; }
+
+__device__ __forceinline__ int wrap(int v, int n) {
+    int m = v % n;
+    return m < 0 ? m + n : m;
+}
+
+// ---- Eq. (3)-(5): moments, relaxation factor, equilibrium coefficients --------
+// g_a^eq of Eq. (4) for a velocity of shell k, with s = c_a . u, written as
+//   w_k (A0_k + A1_k s + A2_k s^2 + A3 s^3 + A4 s^4)
+// (D = 2, theta = T - 1, c2 = |c_a|^2):
+//   order 2: A0 = 1 - u2/2 + theta (c2 - 2)/2,  A1 = 1,  A2 = 1/2
+//   order 3: A1 += -u2/2 + theta (c2 - 4)/2,  A3 = 1/6
+//   order 4: A0 += u2^2/8 - theta (c2 - 4) u2/4 + theta^2 (c2^2 - 8 c2 + 8)/8
+//            A2 += -u2/4 + theta (c2 - 6)/4,  A4 = 1/24
+// A velocity and its opposite share the even part E = A0 + A2 s^2 + A4 s^4 and
+// have opposite odd parts O = s (A1 + A3 s^2).
+template <int Q, class C>
+struct Collision {
+    using L = Lat<Q>;
+    C omc;                  // 1 - omega
+    C cw[L::NSH];           // omega rho w_k
+    C A0[L::NSH], A1[L::NSH], A2[L::NSH];
+    C A3, A4;
+    C sx, sy;               // r u: s_a = e_ax sx + e_ay sy
+    C rho;
+
+    __device__ __forceinline__ void setup(const C (&f)[Q], const KConsts<C> &k) {
+        C r0 = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            r0 += f[a];
+            if (L::ex(a) != 0) jx += C(L::ex(a)) * f[a];
+            if (L::ey(a) != 0) jy += C(L::ey(a)) * f[a];
+        }
+        rho = r0;
+        const C inv = C(1) / r0;
+        const C ux = k.r * jx * inv, uy = k.r * jy * inv;
+        const C u2 = ux * ux + uy * uy;
+        C th = 0, T = 1;
+        if (k.thermal) {
+            C e2 = 0;
+#pragma unroll
+            for (int a = 1; a < Q; ++a) e2 += C(L::e2(a)) * f[a];
+            T = (k.r2 * e2 * inv - u2) * C(0.5);
+            th = T - C(1);
+        }
+        C taul;
+        if (k.const_tau) taul = k.tau_lat;
+        else if (k.mu_is_one || !k.thermal) taul = k.K * inv;
+        else taul = k.K * inv * pow(T, k.mu_m1);
+        const C om = C(1) / (taul + C(0.5));
+        omc = C(1) - om;
+        sx = k.r * ux;
+        sy = k.r * uy;
+        A3 = k.eq_order >= 3 ? C(1) / C(6) : C(0);
+        A4 = k.eq_order >= 4 ? C(1) / C(24) : C(0);
+        const C orho = om * r0;
+#pragma unroll
+        for (int s = 0; s < L::NSH; ++s) {
+            const C c2 = k.r2 * C(L::shell_e2(s));
+            C a0 = C(1) - C(0.5) * u2 + C(0.5) * th * (c2 - C(2));
+            C a1 = C(1), a2 = C(0.5);
+            if (k.eq_order >= 3) a1 += C(-0.5) * u2 + C(0.5) * th * (c2 - C(4));
+            if (k.eq_order >= 4) {
+                a0 += C(0.125) * u2 * u2 - C(0.25) * th * (c2 - C(4)) * u2 +
+                      C(0.125) * th * th * (c2 * c2 - C(8) * c2 + C(8));
+                a2 += C(-0.25) * u2 + C(0.25) * th * (c2 - C(6));
+            }
+            A0[s] = a0; A1[s] = a1; A2[s] = a2;
+            cw[s] = orho * k.wsh[s];
+        }
+    }
+
+    // post-collision values of the rest velocity and of pair (a, a+1)
+    __device__ __forceinline__ C rest(C f0) const { return omc * f0 + cw[0] * A0[0]; }
+    template <int A>
+    __device__ __forceinline__ void pair(C fa, C fb, C &oa, C &ob) const {
+        constexpr int s = L::sh(A);
+        const C sv = C(L::ex(A)) * sx + C(L::ey(A)) * sy;
+        const C s2 = sv * sv;
+        const C E = A0[s] + s2 * (A2[s] + A4 * s2);
+        const C O = sv * (A1[s] + A3 * s2);
+        const C P = cw[s] * E, R = cw[s] * O;
+        oa = omc * fa + (P + R);
+        ob = omc * fb + (P - R);
+    }
+};
+
+// compile-time loop over the velocity pairs (a = 1, 3, 5, ...)
+template <int A, int Q>
+struct PairLoop {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&fn) {
+        if constexpr (A < Q) {
+            fn(std::integral_constant<int, A>{});
+            PairLoop<A + 2, Q>::run(fn);
+        }
+    }
+};
+
+// Store one population at logical column x of row j, and at every periodic
+// image of x inside the padded row [-kPadL, Nx + kPadL).
+template <class S>
+__device__ __forceinline__ void store_with_images(S *__restrict__ row, int x, int Nx, S v) {
+    row[x + kPadL] = v;
+    if (x < kPadL || x >= Nx - kPadL) {
+        for (int q = x - Nx; q >= -kPadL; q -= Nx) row[q + kPadL] = v;
+        for (int q = x + Nx; q < Nx + kPadL; q += Nx) row[q + kPadL] = v;
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,377 @@
+"""Thin ctypes binding of include/lbm.h (argument marshalling only).
+
+Every function named lbm_* here calls the C function of the same name in the
+in-tree CUDA library (paper_1209_5201_gb300/_build/liblbm_gb300.so) and raises
+LBMError on a non-zero status.  There is no fallback: if the library is
+missing, load() raises.  Host arrays are numpy float64; device memory and the
+CUDA stream come from PyTorch when a Solver is built through the helper class.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm_gb300.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_EBUDGET, LBM_ENOTCONVERGED = 0, 1, 2, 3, 4
+LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ECUDA, LBM_EBUSY = 5, 6, 7, 8
+LBM_LATTICE_D2Q17, LBM_LATTICE_D2Q25, LBM_LATTICE_D2Q25B, LBM_LATTICE_D2Q37 = 17, 25, 26, 37
+LBM_FP64, LBM_FP32, LBM_BF16DEV = 0, 1, 2
+LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_STAGED = 0, 1, 2
+
+LATTICE_KIND = {"D2Q17": 17, "D2Q25": 25, "D2Q25b": 26, "D2Q37": 37}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16dev": 2}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class lbm_params(C.Structure):
+    _fields_ = [("Nx", C.c_int32), ("Ny", C.c_int32), ("eq_order", C.c_int32),
+                ("thermal", C.c_int32), ("Kn", C.c_double), ("tau", C.c_double),
+                ("mu_exp", C.c_double), ("u_wall", C.c_double * 2), ("T_wall", C.c_double * 2),
+                ("precision", C.c_int32), ("kernel", C.c_int32), ("rho0", C.c_double),
+                ("noise_amp", C.c_double), ("seed", C.c_uint64)]
+
+
+class lbm_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("mass0", C.c_double), ("mass", C.c_double),
+                ("mass_drift", C.c_double), ("residual", C.c_double),
+                ("wall_in", C.c_double * 2)]
+
+
+_lib = None
+_VP = C.c_void_p
+_DP = C.POINTER(C.c_double)
+
+_SIGS = {
+    "lbm_status_string": ([C.c_int], C.c_char_p),
+    "lbm_last_error": ([C.c_char_p, C.c_size_t], C.c_int),
+    "lbm_version": ([C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "lbm_lattice_create": ([C.c_int, C.POINTER(_VP)], C.c_int),
+    "lbm_lattice_destroy": ([_VP], C.c_int),
+    "lbm_lattice_info": ([_VP, C.POINTER(C.c_int), _DP, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+                         C.c_int),
+    "lbm_lattice_tables": ([_VP, C.POINTER(C.c_int8), _DP], C.c_int),
+    "lbm_lattice_verify": ([_VP, C.c_int, _DP], C.c_int),
+    "lbm_params_default": ([C.POINTER(lbm_params)], None),
+    "lbm_solver_required_bytes": ([_VP, C.POINTER(lbm_params), C.POINTER(C.c_size_t)], C.c_int),
+    "lbm_solver_create": ([_VP, C.POINTER(lbm_params), _VP, _VP, C.c_size_t, C.POINTER(_VP)],
+                          C.c_int),
+    "lbm_solver_destroy": ([_VP], C.c_int),
+    "lbm_solver_init": ([_VP], C.c_int),
+    "lbm_solver_init_fields": ([_VP, _DP, _DP, _DP, _DP], C.c_int),
+    "lbm_solver_step": ([_VP, C.c_int64], C.c_int),
+    "lbm_solver_sync": ([_VP], C.c_int),
+    "lbm_solver_get_f": ([_VP, _DP], C.c_int),
+    "lbm_solver_set_f": ([_VP, _DP], C.c_int),
+    "lbm_solver_macros": ([_VP, _DP, _DP, _DP, _DP], C.c_int),
+    "lbm_solver_state_bytes": ([_VP, C.POINTER(C.c_size_t)], C.c_int),
+    "lbm_solver_get_state": ([_VP, _VP, C.c_size_t], C.c_int),
+    "lbm_solver_set_state": ([_VP, _VP, C.c_size_t], C.c_int),
+    "lbm_solver_run_to_residual": ([_VP, C.c_double, C.c_int64, C.c_int32,
+                                    C.POINTER(C.c_int64), _DP], C.c_int),
+    "lbm_solver_stats": ([_VP, C.POINTER(lbm_stats)], C.c_int),
+    "lbm_solver_wall_mass": ([_VP, _DP], C.c_int),
+}
+
+
+def load() -> C.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                              "(run __graft_entry__.build())")
+        lib = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def lbm_last_error() -> str:
+    buf = C.create_string_buffer(512)
+    load().lbm_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+last_error = lbm_last_error
+
+
+def _check(status: int, where: str, ok=(LBM_OK,)) -> int:
+    if status not in ok:
+        raise LBMError(status, where, last_error())
+    return status
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+# ---- functions with the C names ------------------------------------------------
+
+def lbm_status_string(st: int) -> str:
+    return load().lbm_status_string(st).decode()
+
+
+def lbm_version():
+    a, b = C.c_int(), C.c_int()
+    load().lbm_version(C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def lbm_lattice_create(kind: int):
+    h = _VP()
+    _check(load().lbm_lattice_create(kind, C.byref(h)), "lbm_lattice_create")
+    return h
+
+
+def lbm_lattice_destroy(h) -> None:
+    load().lbm_lattice_destroy(h)
+
+
+def lbm_lattice_info(h):
+    Q, N, deg = C.c_int(), C.c_int(), C.c_int()
+    r = C.c_double()
+    _check(load().lbm_lattice_info(h, C.byref(Q), C.byref(r), C.byref(N), C.byref(deg)),
+           "lbm_lattice_info")
+    return Q.value, r.value, N.value, deg.value
+
+
+def lbm_lattice_tables(h):
+    Q = lbm_lattice_info(h)[0]
+    e = np.zeros((Q, 2), dtype=np.int8)
+    w = np.zeros(Q, dtype=np.float64)
+    _check(load().lbm_lattice_tables(h, e.ctypes.data_as(C.POINTER(C.c_int8)), _dp(w)),
+           "lbm_lattice_tables")
+    return e, w
+
+
+def lbm_lattice_verify(h, degree: int) -> float:
+    v = C.c_double()
+    _check(load().lbm_lattice_verify(h, degree, C.byref(v)), "lbm_lattice_verify")
+    return v.value
+
+
+def lbm_params_default() -> lbm_params:
+    p = lbm_params()
+    load().lbm_params_default(C.byref(p))
+    return p
+
+
+def lbm_solver_required_bytes(lat, p: lbm_params) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_solver_required_bytes(lat, C.byref(p), C.byref(n)),
+           "lbm_solver_required_bytes")
+    return n.value
+
+
+def lbm_solver_create(lat, p: lbm_params, stream: int = 0, device_mem: int = 0,
+                      device_bytes: int = 0):
+    h = _VP()
+    _check(load().lbm_solver_create(lat, C.byref(p), _VP(stream or None), _VP(device_mem or None),
+                                    device_bytes, C.byref(h)), "lbm_solver_create")
+    return h
+
+
+def lbm_solver_destroy(h) -> None:
+    load().lbm_solver_destroy(h)
+
+
+def lbm_solver_init(h) -> None:
+    _check(load().lbm_solver_init(h), "lbm_solver_init")
+
+
+def lbm_solver_init_fields(h, rho, ux=None, uy=None, T=None) -> None:
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+            for a in (rho, ux, uy, T)]
+    _check(load().lbm_solver_init_fields(h, *[_dp(a) for a in arrs]), "lbm_solver_init_fields")
+
+
+def lbm_solver_step(h, n: int) -> None:
+    _check(load().lbm_solver_step(h, int(n)), "lbm_solver_step")
+
+
+def lbm_solver_sync(h) -> None:
+    _check(load().lbm_solver_sync(h), "lbm_solver_sync")
+
+
+def lbm_solver_get_f(h, out: np.ndarray) -> np.ndarray:
+    _check(load().lbm_solver_get_f(h, _dp(out)), "lbm_solver_get_f")
+    return out
+
+
+def lbm_solver_set_f(h, f: np.ndarray) -> None:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(load().lbm_solver_set_f(h, _dp(f)), "lbm_solver_set_f")
+
+
+def lbm_solver_macros(h, rho=None, ux=None, uy=None, T=None) -> None:
+    _check(load().lbm_solver_macros(h, _dp(rho), _dp(ux), _dp(uy), _dp(T)), "lbm_solver_macros")
+
+
+def lbm_solver_state_bytes(h) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_solver_state_bytes(h, C.byref(n)), "lbm_solver_state_bytes")
+    return n.value
+
+
+def lbm_solver_get_state(h) -> bytes:
+    n = lbm_solver_state_bytes(h)
+    buf = C.create_string_buffer(n)
+    _check(load().lbm_solver_get_state(h, buf, n), "lbm_solver_get_state")
+    return buf.raw
+
+
+def lbm_solver_set_state(h, data: bytes) -> None:
+    buf = C.create_string_buffer(data, len(data))
+    _check(load().lbm_solver_set_state(h, buf, len(data)), "lbm_solver_set_state")
+
+
+def lbm_solver_run_to_residual(h, tol: float, max_steps: int, check_every: int = 100):
+    steps = C.c_int64()
+    res = C.c_double()
+    st = _check(load().lbm_solver_run_to_residual(h, tol, int(max_steps), int(check_every),
+                                                  C.byref(steps), C.byref(res)),
+                "lbm_solver_run_to_residual", ok=(LBM_OK, LBM_ENOTCONVERGED))
+    return st, steps.value, res.value
+
+
+def lbm_solver_stats(h) -> lbm_stats:
+    s = lbm_stats()
+    _check(load().lbm_solver_stats(h, C.byref(s)), "lbm_solver_stats")
+    return s
+
+
+def lbm_solver_wall_mass(h, out: np.ndarray) -> np.ndarray:
+    _check(load().lbm_solver_wall_mass(h, _dp(out)), "lbm_solver_wall_mass")
+    return out
+
+
+# ---- convenience wrappers (still marshalling only) -----------------------------
+
+class Lattice:
+    def __init__(self, name: str):
+        self.name = name
+        self.h = lbm_lattice_create(LATTICE_KIND[name])
+        self.Q, self.r, self.ghost_depth, self.degree = lbm_lattice_info(self.h)
+        self.e, self.w = lbm_lattice_tables(self.h)
+
+    def verify(self, degree: int) -> float:
+        return lbm_lattice_verify(self.h, degree)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            lbm_lattice_destroy(self.h)
+            self.h = None
+
+
+@dataclass
+class Config:
+    lattice: str = "D2Q25"
+    Nx: int = 1
+    Ny: int = 64
+    eq_order: int = 2
+    thermal: bool = False
+    Kn: float = 0.1
+    tau: float = 0.0
+    mu_exp: float = 1.0
+    u_wall: tuple = (-0.1, 0.1)
+    T_wall: tuple = (1.0, 1.0)
+    precision: str = "fp64"
+    kernel: int = LBM_KERNEL_AUTO
+    rho0: float = 1.0
+    noise_amp: float = 0.0
+    seed: int = 7
+
+    def params(self) -> lbm_params:
+        p = lbm_params_default()
+        p.Nx, p.Ny, p.eq_order, p.thermal = self.Nx, self.Ny, self.eq_order, int(self.thermal)
+        p.Kn, p.tau, p.mu_exp = self.Kn, self.tau, self.mu_exp
+        p.u_wall[0], p.u_wall[1] = self.u_wall
+        p.T_wall[0], p.T_wall[1] = self.T_wall
+        p.precision, p.kernel = PRECISION[self.precision], self.kernel
+        p.rho0, p.noise_amp, p.seed = self.rho0, self.noise_amp, self.seed
+        return p
+
+
+class Solver:
+    """A solver whose device memory is a torch allocation on the current device
+    and whose work runs on torch's current CUDA stream."""
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        self.cfg = cfg
+        self.lat = Lattice(cfg.lattice)
+        self.p = cfg.params()
+        nbytes = lbm_solver_required_bytes(self.lat.h, self.p)
+        self.mem = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.mem.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = lbm_solver_create(self.lat.h, self.p, self.stream.cuda_stream, aligned, nbytes)
+        self.Q = self.lat.Q
+
+    def init(self):
+        lbm_solver_init(self.h)
+
+    def init_fields(self, rho, ux=None, uy=None, T=None):
+        lbm_solver_init_fields(self.h, rho, ux, uy, T)
+
+    def step(self, n: int):
+        lbm_solver_step(self.h, n)
+
+    def sync(self):
+        lbm_solver_sync(self.h)
+
+    def get_f(self) -> np.ndarray:
+        out = np.empty((self.Q, self.cfg.Ny, self.cfg.Nx), dtype=np.float64)
+        return lbm_solver_get_f(self.h, out)
+
+    def set_f(self, f: np.ndarray):
+        lbm_solver_set_f(self.h, f)
+
+    def macros(self):
+        shp = (self.cfg.Ny, self.cfg.Nx)
+        out = [np.empty(shp) for _ in range(4)]
+        lbm_solver_macros(self.h, *out)
+        return tuple(out)
+
+    def wall_mass(self) -> np.ndarray:
+        return lbm_solver_wall_mass(self.h, np.empty((2, self.cfg.Nx)))
+
+    def run_to_residual(self, tol, max_steps, check_every=100):
+        return lbm_solver_run_to_residual(self.h, tol, max_steps, check_every)
+
+    def stats(self) -> lbm_stats:
+        return lbm_solver_stats(self.h)
+
+    def get_state(self) -> bytes:
+        return lbm_solver_get_state(self.h)
+
+    def set_state(self, data: bytes):
+        lbm_solver_set_state(self.h, data)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,114 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/lbm.h declares, and its host-side parts (lattice solver, parameter
+checks, memory sizing) agree with the oracle and the paper."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lattice as olat
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import __graft_entry__ as ge
+    ge.build_library()
+    from paper_1209_5201_gb300 import lbm as m
+    m.load()
+    return m
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lbm):
+    lib = lbm.load()
+    names = declared_symbols()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_symbol(lbm):
+    for n in declared_symbols():
+        assert hasattr(lbm, n), n
+
+
+@pytest.mark.parametrize("name,kind", [("D2Q17", 17), ("D2Q25", 25), ("D2Q25b", 26),
+                                       ("D2Q37", 37)])
+def test_library_lattice_matches_oracle(lbm, name, kind):
+    # two independent derivations: the oracle's Newton / closed form in numpy and
+    # the library's determinant root search in long double
+    h = lbm.lbm_lattice_create(kind)
+    try:
+        Q, r, N, deg = lbm.lbm_lattice_info(h)
+        e, w = lbm.lbm_lattice_tables(h)
+        ol = olat.get(name)
+        assert Q == ol.Q and N == 3
+        # the oracle solves in float64, the library in long double: 1e-14 relative
+        assert abs(r - ol.r) < 1e-14 * r
+        ow = {tuple(v): x for v, x in zip(ol.e.tolist(), ol.w)}
+        assert set(map(tuple, e.tolist())) == set(ow)
+        for v, x in zip(e.tolist(), w):
+            assert abs(x - ow[tuple(v)]) < 1e-14 * x
+        assert lbm.lbm_lattice_verify(h, deg) < 1e-12
+        assert lbm.lbm_lattice_verify(h, deg + 1) > 1e-3
+    finally:
+        lbm.lbm_lattice_destroy(h)
+
+
+@pytest.mark.parametrize("kind", [17, 25, 37])
+def test_library_velocity_order_is_paired(lbm, kind):
+    # rest first, then opposite pairs (kernels share even/odd equilibrium parts)
+    h = lbm.lbm_lattice_create(kind)
+    e, w = lbm.lbm_lattice_tables(h)
+    lbm.lbm_lattice_destroy(h)
+    assert tuple(e[0]) == (0, 0)
+    for a in range(1, len(e), 2):
+        assert tuple(e[a + 1]) == tuple(-e[a])
+        assert w[a] == w[a + 1]
+    assert np.abs(e[:, 1]).max() == 3
+
+
+def test_params_default_and_checks(lbm):
+    p = lbm.lbm_params_default()
+    assert (p.Nx, p.Ny, p.eq_order, p.precision) == (1, 64, 2, 0)
+    assert (p.u_wall[0], p.u_wall[1], p.seed) == (-0.1, 0.1, 7)
+    h = lbm.lbm_lattice_create(37)
+    try:
+        bad = lbm.lbm_params_default()
+        bad.Ny = 5                        # fewer rows than two ghost depths
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_solver_required_bytes(h, bad)
+        assert ei.value.status == lbm.LBM_EINVAL
+        bad = lbm.lbm_params_default()
+        bad.eq_order = 5
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_solver_required_bytes(h, bad)
+        bad = lbm.lbm_params_default()
+        bad.Kn = float("nan")
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_solver_required_bytes(h, bad)
+        # the large-grid workload: two FP32 state buffers of 37 x 2048 x pitch
+        p = lbm.lbm_params_default()
+        p.Nx, p.Ny, p.precision = 4096, 2048, lbm.LBM_FP32
+        n = lbm.lbm_solver_required_bytes(h, p)
+        assert 2 * 37 * 2048 * 4096 * 4 < n < 2 * 37 * 2048 * 4224 * 4 + 7 * 4096 * 2048 * 8
+    finally:
+        lbm.lbm_lattice_destroy(h)
+
+
+def test_status_strings(lbm):
+    assert lbm.lbm_status_string(0) == "ok"
+    assert lbm.lbm_status_string(4) == "not converged"
+    assert lbm.lbm_version()[0] == 0
