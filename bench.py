@@ -1,0 +1,292 @@
+"""Benchmark of the fused pull-stream + BGK + diffuse-wall step on one GB300.
+
+Workload: thermal Couette, D2Q37 lattice, 4th-order Hermite equilibrium,
+Nx = 4096 periodic columns x Ny = 2048 rows, walls -+0.3, T_w = 1, Kn = 0.05,
+rho = 1 + uniform noise +-1e-3 (SplitMix64 seed 7), FP32 storage and
+arithmetic.  A step is one full lattice update of all cells (one launch of the
+step kernel); the 2.5 GB state is far larger than L2, so no flush is needed.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(the reference arm of this project) on a bounded sample of the same workload.
+Under torchrun every rank runs its own independent replica of the workload
+(the path has no data exchange between domains); the slowest rank's time
+counts and `value` sums the cells of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(lattice="D2Q37", Nx=4096, Ny=2048, eq_order=4, thermal=True, Kn=0.05,
+                u_wall=(-0.3, 0.3), T_wall=(1.0, 1.0), noise_amp=1e-3, seed=7)
+BYTES_PER_LU = {"fp32": 8 * 37, "fp64": 16 * 37, "bf16dev": 4 * 37 + 8}
+DTYPE = {"fp32": "f32", "fp64": "f64", "bf16dev": "bf16-storage/f32"}
+
+
+def workload_name(prec: str, Nx: int, Ny: int) -> str:
+    return f"D2Q37 4th-order thermal Couette {Nx}x{Ny} {prec.upper()}"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(prec: str, budget_s: float = 12.0):
+    """The FP64 oracle (as it stands) on this host's cores, on a bounded sample
+    of the workload: the full 4096-column width with 128 rows (both walls),
+    for as many steps as fit in about budget_s seconds (at least one)."""
+    import numpy as np
+
+    import inputs
+    from oracle import oracle as orc
+    Nx, Ny = WORKLOAD["Nx"], 128
+    p = orc.Problem(lattice="D2Q37", Nx=Nx, Ny=Ny, eq_order=4, thermal=True, Kn=0.05,
+                    u_wall=(-0.3, 0.3), T_wall=(1.0, 1.0))
+    f = orc.init_fields(p, inputs.rho_field(Nx, Ny, 1e-3, seed=7))
+    t0 = time.perf_counter()
+    orc.run(p, f, 1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(50, int(budget_s / max(t1, 1e-6)) - 1))
+    t0 = time.perf_counter()
+    orc.run(p, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": Nx * Ny * steps / dt / 1e6, "unit": "MLUPS", "cores": orc.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle, {Nx}x{Ny} rows of the same Couette setup, {steps} steps "
+                      f"after 1 untimed step ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, one bounded sample step per timed step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import inputs
+    from oracle import oracle as orc
+    orc.build()
+    Nx, Ny = WORKLOAD["Nx"], 32
+    p = orc.Problem(lattice="D2Q37", Nx=Nx, Ny=Ny, eq_order=4, thermal=True, Kn=0.05,
+                    u_wall=(-0.3, 0.3), T_wall=(1.0, 1.0))
+    f = orc.init_fields(p, inputs.rho_field(Nx, Ny, 1e-3, seed=7))
+    orc.run(p, f, args.warmup)
+    t0 = time.perf_counter()
+    orc.run(p, f, args.steps)
+    dt = time.perf_counter() - t0
+    v = Nx * Ny * args.steps / dt / 1e6
+    sample = f"FP64 oracle, {Nx}x{Ny} rows of the same Couette setup per step"
+    print(json.dumps({
+        "impl": "reference", "metric": "D2Q37 MLUPS", "value": v, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.precision, WORKLOAD["Nx"], WORKLOAD["Ny"]),
+                   "sample_rows": Ny},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": orc.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
+    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--Nx", type=int, default=WORKLOAD["Nx"])
+    ap.add_argument("--Ny", type=int, default=WORKLOAD["Ny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1209_5201_gb300 import lbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    lbm.load()
+    cfg = lbm.Config(lattice="D2Q37", Nx=args.Nx, Ny=args.Ny, eq_order=4, thermal=True,
+                     Kn=WORKLOAD["Kn"], u_wall=WORKLOAD["u_wall"], T_wall=WORKLOAD["T_wall"],
+                     precision=args.precision, kernel=args.kernel,
+                     noise_amp=WORKLOAD["noise_amp"], seed=WORKLOAD["seed"])
+    stream = torch.cuda.Stream()
+    s = lbm.Solver(cfg, stream=stream)
+    cells = cfg.Nx * cfg.Ny
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # ---- device-resident throughput -------------------------------------------
+    s.init()
+    s.step(args.warmup)
+    s.sync()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers --------------------
+    # per job: init from a pinned host density field, the K steps, then the four
+    # macroscopic fields back into pinned host memory
+    rho_h = torch.from_numpy(inputs.rho_field(cfg.Nx, cfg.Ny, 1e-3, seed=7)).pin_memory()
+    outs = [torch.empty((cfg.Ny, cfg.Nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    barrier()
+    t0 = time.perf_counter()
+    lbm.lbm_solver_init_fields(s.h, rho_h.numpy())
+    s.step(args.steps)
+    lbm.lbm_solver_macros(s.h, *[o.numpy() for o in outs])
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": cells * 8 / args.steps,
+           "d2h_bytes_per_step": 4 * cells * 8 / args.steps}
+    s.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peaks()
+    bpl = BYTES_PER_LU[args.precision]
+    achieved = bpl * cells / (ms_step * 1e-3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if os.path.exists(tf):
+        try:
+            with open(tf) as fh:
+                d = json.load(fh)
+            key = f"{args.precision}:{args.kernel}:{cfg.Nx}x{cfg.Ny}"
+            traffic = d.get(key)
+        except Exception:
+            traffic = None
+    out = {
+        "metric": "D2Q37 MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": workload_name(args.precision, cfg.Nx, cfg.Ny), "lattice": "D2Q37",
+                   "Nx": cfg.Nx, "Ny": cfg.Ny, "eq_order": 4, "Kn": WORKLOAD["Kn"],
+                   "U_w": 0.3, "kernel": args.kernel,
+                   "l2": "inputs larger than L2 (state %.2f GB)" % (2 * cells * bpl / 2 / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} (copy burst)",
+                     "bytes_per_lu": bpl},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.precision)
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
