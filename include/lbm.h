@@ -194,6 +194,27 @@ typedef struct lbm_stats {
 /* Synchronous (one reduction over the state). */
 int lbm_solver_stats(lbm_solver *s, lbm_stats *st);
 
+/* Step-kernel selection.  LBM_KERNEL_DIRECT: one thread per cell, populations
+ * pulled straight from global memory.  LBM_KERNEL_STAGED: persistent tile
+ * kernel whose producer warp stages each velocity's shifted source window
+ * (tile plus the +-3-cell halo, rounded to 16 bytes in x) into shared memory
+ * with TMA; `variant` picks one of the compiled tile shapes, 0 <= variant <
+ * nvariants.  AUTO uses STAGED for Nx >= 32, else DIRECT.  Both compute the
+ * same step (Eq. (5) with Eq. (12)).  Errors: LBM_EINVAL. */
+int lbm_solver_set_kernel(lbm_solver *s, int32_t kernel, int32_t variant);
+/* Kernel in effect (AUTO resolved), its variant, and the number of variants. */
+int lbm_solver_kernel_info(lbm_solver *s, int32_t *kernel, int32_t *variant,
+                           int32_t *nvariants);
+/* Autotuner: time trial_steps steps of the direct kernel and of every staged
+ * variant on this solver's grid (CUDA events on the solver's stream), keep
+ * the fastest, and cache the choice per (lattice, precision, order, Nx and Ny
+ * rounded up to powers of two) for the process, and in the file named by the
+ * environment variable LBM_AUTOTUNE_CACHE when set.  Overwrites the state:
+ * on return the solver holds the lbm_solver_init state.  Synchronous.
+ * Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_solver_autotune(lbm_solver *s, int32_t trial_steps, int32_t *kernel,
+                        int32_t *variant, double *ms_per_step);
+
 /* Diffuse-wall incoming mass per ghost column (numerator of Eq. (12)) of the
  * current state: m_in[2][Nx] host FP64, bottom row then top row.  M_in(x) sums
  * the post-collision populations that stream into ghost column x through all

@@ -144,6 +144,24 @@ int dispatch_prec(int prec, F &&fn) {
     }
 }
 
+int effective_kernel(const SolverImpl &s) {
+    if (s.p.kernel != LBM_KERNEL_AUTO) return s.p.kernel;
+    return s.p.Nx >= 32 ? LBM_KERNEL_STAGED : LBM_KERNEL_DIRECT;
+}
+
+// Error flags the staged kernel raises when a bounded wait runs out.
+int check_device_error(SolverImpl &s) {
+    int flag = 0;
+    CU(cudaMemcpyAsync(&flag, s.derr, sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+    CU(cudaStreamSynchronize(s.stream));
+    if (flag) {
+        CU(cudaMemsetAsync(s.derr, 0, sizeof(int), s.stream));
+        set_error("a bounded device wait timed out in the step kernel");
+        return LBM_ETIMEOUT;
+    }
+    return LBM_OK;
+}
+
 int sum_rho(SolverImpl &s, double *out) {
     const int nb = reduction_blocks((long long)s.p.Nx * s.p.Ny);
     CU(dispatch_prec(s.p.precision, [&](auto P) { return Launch<decltype(P)::value>::mass_partials(s, s.red, nb); }));
@@ -168,6 +186,24 @@ int after_init(SolverImpl &s) {
 }
 
 }  // namespace
+
+int staged_variant_count(int precision) {
+    return dispatch_prec(precision, [&](auto P) { return Launch<decltype(P)::value>::staged_variants(); });
+}
+
+int dispatch_init_rest(SolverImpl &s) {
+    CU(dispatch_prec(s.p.precision, [&](auto P) { return Launch<decltype(P)::value>::init_rest(s); }));
+    return after_init(s);
+}
+
+int launch_step_variant(SolverImpl &s, int src, int dst, int kernel, int variant) {
+    return dispatch_prec(s.p.precision, [&](auto P) {
+        constexpr int PP = decltype(P)::value;
+        return kernel == LBM_KERNEL_STAGED ? Launch<PP>::step_staged(s, src, dst, variant)
+                                           : Launch<PP>::step(s, src, dst);
+    });
+}
+
 }  // namespace lbm
 
 using namespace lbm;
@@ -333,7 +369,24 @@ int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
     s.prev = (double *)q; q += lo.prev_bytes;
     s.red = (double *)q;
     s.red_elems = lo.red_bytes / 8;
+    s.derr = (int *)(s.red + 8 * 1024 + 48);
     s.cur = 0;
+    s.tm_key = -1;
+    s.variant = 0;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&s.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (s.sm_count < 1) s.sm_count = 1;
+        cudaError_t e = cudaMemsetAsync(s.derr, 0, sizeof(int), s.stream);
+        if (e != cudaSuccess) {
+            if (s.owns_mem) cudaFreeAsync(s.dmem, s.stream);
+            cudaFreeHost(s.pinned);
+            delete h;
+            set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+            return LBM_ECUDA;
+        }
+    }
     fill_consts(s.kd, s.L, s.p, s.pitch);
     fill_consts(s.kf, s.L, s.p, s.pitch);
     s.last_res = -1;
@@ -385,8 +438,9 @@ int lbm_solver_step(lbm_solver *h, int64_t n) {
     API_BEGIN
     if (!h || n < 0) { set_error("NULL solver or negative step count"); return LBM_EINVAL; }
     SolverImpl &s = h->s;
+    const int kern = effective_kernel(s);
     for (int64_t i = 0; i < n; ++i) {
-        CU(dispatch_prec(s.p.precision, [&](auto P) { return Launch<decltype(P)::value>::step(s, s.cur, s.cur ^ 1); }));
+        CU(launch_step_variant(s, s.cur, s.cur ^ 1, kern, s.variant));
         s.cur ^= 1;
         ++s.steps;
     }
@@ -397,7 +451,7 @@ int lbm_solver_step(lbm_solver *h, int64_t n) {
 int lbm_solver_sync(lbm_solver *h) {
     if (!h) { set_error("NULL solver"); return LBM_EINVAL; }
     CU(cudaStreamSynchronize(h->s.stream));
-    return LBM_OK;
+    return check_device_error(h->s);
 }
 
 int lbm_solver_get_f(lbm_solver *h, double *f) {
@@ -534,10 +588,11 @@ int lbm_solver_run_to_residual(lbm_solver *h, double tol, int64_t max_steps, int
     double best = INFINITY, r = INFINITY;
     int since_best = 0;
     int status = LBM_ENOTCONVERGED;
+    int rc = LBM_OK;
     while (done < max_steps) {
         int64_t k = check_every;
         if (done + k > max_steps) k = max_steps - done;
-        int rc = lbm_solver_step(h, k);
+        rc = lbm_solver_step(h, k);
         if (rc) return rc;
         done += k;
         CU(dispatch_prec(s.p.precision, [&](auto P) {
@@ -547,6 +602,7 @@ int lbm_solver_run_to_residual(lbm_solver *h, double tol, int64_t max_steps, int
         CU(launch_final_sum(s.stream, s.red, nb, 5, s.red + 8 * 1024));
         CU(cudaMemcpyAsync(s.pinned, s.red + 8 * 1024, 5 * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
         CU(cudaStreamSynchronize(s.stream));
+        if ((rc = check_device_error(s))) return rc;
         const double *v = s.pinned;
         if (v[4] > 0) { status = LBM_ENONFINITE; r = NAN; break; }
         r = std::sqrt(v[0]) / std::fmax(std::sqrt(v[1]), 1e-30);
@@ -594,6 +650,38 @@ int lbm_solver_wall_mass(lbm_solver *h, double *m_in) {
     CU(dispatch_prec(s.p.precision, [&](auto P) { return Launch<decltype(P)::value>::wall_mass(s, s.stage); }));
     CU(cudaMemcpyAsync(m_in, s.stage, 2 * (size_t)s.p.Nx * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
     CU(cudaStreamSynchronize(s.stream));
+    return LBM_OK;
+    API_END
+}
+
+int lbm_solver_set_kernel(lbm_solver *h, int32_t kernel, int32_t variant) {
+    if (!h) { set_error("NULL solver"); return LBM_EINVAL; }
+    SolverImpl &s = h->s;
+    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_STAGED) { set_error("bad kernel"); return LBM_EINVAL; }
+    if (variant < 0 || variant >= staged_variant_count(s.p.precision)) { set_error("bad variant"); return LBM_EINVAL; }
+    s.p.kernel = kernel;
+    s.variant = variant;
+    return LBM_OK;
+}
+
+int lbm_solver_kernel_info(lbm_solver *h, int32_t *kernel, int32_t *variant, int32_t *nvariants) {
+    if (!h) { set_error("NULL solver"); return LBM_EINVAL; }
+    if (kernel) *kernel = effective_kernel(h->s);
+    if (variant) *variant = h->s.variant;
+    if (nvariants) *nvariants = staged_variant_count(h->s.p.precision);
+    return LBM_OK;
+}
+
+int lbm_solver_autotune(lbm_solver *h, int32_t trial_steps, int32_t *best_kernel,
+                        int32_t *best_variant, double *best_ms) {
+    API_BEGIN
+    if (!h || trial_steps < 1) { set_error("bad argument"); return LBM_EINVAL; }
+    SolverImpl &s = h->s;
+    int rc = autotune_solver(s, trial_steps);
+    if (rc) return rc;
+    if (best_kernel) *best_kernel = s.p.kernel;
+    if (best_variant) *best_variant = s.variant;
+    if (best_ms) *best_ms = s.tuned_ms;
     return LBM_OK;
     API_END
 }

@@ -8,7 +8,9 @@ namespace lbm {
 
 template <int PREC>
 struct Launch {
-    static int step(SolverImpl &s, int src, int dst);
+    static int step(SolverImpl &s, int src, int dst);          // direct kernel
+    static int step_staged(SolverImpl &s, int src, int dst, int variant);
+    static int staged_variants();
     static int init_rest(SolverImpl &s);
     static int init_fields(SolverImpl &s, const double *rho, const double *ux,
                            const double *uy, const double *T);

@@ -3,6 +3,7 @@
 
 #include "k_aux.cuh"
 #include "k_step_direct.cuh"
+#include "k_step_staged.cuh"
 #include "launchers.h"
 
 namespace lbm {
@@ -44,6 +45,71 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst) {
     LBM_DISPATCH_Q(s.L.Q, (k_step_direct<QQ, PREC, BX><<<grid, BX, 0, s.stream>>>(
                                fin, fout, s.rho[src], s.rho[dst], k)));
     return (int)cudaGetLastError();
+}
+
+// ---- TMA-staged kernel variants (tile TX x TY, ring of STAGES, CPT cells per
+// consumer thread); the autotuner picks one per solver ------------------------
+template <int PREC> struct Variants;
+template <> struct Variants<LBM_FP32> {
+    static constexpr int n = 4;
+    static constexpr int v[n][4] = {{128, 2, 4, 1}, {128, 4, 2, 1}, {128, 4, 2, 2}, {64, 4, 4, 1}};
+};
+template <> struct Variants<LBM_FP64> {
+    static constexpr int n = 2;
+    static constexpr int v[n][4] = {{64, 2, 4, 1}, {64, 4, 2, 1}};
+};
+template <> struct Variants<LBM_BF16DEV> {
+    static constexpr int n = 2;
+    static constexpr int v[n][4] = {{128, 2, 4, 1}, {128, 4, 3, 1}};
+};
+
+template <int Q, int PREC, int TX, int TY, int ST, int CPT>
+int launch_staged(SolverImpl &s, int src, int dst) {
+    using Cfg = StagedCfg<Q, PREC, TX, TY, ST, CPT>;
+    using S = typename Store<PREC>::S;
+    auto kern = k_step_staged<Q, PREC, TX, TY, ST, CPT>;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static bool attr_set[64] = {false};
+    if (dev < 64 && !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Cfg::kSmem);
+        if (e != cudaSuccess) return (int)e;
+        attr_set[dev] = true;
+    }
+    if (encode_tensor_maps(s, TX, TY)) return (int)cudaErrorInvalidValue;
+    const int ntiles = ((s.p.Nx + TX - 1) / TX) * ((s.p.Ny + TY - 1) / TY);
+    const int grid = ntiles < s.sm_count ? ntiles : s.sm_count;
+    const auto &k = Consts<PREC>::get(s);
+    kern<<<grid, Cfg::kThreads, Cfg::kSmem, s.stream>>>(
+        s.tm_f[src], s.tm_r[src], (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst],
+        s.derr, k);
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::staged_variants() { return Variants<PREC>::n; }
+
+template <int PREC>
+int Launch<PREC>::step_staged(SolverImpl &s, int src, int dst, int variant) {
+    using V = Variants<PREC>;
+    if (variant < 0 || variant >= V::n) return (int)cudaErrorInvalidValue;
+#define LBM_VARIANT_CASE(I)                                                              \
+    case I:                                                                              \
+        if constexpr (I < V::n) {                                                        \
+            LBM_DISPATCH_Q(s.L.Q, return (launch_staged<QQ, PREC, V::v[I][0], V::v[I][1],  \
+                                                        V::v[I][2], V::v[I][3]>(s, src, dst))); \
+        }                                                                                \
+        break;
+    switch (variant) {
+        LBM_VARIANT_CASE(0)
+        LBM_VARIANT_CASE(1)
+        LBM_VARIANT_CASE(2)
+        LBM_VARIANT_CASE(3)
+    default: break;
+    }
+#undef LBM_VARIANT_CASE
+    return (int)cudaErrorInvalidValue;
 }
 
 template <int PREC>

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <string>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
@@ -71,24 +72,26 @@ struct SolverImpl {
     double wall_in[2];
     KConsts<float> kf;
     KConsts<double> kd;
+    int sm_count;
+    int *derr;                // device error flags of the staged kernel
+    int variant;              // staged-kernel variant in use (see launchers)
+    long long tm_key;         // (TX, TY) the tensor maps were encoded for; -1 none
+    CUtensorMap tm_f[2];      // 3-D maps (x, y, a) of the two state buffers
+    CUtensorMap tm_r[2];      // 2-D maps of the BF16DEV density planes
+    double tuned_ms;          // step time of the autotuned choice
 };
+
+// Encode tm_f / tm_r for boxes of (TX + 2 kPadL) x TY (density: TY + 6 rows).
+int encode_tensor_maps(SolverImpl &s, int TX, int TY);
+int staged_variant_count(int precision);
+int launch_step_variant(SolverImpl &s, int src, int dst, int kernel, int variant);
+// Re-initialise the state as lbm_solver_init does (rest equilibrium + noise).
+int dispatch_init_rest(SolverImpl &s);
+// Pick the fastest step kernel / variant for this solver (autotune.cpp).
+int autotune_solver(SolverImpl &s, int trial_steps);
 
 size_t storage_elem_bytes(int precision);
 int padded_pitch(int Nx, int precision);
-
-// ---- kernel launchers (return cudaError_t as int) --------------------------
-int launch_step(SolverImpl &s, int src, int dst);
-int launch_init_rest(SolverImpl &s);
-int launch_init_fields(SolverImpl &s, const double *rho, const double *ux,
-                       const double *uy, const double *T);   // device planes
-int launch_plane_to_f64(SolverImpl &s, int a, double *out);   // logical plane
-int launch_plane_from_f64(SolverImpl &s, int a, const double *in);
-int launch_fill_pads(SolverImpl &s);                           // after set_f
-int launch_macros(SolverImpl &s, double *rho, double *ux, double *uy, double *T);
-int launch_wall_mass(SolverImpl &s, double *m_in);             // [2][Nx]
-// Reductions: out[0..] written to s.pinned after the stream reaches them.
-int launch_residual(SolverImpl &s, int thermal, double Tref);  // uses stage + prev
-int launch_mass(SolverImpl &s);                                // sum rho
 
 void set_error(const std::string &msg);
 

@@ -80,6 +80,11 @@ _SIGS = {
                                     C.POINTER(C.c_int64), _DP], C.c_int),
     "lbm_solver_stats": ([_VP, C.POINTER(lbm_stats)], C.c_int),
     "lbm_solver_wall_mass": ([_VP, _DP], C.c_int),
+    "lbm_solver_set_kernel": ([_VP, C.c_int32, C.c_int32], C.c_int),
+    "lbm_solver_kernel_info": ([_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                C.POINTER(C.c_int32)], C.c_int),
+    "lbm_solver_autotune": ([_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _DP],
+                            C.c_int),
 }
 
 
@@ -261,6 +266,25 @@ def lbm_solver_wall_mass(h, out: np.ndarray) -> np.ndarray:
     return out
 
 
+def lbm_solver_set_kernel(h, kernel: int, variant: int = 0) -> None:
+    _check(load().lbm_solver_set_kernel(h, int(kernel), int(variant)), "lbm_solver_set_kernel")
+
+
+def lbm_solver_kernel_info(h):
+    k, v, n = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().lbm_solver_kernel_info(h, C.byref(k), C.byref(v), C.byref(n)),
+           "lbm_solver_kernel_info")
+    return k.value, v.value, n.value
+
+
+def lbm_solver_autotune(h, trial_steps: int = 10):
+    k, v = C.c_int32(), C.c_int32()
+    ms = C.c_double()
+    _check(load().lbm_solver_autotune(h, int(trial_steps), C.byref(k), C.byref(v), C.byref(ms)),
+           "lbm_solver_autotune")
+    return k.value, v.value, ms.value
+
+
 # ---- convenience wrappers (still marshalling only) -----------------------------
 
 class Lattice:
@@ -349,6 +373,15 @@ class Solver:
         out = [np.empty(shp) for _ in range(4)]
         lbm_solver_macros(self.h, *out)
         return tuple(out)
+
+    def set_kernel(self, kernel: int, variant: int = 0):
+        lbm_solver_set_kernel(self.h, kernel, variant)
+
+    def kernel_info(self):
+        return lbm_solver_kernel_info(self.h)
+
+    def autotune(self, trial_steps: int = 10):
+        return lbm_solver_autotune(self.h, trial_steps)
 
     def wall_mass(self) -> np.ndarray:
         return lbm_solver_wall_mass(self.h, np.empty((2, self.cfg.Nx)))
