@@ -63,7 +63,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -158,14 +158,18 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
-    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=-1,
+                    help="-1: autotune; 1: direct; 2: staged (with --variant)")
+    ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--Nx", type=int, default=WORKLOAD["Nx"])
     ap.add_argument("--Ny", type=int, default=WORKLOAD["Ny"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the per-variant timing diagnostic")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -190,11 +194,30 @@ def main():
     lbm.load()
     cfg = lbm.Config(lattice="D2Q37", Nx=args.Nx, Ny=args.Ny, eq_order=4, thermal=True,
                      Kn=WORKLOAD["Kn"], u_wall=WORKLOAD["u_wall"], T_wall=WORKLOAD["T_wall"],
-                     precision=args.precision, kernel=args.kernel,
+                     precision=args.precision, kernel=max(args.kernel, 0),
                      noise_amp=WORKLOAD["noise_amp"], seed=WORKLOAD["seed"])
     stream = torch.cuda.Stream()
     s = lbm.Solver(cfg, stream=stream)
     cells = cfg.Nx * cfg.Ny
+
+    # step time of every compiled kernel variant (diagnostic), then the choice
+    variants_ms = {}
+    s.init()
+    nvar = s.kernel_info()[2]
+    for kv in ([] if args.no_variants else [(1, 0)] + [(2, v) for v in range(nvar)]):
+        s.set_kernel(*kv)
+        s.step(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(20)
+        e1.record(stream)
+        e1.synchronize()
+        variants_ms["direct" if kv[0] == 1 else f"staged{kv[1]}"] = e0.elapsed_time(e1) / 20
+    if args.kernel < 0:
+        kern, var, _ = s.autotune(10)
+    else:
+        s.set_kernel(args.kernel, args.variant)
+        kern, var = args.kernel, args.variant
 
     def barrier():
         torch.cuda.synchronize()
@@ -258,7 +281,7 @@ def main():
         try:
             with open(tf) as fh:
                 d = json.load(fh)
-            key = f"{args.precision}:{args.kernel}:{cfg.Nx}x{cfg.Ny}"
+            key = f"{args.precision}:{kern}:{var}:{cfg.Nx}x{cfg.Ny}"
             traffic = d.get(key)
         except Exception:
             traffic = None
@@ -269,7 +292,7 @@ def main():
         "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": workload_name(args.precision, cfg.Nx, cfg.Ny), "lattice": "D2Q37",
                    "Nx": cfg.Nx, "Ny": cfg.Ny, "eq_order": 4, "Kn": WORKLOAD["Kn"],
-                   "U_w": 0.3, "kernel": args.kernel,
+                   "U_w": 0.3, "kernel": "direct" if kern == 1 else f"staged{var}",
                    "l2": "inputs larger than L2 (state %.2f GB)" % (2 * cells * bpl / 2 / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -279,6 +302,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
+        "variants_ms": variants_ms,
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.precision)

@@ -98,7 +98,10 @@ struct StagedCfg {
     static constexpr int kConsumers = TX * TY / CPT;
     static constexpr int kConsumerWarps = kConsumers / 32;
     static constexpr int kThreads = kConsumers + 32;
-    static constexpr int kSmem = 1024 + STAGES * kStageBytes + 2 * (TX + 6) * 8;
+    // 128 bytes of slack for aligning the dynamic base, 1 KB of barriers,
+    // the stage ring, and the two walls' incoming-mass sums
+    static constexpr int kSmem = 128 + 1024 + STAGES * kStageBytes + 2 * (TX + 6) * 8;
+    static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     static_assert(kConsumers % 32 == 0, "consumer threads must fill warps");
     static_assert(TX % 32 == 0, "tile width must be a multiple of 32 columns");
     static_assert(kW * (int)sizeof(S) % 16 == 0, "TMA rows must be 16-byte multiples");
