@@ -221,6 +221,92 @@ int lbm_solver_autotune(lbm_solver *s, int32_t trial_steps, int32_t *kernel,
  * N ghost layers (Sec. III).  Synchronous. */
 int lbm_solver_wall_mass(lbm_solver *s, double *m_in);
 
+/* ---- batched steady-state solves and the continuous-batching server ------
+ * Each request is one steady Couette solve on a single periodic column
+ * (Nx = 1) between the paper's two diffuse walls (Sec. IV set-up): its own
+ * lattice, height, Kn (or tau), wall speeds and temperatures, FP32 storage
+ * and arithmetic, FP64 wall-flux and residual reductions.  The solve starts
+ * from rest (rho = 1, u = 0, T = 1) and stops when the extrapolated distance
+ * to the steady state, res q / (1 - q) with res the relative change of u_x
+ * (and T - T_ref when thermal) over one check and q the ratio of successive
+ * residuals, is at most `tol`; checks run about four times per e-folding time
+ * of the slowest shear mode, 0.127 Ny r / Kn steps. */
+typedef struct lbm_request {
+    int32_t lattice;      /* LBM_LATTICE_*                                     */
+    int32_t Ny;           /* rows, 6 <= Ny <= 8192                             */
+    int32_t eq_order;     /* 2, 3 or 4                                         */
+    int32_t thermal;      /* 0: isothermal (T = 1 in the collision)            */
+    double Kn;            /* Knudsen number (Eq. (15)); or tau > 0             */
+    double tau;
+    double mu_exp;        /* mu = T^mu_exp                                     */
+    double u_wall[2];     /* bottom, top wall x-velocity                       */
+    double T_wall[2];     /* bottom, top wall temperature (thermal only)       */
+    double tol;           /* target distance to the steady state, e.g. 1e-5    */
+    int64_t max_steps;    /* give up after this many steps                     */
+    uint64_t tag;         /* caller's tag, returned in the result              */
+} lbm_request;
+
+typedef struct lbm_result {
+    uint64_t id, tag;
+    int32_t status;       /* LBM_OK, LBM_ENOTCONVERGED (max_steps or residual
+                             stagnation), LBM_ENONFINITE                       */
+    int32_t Ny;
+    int64_t steps;
+    double residual;      /* last relative change over one check              */
+    double err_est;       /* extrapolated distance to the steady state        */
+    double mass;          /* sum of rho over the column at the last check     */
+    double t_submit, t_admit, t_done;   /* seconds since server creation      */
+} lbm_result;
+
+typedef struct lbm_server_cfg {
+    size_t mem_budget_bytes; /* device pool for the requests' f-arrays        */
+    int32_t max_slots;       /* requests on the GPU at once (1..4096)          */
+    int32_t chunk_steps;     /* steps per chunk launch                         */
+    int32_t precision;       /* LBM_FP32                                       */
+    int32_t use_graph;       /* replay the chunk launch as a CUDA graph        */
+} lbm_server_cfg;
+
+typedef struct lbm_server_metrics {
+    int64_t submitted, completed, running, queued, chunks;
+    double p50_latency_s, p99_latency_s, mean_latency_s;  /* submit -> done  */
+    double solves_per_s;     /* completed / (last completion - first submit)  */
+    double mean_occupancy;   /* mean fraction of busy slots per chunk         */
+    size_t pool_bytes, pool_used_bytes;
+} lbm_server_metrics;
+
+typedef struct lbm_server lbm_server;
+
+/* 40 GB budget, 256 slots, 100-step chunks, FP32, CUDA graph on. */
+void lbm_server_cfg_default(lbm_server_cfg *cfg);
+/* Device bytes one request occupies while admitted (two f-arrays of Q x Ny
+ * floats plus two rows of previous-check fields, 256-byte granules). */
+int lbm_request_bytes(const lbm_request *req, size_t *bytes);
+/* Start a server: allocates the pool (cudaMallocAsync on `stream`), the slot
+ * table and a host worker thread that owns `stream`.  Errors: LBM_EINVAL,
+ * LBM_ENOMEM, LBM_ECUDA. */
+int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out);
+/* Queue a request (thread-safe, non-blocking); it is admitted as soon as a
+ * slot and pool memory are free, while other requests keep running.
+ * Errors: LBM_EINVAL (bad request), LBM_EBUDGET (larger than the budget). */
+int lbm_server_submit(lbm_server *srv, const lbm_request *req, uint64_t *id);
+/* Non-blocking: copy up to max finished results (oldest first) to out. */
+int lbm_server_poll(lbm_server *srv, lbm_result *out, int32_t max, int32_t *n);
+/* Copy a finished request's profiles (host FP64 arrays of Ny, any may be
+ * NULL) and release them.  Errors: LBM_EINVAL for an unknown / fetched id. */
+int lbm_server_fetch(lbm_server *srv, uint64_t id, double *rho, double *ux,
+                     double *uy, double *T);
+/* Block until every submitted request has finished, or timeout_s seconds.
+ * Errors: LBM_ETIMEOUT, or the worker's LBM_ECUDA. */
+int lbm_server_drain(lbm_server *srv, double timeout_s);
+/* Latency percentiles, throughput and occupancy so far. */
+int lbm_server_stats(lbm_server *srv, lbm_server_metrics *st);
+/* Stop the worker (running requests are abandoned) and free everything. */
+int lbm_server_destroy(lbm_server *srv);
+/* Batched solve: a server with `cfg`, all n requests submitted at once,
+ * drained (timeout_s), results written to out[i] for reqs[i]. */
+int lbm_batch_solve(const lbm_server_cfg *cfg, void *stream, const lbm_request *reqs,
+                    int32_t n, lbm_result *out, double timeout_s);
+
 #ifdef __cplusplus
 }
 #endif

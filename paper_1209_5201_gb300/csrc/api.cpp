@@ -93,39 +93,6 @@ void wall_equilibrium(const LatticeHost &L, int order, double uw, double Tw, dou
     }
 }
 
-template <class C>
-void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int pitch) {
-    std::memset(&k, 0, sizeof(k));
-    k.Nx = p.Nx;
-    k.Ny = p.Ny;
-    k.pitch = pitch;
-    k.plane = (long long)p.Ny * pitch;
-    k.thermal = p.thermal;
-    k.eq_order = p.eq_order;
-    k.const_tau = p.tau > 0;
-    k.mu_is_one = p.mu_exp == 1.0;
-    k.r = (C)L.r;
-    k.r2 = (C)(L.r * L.r);
-    k.K = (C)(std::sqrt(2.0 / M_PI) * p.Kn * L.r * p.Ny);
-    k.tau_lat = (C)(p.tau * L.r * p.Ny);
-    k.mu_m1 = (C)(p.mu_exp - 1.0);
-    for (int a = 0; a < L.Q; ++a) {
-        k.w[a] = (C)L.w[a];
-        k.wsh[L.shell[a]] = (C)L.w[a];
-    }
-    // Eq. (11)-(12): g^w_a / sum_{l<N} sum_{e.n>l} g^w = g^w_a / sum_{e.n>0} |e.n| g^w
-    for (int wall = 0; wall < 2; ++wall) {
-        double g[kMaxQ];
-        const double Tw = p.thermal ? p.T_wall[wall] : 1.0;
-        wall_equilibrium(L, p.eq_order, p.u_wall[wall], Tw, g);
-        const int nsgn = wall == 0 ? 1 : -1;
-        double den = 0;
-        for (int a = 0; a < L.Q; ++a)
-            if (nsgn * L.ey[a] > 0) den += nsgn * L.ey[a] * g[a];
-        for (int a = 0; a < L.Q; ++a) k.wcoef[wall][a] = nsgn * L.ey[a] > 0 ? g[a] / den : 0.0;
-    }
-}
-
 #define CU(call)                                                                   \
     do {                                                                           \
         cudaError_t e_ = (cudaError_t)(call);                                      \
@@ -186,6 +153,42 @@ int after_init(SolverImpl &s) {
 }
 
 }  // namespace
+
+template <class C>
+void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int pitch) {
+    std::memset(&k, 0, sizeof(k));
+    k.Nx = p.Nx;
+    k.Ny = p.Ny;
+    k.pitch = pitch;
+    k.plane = (long long)p.Ny * pitch;
+    k.thermal = p.thermal;
+    k.eq_order = p.eq_order;
+    k.const_tau = p.tau > 0;
+    k.mu_is_one = p.mu_exp == 1.0;
+    k.r = (C)L.r;
+    k.r2 = (C)(L.r * L.r);
+    k.K = (C)(std::sqrt(2.0 / M_PI) * p.Kn * L.r * p.Ny);
+    k.tau_lat = (C)(p.tau * L.r * p.Ny);
+    k.mu_m1 = (C)(p.mu_exp - 1.0);
+    for (int a = 0; a < L.Q; ++a) {
+        k.w[a] = (C)L.w[a];
+        k.wsh[L.shell[a]] = (C)L.w[a];
+    }
+    // Eq. (11)-(12): g^w_a / sum_{l<N} sum_{e.n>l} g^w = g^w_a / sum_{e.n>0} |e.n| g^w
+    for (int wall = 0; wall < 2; ++wall) {
+        double g[kMaxQ];
+        const double Tw = p.thermal ? p.T_wall[wall] : 1.0;
+        wall_equilibrium(L, p.eq_order, p.u_wall[wall], Tw, g);
+        const int nsgn = wall == 0 ? 1 : -1;
+        double den = 0;
+        for (int a = 0; a < L.Q; ++a)
+            if (nsgn * L.ey[a] > 0) den += nsgn * L.ey[a] * g[a];
+        for (int a = 0; a < L.Q; ++a) k.wcoef[wall][a] = nsgn * L.ey[a] > 0 ? g[a] / den : 0.0;
+    }
+}
+
+template void fill_consts<float>(KConsts<float> &, const LatticeHost &, const lbm_params &, int);
+template void fill_consts<double>(KConsts<double> &, const LatticeHost &, const lbm_params &, int);
 
 int staged_variant_count(int precision) {
     return dispatch_prec(precision, [&](auto P) { return Launch<decltype(P)::value>::staged_variants(); });

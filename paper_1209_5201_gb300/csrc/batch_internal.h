@@ -1,0 +1,50 @@
+// Slot table of the batched / serving path, shared by the chunk kernel and
+// the host runtime.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// States of a slot (SlotStatus::state).
+constexpr int kSlotIdle = 0;
+constexpr int kSlotRunning = 1;
+constexpr int kSlotConverged = 2;
+constexpr int kSlotNonFinite = 3;
+constexpr int kSlotMaxSteps = 4;
+constexpr int kSlotStagnated = 5;
+
+struct SlotDesc {
+    int Q;                    // 17, 25 or 37 (0: idle slot)
+    int Ny;
+    int cur;                  // buffer holding the current state (0 / 1)
+    int check_every;          // residual every check_every chunks
+    long long f_off;          // element offset of buffer 0 in the pool
+    long long prev_off;       // element offset of the previous-check u_x, T
+    double tol;               // target of the extrapolated distance to steady state
+    long long max_steps;
+    double T_ref;             // mean wall temperature
+    KConsts<float> k;         // per-instance constants (Nx = 1, pitch = 1)
+};
+
+struct SlotStatus {
+    long long steps;          // steps run since admission
+    double res;               // last residual (relative change over one check)
+    double res_prev;          // residual of the check before
+    double err_est;           // extrapolated distance to the steady state
+    double best_res;          // smallest residual so far
+    double mass;              // sum of rho (FP64) at the last check
+    int state;                // kSlot*
+    int checks;
+    int since_best;           // checks without a new smallest residual
+    int chunks;               // chunks run since admission
+};
+
+int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, float *pool,
+                       int nslots, int chunk);
+int launch_batch_init(cudaStream_t st, SlotDesc *desc, float *pool, const int *slots, int n,
+                      float rho0);
+int launch_batch_macros(cudaStream_t st, const SlotDesc *desc, const float *pool,
+                        const int *slots, const long long *out_off, double *out, int n);
+
+}  // namespace lbm

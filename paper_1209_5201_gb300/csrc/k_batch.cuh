@@ -1,0 +1,176 @@
+// Batched chunk kernel: many independent single-column Couette instances
+// (Nx = 1, each with its own lattice, height, Kn, wall speeds and wall
+// temperatures) advanced together, one CTA per slot, `chunk` time steps per
+// launch, then an FP64 steady-state residual per slot.
+//
+// With Nx = 1 the pull of Eq. (5) only shifts in y: f_in(j, a) =
+// f~*(j - e_ay, a).  Per step one warp sums the incoming mass of each wall
+// (numerator of Eq. (12)): lane l loads the l-th (velocity, row) term of the
+// wall's list, then a warp-shuffle FP64 reduction in a fixed lane order gives
+// M_in; every slot's arithmetic is independent of the slot index, the grid
+// and the other slots.
+#pragma once
+
+#include "batch_internal.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <int Q>
+struct WallTerms {
+    // incoming (velocity, row-from-wall) terms of the bottom wall; the top wall
+    // uses the mirrored velocity and row Ny-1-k
+    static constexpr int count() {
+        int n = 0;
+        for (int a = 0; a < Q; ++a) if (Lat<Q>::ey(a) < 0) n += -Lat<Q>::ey(a);
+        return n;
+    }
+};
+
+template <int Q>
+__device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict__ pool,
+                                           SlotStatus *__restrict__ st, int chunk,
+                                           double *s_min, int *s_term) {
+    using L = Lat<Q>;
+    const KConsts<float> &k = d.k;
+    const int Ny = d.Ny;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int NT = WallTerms<Q>::count();
+    static_assert(NT <= 32, "wall terms must fit a warp");
+
+    // term tables: bottom wall (velocity with e_y < 0, row k < |e_y|); the top
+    // wall's l-th term is velocity with e_y > 0 at row Ny - 1 - k
+    if (tid == 0) {
+        int n = 0, m = 0;
+        for (int a = 0; a < Q; ++a) {
+            for (int kk = 0; kk < -L::ey(a); ++kk) { s_term[n] = a; s_term[32 + n] = kk; ++n; }
+            for (int kk = 0; kk < L::ey(a); ++kk) { s_term[64 + m] = a; s_term[96 + m] = kk; ++m; }
+        }
+    }
+    __syncthreads();
+
+    float *buf0 = pool + d.f_off;
+    float *buf1 = buf0 + (long long)Q * Ny;
+    const float *src = d.cur ? buf1 : buf0;
+    float *dst = d.cur ? buf0 : buf1;
+
+    for (int step = 0; step < chunk; ++step) {
+        if (warp < 2) {
+            double v = 0.0;
+            if (lane < NT) {
+                const int a = s_term[64 * warp + lane];
+                const int kk = s_term[64 * warp + 32 + lane];
+                const int row = warp == 0 ? kk : Ny - 1 - kk;
+                v = (double)src[(long long)a * Ny + row];
+            }
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) s_min[warp] = v;
+        }
+        __syncthreads();
+        const double mb = s_min[0], mt = s_min[1];
+        for (int j = tid; j < Ny; j += nth) {
+            float f[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const int sj = j - L::ey(a);
+                if (sj < 0) f[a] = (float)(mb * k.wcoef[0][a]);
+                else if (sj >= Ny) f[a] = (float)(mt * k.wcoef[1][a]);
+                else f[a] = src[(long long)a * Ny + sj];
+            }
+            Collision<Q, float> col;
+            col.setup(f, k);
+            float o[Q];
+            o[0] = col.rest(f[0]);
+            PairLoop<1, Q>::run([&](auto ic) {
+                constexpr int A = decltype(ic)::value;
+                col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
+            });
+#pragma unroll
+            for (int a = 0; a < Q; ++a) dst[(long long)a * Ny + j] = o[a];
+        }
+        __syncthreads();
+        const float *t = src;
+        src = dst;
+        dst = (float *)t;
+    }
+
+    const int chunks = st->chunks + 1;     // read before thread 0 updates it
+    __syncthreads();
+    if (tid == 0) st->chunks = chunks;
+    if (chunks % d.check_every != 0) {
+        if (tid == 0) {
+            st->steps += chunk;
+            if (st->steps >= d.max_steps) st->state = kSlotMaxSteps;
+        }
+        return;
+    }
+
+    // residual over the slot's cells (Eq. (3) moments of the current state)
+    float *prev_u = (float *)(pool + d.prev_off);
+    float *prev_T = prev_u + Ny;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const double r = (double)k.r;
+    for (int j = tid; j < Ny; j += nth) {
+        double s0 = 0, sx = 0, sy = 0;
+        float f[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            f[a] = src[(long long)a * Ny + j];
+            s0 += f[a];
+            sx += L::ex(a) * (double)f[a];
+            sy += L::ey(a) * (double)f[a];
+        }
+        const double u = r * sx / s0, v = r * sy / s0;
+        double e = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const double cx = r * L::ex(a) - u, cy = r * L::ey(a) - v;
+            e += f[a] * (cx * cx + cy * cy);
+        }
+        const double T = e / (2.0 * s0);
+        const double du = u - prev_u[j], dT = T - prev_T[j], tr = T - d.T_ref;
+        acc[0] += du * du;
+        acc[1] += u * u;
+        acc[2] += dT * dT;
+        acc[3] += tr * tr;
+        acc[4] += s0;
+        if (!isfinite(u) || !isfinite(T)) acc[5] += 1.0;
+        prev_u[j] = (float)u;
+        prev_T[j] = (float)T;
+    }
+    __shared__ double red[32][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+    if (lane == 0)
+        for (int i = 0; i < 6; ++i) red[warp][i] = acc[i];
+    __syncthreads();
+    if (tid == 0) {
+        double tot[6] = {0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < (nth + 31) / 32; ++w)
+            for (int i = 0; i < 6; ++i) tot[i] += red[w][i];
+        SlotStatus &s = *st;
+        s.steps += chunk;
+        s.checks += 1;
+        s.mass = tot[4];
+        double res = sqrt(tot[0]) / fmax(sqrt(tot[1]), 1e-30);
+        if (k.thermal) res = fmax(res, sqrt(tot[2]) / fmax(sqrt(tot[3]), 1e-30));
+        // geometric extrapolation of the remaining change: with a per-check
+        // contraction q = res / res_prev < 1, the distance to the steady state
+        // is about res q / (1 - q)
+        const double q = s.res > 0 ? res / s.res : 1.0;
+        s.res_prev = s.res;
+        s.res = res;
+        s.err_est = (q < 0.999) ? res * q / (1.0 - q) : 1e30;
+        if (res < s.best_res) { s.best_res = res; s.since_best = 0; }
+        else s.since_best += 1;
+        if (tot[5] > 0 || !isfinite(res)) s.state = kSlotNonFinite;
+        else if (s.checks >= 3 && s.err_est <= d.tol) s.state = kSlotConverged;
+        else if (s.since_best >= 50) s.state = kSlotStagnated;
+        else if (s.steps >= d.max_steps) s.state = kSlotMaxSteps;
+    }
+}
+
+
+}  // namespace lbm

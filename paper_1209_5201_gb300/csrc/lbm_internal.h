@@ -49,6 +49,11 @@ struct KConsts {
     double wcoef[2][kMaxQ];   // g^w_a / D_w (0 unless a leaves the wall)
 };
 
+// Kernel constants of one solve (Eq. (4)-(5) factors, Eq. (11)-(12) wall
+// coefficients); defined in api.cpp.
+template <class C>
+void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int pitch);
+
 struct SolverImpl {
     LatticeHost L;
     lbm_params p;

@@ -1,0 +1,592 @@
+// Continuous-batching server of steady-state Couette solves (and the batched
+// solve built on it).
+//
+// Requests (one single-column Couette instance each: lattice, height, Kn,
+// wall speeds and temperatures, tolerance) queue on the host.  A worker
+// thread owns the GPU side: a device memory pool of the configured budget,
+// a slot table (SlotDesc / SlotStatus) and the chunk kernel.  Every loop it
+//   1. admits queued requests into idle slots while the pool has room for
+//      their two state buffers (first-fit allocator), initialises them;
+//   2. runs one chunk launch over all slots (a CUDA graph: kernel + status
+//      read-back), so admitted work overlaps with slots already running;
+//   3. retires slots whose status left "running": reads their Eq. (3)
+//      profiles back, frees their memory, records the latency.
+// The f-arrays of a request stay resident on the device from admission to
+// retirement.  A request too large for the whole budget is refused with
+// LBM_EBUDGET at submission.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "batch_internal.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int kMaxNy = 8192;
+constexpr long long kAlignElems = 64;        // 256-byte granularity (floats)
+
+struct Pending {
+    uint64_t id;
+    lbm_request req;
+    double t_submit;
+};
+
+struct SlotInfo {
+    bool busy = false;
+    uint64_t id = 0;
+    lbm_request req{};
+    double t_submit = 0, t_admit = 0;
+    long long off = 0, elems = 0;
+};
+
+struct Done {
+    lbm_result meta;
+    std::vector<double> fields;              // [4][Ny]: rho, u_x, u_y, T
+};
+
+long long request_elems(const lbm_request &r, int Q) {
+    long long e = 2LL * Q * r.Ny + 2LL * r.Ny;
+    return (e + kAlignElems - 1) / kAlignElems * kAlignElems;
+}
+
+int lattice_q(int kind) {
+    return kind == LBM_LATTICE_D2Q17 ? 17 : kind == LBM_LATTICE_D2Q37 ? 37 : 25;
+}
+
+}  // namespace
+
+struct ServerImpl {
+    lbm_server_cfg cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::chrono::steady_clock::time_point t0;
+    // device side
+    float *pool = nullptr;
+    long long pool_elems = 0;
+    SlotDesc *d_desc = nullptr;
+    SlotStatus *d_status = nullptr;
+    int *d_idx = nullptr;                    // slot lists for init / read-out
+    long long *d_off = nullptr;
+    double *d_out = nullptr;                 // read-out staging
+    long long out_elems = 0;
+    // host mirrors (pinned)
+    SlotDesc *h_desc = nullptr;
+    SlotStatus *h_status = nullptr;
+    int *h_idx = nullptr;
+    long long *h_off = nullptr;
+    double *h_out = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    // host state
+    std::map<long long, long long> free_list;        // offset -> length
+    long long used_elems = 0;
+    std::vector<SlotInfo> slots;
+    LatticeHost lat[4];                      // D2Q17, D2Q25, D2Q25B, D2Q37
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Pending> queue;
+    std::map<uint64_t, Done> done;
+    std::deque<uint64_t> unpolled;
+    std::vector<double> latencies;
+    uint64_t next_id = 1;
+    int64_t submitted = 0, completed = 0;
+    int running = 0;
+    int64_t chunks = 0;
+    double occupancy_sum = 0;
+    double t_first_submit = -1, t_last_done = 0;
+    std::atomic<bool> stop{false};
+    std::atomic<int> worker_error{0};
+    std::string worker_msg;
+    std::thread worker;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    const LatticeHost &lattice(int kind) const {
+        return lat[kind == 17 ? 0 : kind == 25 ? 1 : kind == 26 ? 2 : 3];
+    }
+
+    // ---- pool allocator (first fit, coalescing) ---------------------------------
+    long long alloc(long long n) {
+        for (auto it = free_list.begin(); it != free_list.end(); ++it) {
+            if (it->second >= n) {
+                long long off = it->first, len = it->second;
+                free_list.erase(it);
+                if (len > n) free_list[off + n] = len - n;
+                used_elems += n;
+                return off;
+            }
+        }
+        return -1;
+    }
+    void release(long long off, long long n) {
+        used_elems -= n;
+        auto it = free_list.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_list.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_list.erase(nx);
+        }
+        if (it != free_list.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_list.erase(it);
+            }
+        }
+    }
+
+    void fill_slot(int s, const Pending &pd, long long off) {
+        const lbm_request &r = pd.req;
+        const LatticeHost &L = lattice(r.lattice);
+        lbm_params p;
+        lbm_params_default(&p);
+        p.Nx = 1;
+        p.Ny = r.Ny;
+        p.eq_order = r.eq_order;
+        p.thermal = r.thermal;
+        p.Kn = r.Kn;
+        p.tau = r.tau;
+        p.mu_exp = r.mu_exp;
+        p.u_wall[0] = r.u_wall[0];
+        p.u_wall[1] = r.u_wall[1];
+        p.T_wall[0] = r.T_wall[0];
+        p.T_wall[1] = r.T_wall[1];
+        p.precision = LBM_FP32;
+        SlotDesc &d = h_desc[s];
+        std::memset(&d, 0, sizeof(d));
+        d.Q = L.Q;
+        d.Ny = r.Ny;
+        d.cur = 0;
+        // residual every ~quarter of the slowest e-folding time of the start-up
+        // (0.127 Ny r / Kn steps for the fundamental shear mode), in chunks
+        const double efold = r.tau > 0 ? r.Ny * r.Ny / (9.8696 * r.tau * L.r * r.Ny)
+                                       : 0.127 * r.Ny * L.r / r.Kn;
+        d.check_every = std::max(1, (int)std::lround(efold / (4.0 * cfg.chunk_steps)));
+        d.f_off = off;
+        d.prev_off = off + 2LL * L.Q * r.Ny;
+        d.tol = r.tol;
+        d.max_steps = r.max_steps;
+        d.T_ref = r.thermal ? 0.5 * (r.T_wall[0] + r.T_wall[1]) : 1.0;
+        fill_consts(d.k, L, p, 1);
+        SlotStatus &st = h_status[s];
+        std::memset(&st, 0, sizeof(st));
+        st.state = kSlotRunning;
+        st.best_res = 1e300;
+        SlotInfo &si = slots[s];
+        si.busy = true;
+        si.id = pd.id;
+        si.req = r;
+        si.t_submit = pd.t_submit;
+        si.t_admit = now();
+        si.off = off;
+        si.elems = request_elems(r, L.Q);
+    }
+
+    int fail(const char *what, cudaError_t e) {
+        worker_msg = std::string(what) + ": " + cudaGetErrorString(e);
+        worker_error = LBM_ECUDA;
+        return LBM_ECUDA;
+    }
+
+    // one loop of the worker; returns false when there is nothing to do
+    int loop_once(bool &idle) {
+        std::vector<int> admitted;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            for (int s = 0; s < (int)slots.size() && !queue.empty(); ++s) {
+                if (slots[s].busy) continue;
+                const Pending &pd = queue.front();
+                const long long n = request_elems(pd.req, lattice_q(pd.req.lattice));
+                const long long off = alloc(n);
+                if (off < 0) break;                  // wait for memory to free up
+                fill_slot(s, pd, off);
+                admitted.push_back(s);
+                queue.pop_front();
+                ++running;
+            }
+            idle = running == 0;
+        }
+        if (idle) return LBM_OK;
+        cudaError_t e;
+        if (!admitted.empty()) {
+            const int ns = (int)slots.size();
+            if ((e = cudaMemcpyAsync(d_desc, h_desc, sizeof(SlotDesc) * ns, cudaMemcpyHostToDevice, stream)))
+                return fail("upload slot table", e);
+            if ((e = cudaMemcpyAsync(d_status, h_status, sizeof(SlotStatus) * ns, cudaMemcpyHostToDevice, stream)))
+                return fail("upload slot status", e);
+            for (size_t i = 0; i < admitted.size(); ++i) h_idx[i] = admitted[i];
+            if ((e = cudaMemcpyAsync(d_idx, h_idx, sizeof(int) * admitted.size(), cudaMemcpyHostToDevice, stream)))
+                return fail("upload slot list", e);
+            if ((e = (cudaError_t)launch_batch_init(stream, d_desc, pool, d_idx, (int)admitted.size(), 1.0f)))
+                return fail("init kernel", e);
+        }
+        // chunk launch + status read-back
+        if (graph) {
+            if ((e = cudaGraphLaunch(graph, stream))) return fail("graph launch", e);
+        } else {
+            if ((e = (cudaError_t)launch_batch_chunk(stream, d_desc, d_status, pool, (int)slots.size(), cfg.chunk_steps)))
+                return fail("chunk kernel", e);
+            if ((e = cudaMemcpyAsync(h_status, d_status, sizeof(SlotStatus) * slots.size(), cudaMemcpyDeviceToHost, stream)))
+                return fail("status read-back", e);
+        }
+        if ((e = cudaStreamSynchronize(stream))) return fail("chunk", e);
+        ++chunks;
+        occupancy_sum += running;
+        // retire finished slots
+        std::vector<int> fin;
+        for (int s = 0; s < (int)slots.size(); ++s)
+            if (slots[s].busy && h_status[s].state != kSlotRunning) fin.push_back(s);
+        size_t pos = 0;
+        while (pos < fin.size()) {
+            // read-out in batches that fit the staging buffer
+            long long o = 0;
+            size_t n = 0;
+            while (pos + n < fin.size() && o + 4LL * slots[fin[pos + n]].req.Ny <= out_elems) {
+                h_idx[n] = fin[pos + n];
+                h_off[n] = o;
+                o += 4LL * slots[fin[pos + n]].req.Ny;
+                ++n;
+            }
+            if ((e = cudaMemcpyAsync(d_idx, h_idx, sizeof(int) * n, cudaMemcpyHostToDevice, stream)))
+                return fail("upload read-out list", e);
+            if ((e = cudaMemcpyAsync(d_off, h_off, sizeof(long long) * n, cudaMemcpyHostToDevice, stream)))
+                return fail("upload read-out offsets", e);
+            if ((e = (cudaError_t)launch_batch_macros(stream, d_desc, pool, d_idx, d_off, d_out, (int)n)))
+                return fail("read-out kernel", e);
+            if ((e = cudaMemcpyAsync(h_out, d_out, sizeof(double) * o, cudaMemcpyDeviceToHost, stream)))
+                return fail("read-out copy", e);
+            if ((e = cudaStreamSynchronize(stream))) return fail("read-out", e);
+            const double t = now();
+            std::unique_lock<std::mutex> lk(mu);
+            for (size_t i = 0; i < n; ++i) {
+                const int s = fin[pos + i];
+                SlotInfo &si = slots[s];
+                const SlotStatus &st = h_status[s];
+                Done d;
+                std::memset(&d.meta, 0, sizeof(d.meta));
+                d.meta.id = si.id;
+                d.meta.tag = si.req.tag;
+                d.meta.status = st.state == kSlotConverged ? LBM_OK
+                                : st.state == kSlotNonFinite ? LBM_ENONFINITE
+                                                             : LBM_ENOTCONVERGED;
+                d.meta.Ny = si.req.Ny;
+                d.meta.steps = st.steps;
+                d.meta.residual = st.res;
+                d.meta.err_est = st.err_est;
+                d.meta.mass = st.mass;
+                d.meta.t_submit = si.t_submit;
+                d.meta.t_admit = si.t_admit;
+                d.meta.t_done = t;
+                d.fields.assign(h_out + h_off[i], h_out + h_off[i] + 4LL * si.req.Ny);
+                latencies.push_back(t - si.t_submit);
+                t_last_done = t;
+                done.emplace(si.id, std::move(d));
+                unpolled.push_back(si.id);
+                release(si.off, si.elems);
+                si.busy = false;
+                h_desc[s].Q = 0;
+                h_status[s].state = kSlotIdle;
+                --running;
+                ++completed;
+            }
+            pos += n;
+        }
+        if (!fin.empty()) {
+            // idle the retired slots on the device too
+            if ((e = cudaMemcpyAsync(d_desc, h_desc, sizeof(SlotDesc) * slots.size(), cudaMemcpyHostToDevice, stream)))
+                return fail("upload slot table", e);
+            if ((e = cudaMemcpyAsync(d_status, h_status, sizeof(SlotStatus) * slots.size(), cudaMemcpyHostToDevice, stream)))
+                return fail("upload slot status", e);
+            cv_done.notify_all();
+        }
+        return LBM_OK;
+    }
+
+    void run() {
+        cudaSetDevice(device);
+        while (!stop) {
+            bool idle = false;
+            if (loop_once(idle)) {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_done.notify_all();
+                return;
+            }
+            if (idle) {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait_for(lk, std::chrono::milliseconds(2),
+                                 [&] { return stop || !queue.empty(); });
+            }
+        }
+    }
+};
+
+}  // namespace lbm
+
+struct lbm_server {
+    lbm::ServerImpl s;
+};
+
+using namespace lbm;
+
+extern "C" {
+
+void lbm_server_cfg_default(lbm_server_cfg *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->mem_budget_bytes = (size_t)40 << 30;
+    c->max_slots = 256;
+    c->chunk_steps = 100;
+    c->precision = LBM_FP32;
+    c->use_graph = 1;
+}
+
+static int check_request(const lbm_request *r) {
+    if (!r) { set_error("NULL request"); return LBM_EINVAL; }
+    if (r->lattice != LBM_LATTICE_D2Q17 && r->lattice != LBM_LATTICE_D2Q25 &&
+        r->lattice != LBM_LATTICE_D2Q25B && r->lattice != LBM_LATTICE_D2Q37) {
+        set_error("unknown lattice");
+        return LBM_EINVAL;
+    }
+    if (r->Ny < 6 || r->Ny > kMaxNy) { set_error("Ny must be in [6, 8192]"); return LBM_EINVAL; }
+    if (r->eq_order < 2 || r->eq_order > 4) { set_error("eq_order must be 2..4"); return LBM_EINVAL; }
+    if (!(r->Kn > 0) && !(r->tau > 0)) { set_error("need Kn > 0 or tau > 0"); return LBM_EINVAL; }
+    if (!std::isfinite(r->Kn) || !std::isfinite(r->tau) || !std::isfinite(r->mu_exp) ||
+        !std::isfinite(r->u_wall[0]) || !std::isfinite(r->u_wall[1]) ||
+        !std::isfinite(r->T_wall[0]) || !std::isfinite(r->T_wall[1]) || !(r->tol > 0) ||
+        !std::isfinite(r->tol)) {
+        set_error("non-finite or non-positive request parameter");
+        return LBM_EINVAL;
+    }
+    if (r->thermal && (r->T_wall[0] <= 0 || r->T_wall[1] <= 0)) { set_error("T_wall <= 0"); return LBM_EINVAL; }
+    if (r->max_steps < 1) { set_error("max_steps < 1"); return LBM_EINVAL; }
+    return LBM_OK;
+}
+
+int lbm_request_bytes(const lbm_request *r, size_t *bytes) {
+    int rc = check_request(r);
+    if (rc) return rc;
+    if (!bytes) { set_error("NULL bytes"); return LBM_EINVAL; }
+    *bytes = (size_t)request_elems(*r, lattice_q(r->lattice)) * sizeof(float);
+    return LBM_OK;
+}
+
+int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out) {
+    try {
+        if (!cfg || !out) { set_error("NULL argument"); return LBM_EINVAL; }
+        *out = nullptr;
+        if (cfg->max_slots < 1 || cfg->max_slots > 4096 || cfg->chunk_steps < 1 ||
+            cfg->mem_budget_bytes < 4096 || cfg->precision != LBM_FP32) {
+            set_error("bad server configuration (slots 1..4096, chunk >= 1, FP32)");
+            return LBM_EINVAL;
+        }
+        lbm_server *h = new lbm_server;
+        ServerImpl &S = h->s;
+        S.cfg = *cfg;
+        S.stream = (cudaStream_t)stream;
+        S.t0 = std::chrono::steady_clock::now();
+        cudaGetDevice(&S.device);
+        const int kinds[4] = {17, 25, 26, 37};
+        for (int i = 0; i < 4; ++i)
+            if (lattice_build(kinds[i], S.lat[i])) { delete h; set_error("lattice build"); return LBM_EINVAL; }
+        const int ns = cfg->max_slots;
+        S.slots.resize(ns);
+        S.pool_elems = (long long)(cfg->mem_budget_bytes / sizeof(float)) / kAlignElems * kAlignElems;
+        S.out_elems = 4LL * kMaxNy * std::min(ns, 64);
+        cudaError_t e = cudaSuccess;
+        auto ck = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+        ck(cudaMallocAsync((void **)&S.pool, (size_t)S.pool_elems * sizeof(float), S.stream));
+        ck(cudaMallocAsync((void **)&S.d_desc, sizeof(SlotDesc) * ns, S.stream));
+        ck(cudaMallocAsync((void **)&S.d_status, sizeof(SlotStatus) * ns, S.stream));
+        ck(cudaMallocAsync((void **)&S.d_idx, sizeof(int) * ns, S.stream));
+        ck(cudaMallocAsync((void **)&S.d_off, sizeof(long long) * ns, S.stream));
+        ck(cudaMallocAsync((void **)&S.d_out, sizeof(double) * S.out_elems, S.stream));
+        ck(cudaMallocHost((void **)&S.h_desc, sizeof(SlotDesc) * ns));
+        ck(cudaMallocHost((void **)&S.h_status, sizeof(SlotStatus) * ns));
+        ck(cudaMallocHost((void **)&S.h_idx, sizeof(int) * ns));
+        ck(cudaMallocHost((void **)&S.h_off, sizeof(long long) * ns));
+        ck(cudaMallocHost((void **)&S.h_out, sizeof(double) * S.out_elems));
+        if (e == cudaSuccess) {
+            std::memset(S.h_desc, 0, sizeof(SlotDesc) * ns);
+            std::memset(S.h_status, 0, sizeof(SlotStatus) * ns);
+            ck(cudaMemcpyAsync(S.d_desc, S.h_desc, sizeof(SlotDesc) * ns, cudaMemcpyHostToDevice, S.stream));
+            ck(cudaMemcpyAsync(S.d_status, S.h_status, sizeof(SlotStatus) * ns, cudaMemcpyHostToDevice, S.stream));
+            ck(cudaStreamSynchronize(S.stream));
+        }
+        if (e == cudaSuccess && cfg->use_graph) {
+            // capture: chunk kernel over every slot, then the status read-back
+            cudaStream_t cs;
+            ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g;
+            ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            ck((cudaError_t)launch_batch_chunk(cs, S.d_desc, S.d_status, S.pool, ns, cfg->chunk_steps));
+            ck(cudaMemcpyAsync(S.h_status, S.d_status, sizeof(SlotStatus) * ns, cudaMemcpyDeviceToHost, cs));
+            ck(cudaStreamEndCapture(cs, &g));
+            if (e == cudaSuccess) ck(cudaGraphInstantiate(&S.graph, g, 0));
+            cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+        }
+        if (e != cudaSuccess) {
+            const bool oom = e == cudaErrorMemoryAllocation;
+            set_error(std::string("server set-up: ") + cudaGetErrorString(e));
+            lbm_server_destroy(h);
+            return oom ? LBM_ENOMEM : LBM_ECUDA;
+        }
+        S.free_list[0] = S.pool_elems;
+        S.worker = std::thread([&S] { S.run(); });
+        *out = h;
+        return LBM_OK;
+    } catch (...) {
+        set_error("server creation failed");
+        return LBM_ENOMEM;
+    }
+}
+
+int lbm_server_submit(lbm_server *h, const lbm_request *r, uint64_t *id) {
+    if (!h) { set_error("NULL server"); return LBM_EINVAL; }
+    int rc = check_request(r);
+    if (rc) return rc;
+    ServerImpl &S = h->s;
+    if (S.worker_error) { set_error(S.worker_msg); return S.worker_error; }
+    const long long n = request_elems(*r, lattice_q(r->lattice));
+    if (n > S.pool_elems) { set_error("request exceeds the whole memory budget"); return LBM_EBUDGET; }
+    {
+        std::unique_lock<std::mutex> lk(S.mu);
+        Pending p{S.next_id++, *r, S.now()};
+        if (S.t_first_submit < 0) S.t_first_submit = p.t_submit;
+        if (id) *id = p.id;
+        S.queue.push_back(p);
+        ++S.submitted;
+    }
+    S.cv_work.notify_one();
+    return LBM_OK;
+}
+
+int lbm_server_poll(lbm_server *h, lbm_result *out, int32_t max, int32_t *n) {
+    if (!h || !n || (max > 0 && !out)) { set_error("bad argument"); return LBM_EINVAL; }
+    ServerImpl &S = h->s;
+    std::unique_lock<std::mutex> lk(S.mu);
+    int k = 0;
+    while (k < max && !S.unpolled.empty()) {
+        out[k++] = S.done.at(S.unpolled.front()).meta;
+        S.unpolled.pop_front();
+    }
+    *n = k;
+    if (S.worker_error) { set_error(S.worker_msg); return S.worker_error; }
+    return LBM_OK;
+}
+
+int lbm_server_fetch(lbm_server *h, uint64_t id, double *rho, double *ux, double *uy, double *T) {
+    if (!h) { set_error("NULL server"); return LBM_EINVAL; }
+    ServerImpl &S = h->s;
+    std::unique_lock<std::mutex> lk(S.mu);
+    auto it = S.done.find(id);
+    if (it == S.done.end()) { set_error("no finished result with this id"); return LBM_EINVAL; }
+    const int Ny = it->second.meta.Ny;
+    double *dst[4] = {rho, ux, uy, T};
+    for (int i = 0; i < 4; ++i)
+        if (dst[i]) std::memcpy(dst[i], it->second.fields.data() + (size_t)i * Ny, sizeof(double) * Ny);
+    S.done.erase(it);
+    return LBM_OK;
+}
+
+int lbm_server_drain(lbm_server *h, double timeout_s) {
+    if (!h) { set_error("NULL server"); return LBM_EINVAL; }
+    ServerImpl &S = h->s;
+    std::unique_lock<std::mutex> lk(S.mu);
+    const bool ok = S.cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
+        return S.completed == S.submitted || S.worker_error != 0;
+    });
+    if (S.worker_error) { set_error(S.worker_msg); return S.worker_error; }
+    if (!ok) { set_error("drain timed out"); return LBM_ETIMEOUT; }
+    return LBM_OK;
+}
+
+int lbm_server_stats(lbm_server *h, lbm_server_metrics *st) {
+    if (!h || !st) { set_error("NULL argument"); return LBM_EINVAL; }
+    ServerImpl &S = h->s;
+    std::unique_lock<std::mutex> lk(S.mu);
+    std::memset(st, 0, sizeof(*st));
+    st->submitted = S.submitted;
+    st->completed = S.completed;
+    st->running = S.running;
+    st->queued = (int64_t)S.queue.size();
+    st->chunks = S.chunks;
+    st->pool_bytes = (size_t)S.pool_elems * sizeof(float);
+    st->pool_used_bytes = (size_t)S.used_elems * sizeof(float);
+    st->mean_occupancy = S.chunks ? S.occupancy_sum / (S.chunks * (double)S.slots.size()) : 0.0;
+    if (!S.latencies.empty()) {
+        std::vector<double> l = S.latencies;
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double q) {
+            const double pos = q * (l.size() - 1);
+            const size_t i = (size_t)pos;
+            const double fr = pos - i;
+            return i + 1 < l.size() ? l[i] * (1 - fr) + l[i + 1] * fr : l[i];
+        };
+        st->p50_latency_s = pct(0.50);
+        st->p99_latency_s = pct(0.99);
+        double sum = 0;
+        for (double v : l) sum += v;
+        st->mean_latency_s = sum / l.size();
+        const double span = S.t_last_done - S.t_first_submit;
+        st->solves_per_s = span > 0 ? S.completed / span : 0.0;
+    }
+    return LBM_OK;
+}
+
+int lbm_server_destroy(lbm_server *h) {
+    if (!h) return LBM_OK;
+    ServerImpl &S = h->s;
+    S.stop = true;
+    S.cv_work.notify_all();
+    if (S.worker.joinable()) S.worker.join();
+    if (S.graph) cudaGraphExecDestroy(S.graph);
+    cudaStreamSynchronize(S.stream);
+    if (S.pool) cudaFreeAsync(S.pool, S.stream);
+    if (S.d_desc) cudaFreeAsync(S.d_desc, S.stream);
+    if (S.d_status) cudaFreeAsync(S.d_status, S.stream);
+    if (S.d_idx) cudaFreeAsync(S.d_idx, S.stream);
+    if (S.d_off) cudaFreeAsync(S.d_off, S.stream);
+    if (S.d_out) cudaFreeAsync(S.d_out, S.stream);
+    cudaStreamSynchronize(S.stream);
+    if (S.h_desc) cudaFreeHost(S.h_desc);
+    if (S.h_status) cudaFreeHost(S.h_status);
+    if (S.h_idx) cudaFreeHost(S.h_idx);
+    if (S.h_off) cudaFreeHost(S.h_off);
+    if (S.h_out) cudaFreeHost(S.h_out);
+    delete h;
+    return LBM_OK;
+}
+
+int lbm_batch_solve(const lbm_server_cfg *cfg, void *stream, const lbm_request *reqs, int32_t n,
+                    lbm_result *out, double timeout_s) {
+    if (!cfg || (n > 0 && (!reqs || !out)) || n < 0) { set_error("bad argument"); return LBM_EINVAL; }
+    lbm_server *h = nullptr;
+    int rc = lbm_server_create(cfg, stream, &h);
+    if (rc) return rc;
+    std::vector<uint64_t> ids(n);
+    for (int i = 0; i < n && !rc; ++i) rc = lbm_server_submit(h, &reqs[i], &ids[i]);
+    if (!rc) rc = lbm_server_drain(h, timeout_s);
+    if (!rc) {
+        std::map<uint64_t, int> pos;
+        for (int i = 0; i < n; ++i) pos[ids[i]] = i;
+        std::vector<lbm_result> tmp(n > 0 ? n : 1);
+        int32_t got = 0;
+        rc = lbm_server_poll(h, tmp.data(), n, &got);
+        for (int i = 0; i < got; ++i) out[pos[tmp[i].id]] = tmp[i];
+    }
+    lbm_server_destroy(h);
+    return rc;
+}
+
+}  // extern "C"

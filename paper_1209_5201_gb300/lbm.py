@@ -47,6 +47,33 @@ class lbm_stats(C.Structure):
                 ("wall_in", C.c_double * 2)]
 
 
+class lbm_request(C.Structure):
+    _fields_ = [("lattice", C.c_int32), ("Ny", C.c_int32), ("eq_order", C.c_int32),
+                ("thermal", C.c_int32), ("Kn", C.c_double), ("tau", C.c_double),
+                ("mu_exp", C.c_double), ("u_wall", C.c_double * 2), ("T_wall", C.c_double * 2),
+                ("tol", C.c_double), ("max_steps", C.c_int64), ("tag", C.c_uint64)]
+
+
+class lbm_result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("tag", C.c_uint64), ("status", C.c_int32),
+                ("Ny", C.c_int32), ("steps", C.c_int64), ("residual", C.c_double),
+                ("err_est", C.c_double), ("mass", C.c_double), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class lbm_server_cfg(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_slots", C.c_int32),
+                ("chunk_steps", C.c_int32), ("precision", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class lbm_server_metrics(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("running", C.c_int64),
+                ("queued", C.c_int64), ("chunks", C.c_int64), ("p50_latency_s", C.c_double),
+                ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double),
+                ("solves_per_s", C.c_double), ("mean_occupancy", C.c_double),
+                ("pool_bytes", C.c_size_t), ("pool_used_bytes", C.c_size_t)]
+
+
 _lib = None
 _VP = C.c_void_p
 _DP = C.POINTER(C.c_double)
@@ -85,6 +112,17 @@ _SIGS = {
                                 C.POINTER(C.c_int32)], C.c_int),
     "lbm_solver_autotune": ([_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _DP],
                             C.c_int),
+    "lbm_server_cfg_default": ([C.POINTER(lbm_server_cfg)], None),
+    "lbm_request_bytes": ([C.POINTER(lbm_request), C.POINTER(C.c_size_t)], C.c_int),
+    "lbm_server_create": ([C.POINTER(lbm_server_cfg), _VP, C.POINTER(_VP)], C.c_int),
+    "lbm_server_submit": ([_VP, C.POINTER(lbm_request), C.POINTER(C.c_uint64)], C.c_int),
+    "lbm_server_poll": ([_VP, C.POINTER(lbm_result), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+    "lbm_server_fetch": ([_VP, C.c_uint64, _DP, _DP, _DP, _DP], C.c_int),
+    "lbm_server_drain": ([_VP, C.c_double], C.c_int),
+    "lbm_server_stats": ([_VP, C.POINTER(lbm_server_metrics)], C.c_int),
+    "lbm_server_destroy": ([_VP], C.c_int),
+    "lbm_batch_solve": ([C.POINTER(lbm_server_cfg), _VP, C.POINTER(lbm_request), C.c_int32,
+                         C.POINTER(lbm_result), C.c_double], C.c_int),
 }
 
 
@@ -285,6 +323,85 @@ def lbm_solver_autotune(h, trial_steps: int = 10):
     return k.value, v.value, ms.value
 
 
+def lbm_server_cfg_default() -> lbm_server_cfg:
+    c = lbm_server_cfg()
+    load().lbm_server_cfg_default(C.byref(c))
+    return c
+
+
+def lbm_request_bytes(req: lbm_request) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_request_bytes(C.byref(req), C.byref(n)), "lbm_request_bytes")
+    return n.value
+
+
+def lbm_server_create(cfg: lbm_server_cfg, stream: int = 0):
+    h = _VP()
+    _check(load().lbm_server_create(C.byref(cfg), _VP(stream or None), C.byref(h)),
+           "lbm_server_create")
+    return h
+
+
+def lbm_server_submit(h, req: lbm_request) -> int:
+    i = C.c_uint64()
+    _check(load().lbm_server_submit(h, C.byref(req), C.byref(i)), "lbm_server_submit")
+    return i.value
+
+
+def lbm_server_poll(h, max_results: int = 1024):
+    buf = (lbm_result * max(1, max_results))()
+    n = C.c_int32()
+    _check(load().lbm_server_poll(h, buf, int(max_results), C.byref(n)), "lbm_server_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def lbm_server_fetch(h, rid: int, Ny: int):
+    out = [np.empty(Ny) for _ in range(4)]
+    _check(load().lbm_server_fetch(h, C.c_uint64(rid), *[_dp(a) for a in out]),
+           "lbm_server_fetch")
+    return tuple(out)
+
+
+def lbm_server_drain(h, timeout_s: float = 600.0) -> None:
+    _check(load().lbm_server_drain(h, float(timeout_s)), "lbm_server_drain")
+
+
+def lbm_server_stats(h) -> lbm_server_metrics:
+    m = lbm_server_metrics()
+    _check(load().lbm_server_stats(h, C.byref(m)), "lbm_server_stats")
+    return m
+
+
+def lbm_server_destroy(h) -> None:
+    load().lbm_server_destroy(h)
+
+
+def lbm_batch_solve(cfg: lbm_server_cfg, reqs, stream: int = 0, timeout_s: float = 600.0):
+    arr = (lbm_request * len(reqs))(*reqs)
+    out = (lbm_result * max(1, len(reqs)))()
+    _check(load().lbm_batch_solve(C.byref(cfg), _VP(stream or None), arr, len(reqs), out,
+                                  float(timeout_s)), "lbm_batch_solve")
+    return [out[i] for i in range(len(reqs))]
+
+
+def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
+                 tol: float = 1e-5, max_steps: int = 10_000_000, tag: int = 0,
+                 eq_order: int | None = None, thermal: bool | None = None,
+                 tau: float = 0.0) -> lbm_request:
+    """A Couette request: walls at -U_w (bottom) and +U_w (top), both at T_w."""
+    o, t = (4, True) if lattice == "D2Q37" else (2, False)
+    r = lbm_request()
+    r.lattice = LATTICE_KIND[lattice]
+    r.Ny = Ny
+    r.eq_order = o if eq_order is None else eq_order
+    r.thermal = int(t if thermal is None else thermal)
+    r.Kn, r.tau, r.mu_exp = Kn, tau, 1.0
+    r.u_wall[0], r.u_wall[1] = -U_w, U_w
+    r.T_wall[0] = r.T_wall[1] = T_w
+    r.tol, r.max_steps, r.tag = tol, max_steps, tag
+    return r
+
+
 # ---- convenience wrappers (still marshalling only) -----------------------------
 
 class Lattice:
@@ -330,6 +447,48 @@ class Config:
         p.precision, p.kernel = PRECISION[self.precision], self.kernel
         p.rho0, p.noise_amp, p.seed = self.rho0, self.noise_amp, self.seed
         return p
+
+
+class Server:
+    """Continuous-batching server on torch's current CUDA device; the worker
+    thread owns its own CUDA stream."""
+
+    def __init__(self, mem_budget_bytes: int = 40 << 30, max_slots: int = 256,
+                 chunk_steps: int = 100, use_graph: bool = True):
+        import torch
+        self.cfg = lbm_server_cfg_default()
+        self.cfg.mem_budget_bytes = int(mem_budget_bytes)
+        self.cfg.max_slots = int(max_slots)
+        self.cfg.chunk_steps = int(chunk_steps)
+        self.cfg.use_graph = int(use_graph)
+        self.stream = torch.cuda.Stream()
+        self.h = lbm_server_create(self.cfg, self.stream.cuda_stream)
+
+    def submit(self, req: lbm_request) -> int:
+        return lbm_server_submit(self.h, req)
+
+    def poll(self, max_results: int = 1024):
+        return lbm_server_poll(self.h, max_results)
+
+    def fetch(self, rid: int, Ny: int):
+        return lbm_server_fetch(self.h, rid, Ny)
+
+    def drain(self, timeout_s: float = 600.0):
+        lbm_server_drain(self.h, timeout_s)
+
+    def stats(self) -> lbm_server_metrics:
+        return lbm_server_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

@@ -112,3 +112,20 @@ def test_status_strings(lbm):
     assert lbm.lbm_status_string(0) == "ok"
     assert lbm.lbm_status_string(4) == "not converged"
     assert lbm.lbm_version()[0] == 0
+
+
+def test_server_request_validation(lbm):
+    r = lbm.make_request("D2Q37", 2048, 0.05, 0.3)
+    assert lbm.lbm_request_bytes(r) == (2 * 37 * 2048 + 2 * 2048) * 4
+    r = lbm.make_request("D2Q17", 33, 0.05, 0.1)
+    n = lbm.lbm_request_bytes(r)
+    assert n % 256 == 0 and n >= (2 * 17 * 33 + 2 * 33) * 4
+    for bad in (dict(Ny=5), dict(Ny=9000), dict(Kn=0.0), dict(tol=0.0)):
+        q = lbm.make_request("D2Q25", 64, 0.1, 0.1)
+        for k, v in bad.items():
+            setattr(q, k, v)
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_request_bytes(q)
+        assert ei.value.status == lbm.LBM_EINVAL
+    c = lbm.lbm_server_cfg_default()
+    assert (c.max_slots, c.chunk_steps, c.mem_budget_bytes) == (256, 100, 40 << 30)
