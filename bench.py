@@ -123,6 +123,130 @@ def cpu_baseline(prec: str, budget_s: float = 12.0):
                       f"after 1 untimed step ({dt:.1f} s)"}
 
 
+def _request(lbm, inst, tol):
+    return lbm.make_request(inst.lattice, inst.Ny, inst.Kn, inst.U_w, inst.T_w, tol=tol,
+                            max_steps=20_000_000)
+
+
+def _oracle_err(inst, ux, T, budget_cell_steps):
+    """L-inf error of a steady profile against the FP64 oracle's steady state,
+    or None when the oracle's run would exceed the CPU budget."""
+    import numpy as np
+    from oracle import oracle as orc
+    from oracle import lattice as olat
+    r = olat.get(inst.lattice).r
+    est = 14 * 0.127 * inst.Ny * r / inst.Kn * inst.Ny
+    if est > budget_cell_steps:
+        return None
+    p = orc.Problem(lattice=inst.lattice, Nx=1, Ny=inst.Ny, eq_order=inst.eq_order,
+                    thermal=inst.thermal, Kn=inst.Kn, u_wall=(-inst.U_w, inst.U_w),
+                    T_wall=(inst.T_w, inst.T_w))
+    f = orc.init_fields(p, np.ones((inst.Ny, 1)))
+    ok, _, _ = orc.run_to_residual(p, f, 1e-12, 50_000_000, 200)
+    _, oux, _, oT = orc.macros(p, f)
+    e = float(np.max(np.abs(ux - oux[:, 0])) / inst.U_w)
+    if inst.thermal:
+        e = max(e, float(np.max(np.abs(T - oT[:, 0]))))
+    return e
+
+
+def run_batched(lbm, n=256, seed=7, tol=1e-5, baseline_every=16, oracle_budget=3e7,
+                baseline_budget_s=1.5):
+    """Batched workload: n single-column instances in one slot table, all
+    submitted at t=0, solved to the extrapolated distance tol; against the
+    same instances run alone with the single-domain solver (one step launch
+    per step) for the same step counts, timed on every baseline_every-th
+    instance and extrapolated."""
+    import inputs
+    insts = inputs.batched_instances(n, seed=seed)
+    srv = lbm.Server(mem_budget_bytes=40 << 30, max_slots=256, chunk_steps=100)
+    t0 = time.perf_counter()
+    ids = [srv.submit(_request(lbm, it, tol)) for it in insts]
+    srv.drain(3600)
+    makespan = time.perf_counter() - t0
+    res = {r.id: r for r in srv.poll(n)}
+    prof = {i: srv.fetch(i, it.Ny) for i, it in zip(ids, insts)}
+    st = srv.stats()
+    srv.close()
+    ok = sum(res[i].status == 0 for i in ids)
+    # accuracy against the oracle on a CPU-budgeted sample
+    errs = {}
+    for k in range(0, n, baseline_every):
+        e = _oracle_err(insts[k], prof[ids[k]][1], prof[ids[k]][3], oracle_budget)
+        if e is not None:
+            errs[k] = e
+    # one launch per step, each instance alone, same step counts
+    base_t, base_n = 0.0, 0
+    import torch
+    for k in range(0, n, baseline_every):
+        it = insts[k]
+        cfg = lbm.Config(lattice=it.lattice, Nx=1, Ny=it.Ny, eq_order=it.eq_order,
+                         thermal=it.thermal, Kn=it.Kn, u_wall=(-it.U_w, it.U_w),
+                         T_wall=(it.T_w, it.T_w), precision="fp32", kernel=1)
+        sv = lbm.Solver(cfg)
+        sv.init()
+        sv.sync()
+        # time the instance's step count; beyond baseline_budget_s the rest
+        # is extrapolated at the measured per-step rate
+        need, done = res[ids[k]].steps, 0
+        t1 = time.perf_counter()
+        while done < need and time.perf_counter() - t1 < baseline_budget_s:
+            m = min(2000, need - done)
+            sv.step(m)
+            sv.sync()
+            done += m
+        el = time.perf_counter() - t1
+        base_t += el * need / max(done, 1)
+        base_n += 1
+        sv.close()
+    base_rate = base_n / base_t if base_t > 0 else None
+    return {"instances": n, "seed": seed, "tol": tol, "converged": ok,
+            "makespan_s": makespan, "solves_per_s": n / makespan,
+            "one_launch_per_solve_solves_per_s": base_rate,
+            "speedup_vs_one_launch_per_solve": (n / makespan) / base_rate if base_rate else None,
+            "baseline_sample": f"every {baseline_every}th instance ({base_n}), same step counts "
+                              f"(timed up to {baseline_budget_s} s each, rest extrapolated)",
+            "max_err_vs_oracle": max(errs.values()) if errs else None,
+            "oracle_sample": sorted(errs), "p50_latency_s": st.p50_latency_s,
+            "p99_latency_s": st.p99_latency_s, "mean_occupancy": st.mean_occupancy,
+            "total_steps": int(sum(res[i].steps for i in ids)),
+            "cell_steps": int(sum(res[i].steps * it.Ny for i, it in zip(ids, insts)))}
+
+
+def run_serving(lbm, n=10000, seed=11, rate=200.0, tol=1e-5, oracle_every=50,
+                oracle_budget=3e7):
+    """Serving workload: Poisson arrivals at `rate`/s submitted in real time
+    to a continuous-batching server (40 GB budget, 256 slots)."""
+    import inputs
+    reqs = inputs.serving_requests(n, seed=seed, rate=rate)
+    srv = lbm.Server(mem_budget_bytes=40 << 30, max_slots=256, chunk_steps=100)
+    t0 = time.perf_counter()
+    ids = []
+    for q in reqs:
+        dt = q.arrival - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(_request(lbm, q, tol)))
+    srv.drain(3600)
+    wall = time.perf_counter() - t0
+    res = {r.id: r for r in srv.poll(n)}
+    st = srv.stats()
+    errs = {}
+    for k in range(0, n, oracle_every):
+        rho, ux, uy, T = srv.fetch(ids[k], reqs[k].Ny)
+        e = _oracle_err(reqs[k], ux, T, oracle_budget)
+        if e is not None:
+            errs[k] = e
+    srv.close()
+    return {"requests": n, "seed": seed, "rate_per_s": rate, "tol": tol,
+            "converged": sum(res[i].status == 0 for i in ids),
+            "p50_latency_s": st.p50_latency_s, "p99_latency_s": st.p99_latency_s,
+            "mean_latency_s": st.mean_latency_s, "solves_per_s": st.solves_per_s,
+            "wall_s": wall, "mean_occupancy": st.mean_occupancy,
+            "max_err_vs_oracle": max(errs.values()) if errs else None,
+            "oracle_sample_size": len(errs)}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, one bounded sample step per timed step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -170,6 +294,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the per-variant timing diagnostic")
+    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "serving"],
+                    help="grid: the D2Q37 4096x2048 line (default, also runs the batched "
+                         "workload and a shortened serving run); batched / serving: only that")
+    ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -192,6 +320,12 @@ def main():
         dist.init_process_group("nccl")
 
     lbm.load()
+    if args.workload in ("batched", "serving"):
+        if rank == 0:
+            r = run_batched(lbm) if args.workload == "batched" else \
+                run_serving(lbm, n=args.serving_requests)
+            print(json.dumps({"workload": args.workload, **r}))
+        return 0
     cfg = lbm.Config(lattice="D2Q37", Nx=args.Nx, Ny=args.Ny, eq_order=4, thermal=True,
                      Kn=WORKLOAD["Kn"], u_wall=WORKLOAD["u_wall"], T_wall=WORKLOAD["T_wall"],
                      precision=args.precision, kernel=max(args.kernel, 0),
@@ -203,8 +337,8 @@ def main():
     # step time of every compiled kernel variant (diagnostic), then the choice
     variants_ms = {}
     s.init()
-    nvar = s.kernel_info()[2]
-    for kv in ([] if args.no_variants else [(1, 0)] + [(2, v) for v in range(nvar)]):
+    nd, ns = s.variant_count(1), s.variant_count(2)
+    for kv in ([] if args.no_variants else [(1, v) for v in range(nd)] + [(2, v) for v in range(ns)]):
         s.set_kernel(*kv)
         s.step(3)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -212,7 +346,7 @@ def main():
         s.step(20)
         e1.record(stream)
         e1.synchronize()
-        variants_ms["direct" if kv[0] == 1 else f"staged{kv[1]}"] = e0.elapsed_time(e1) / 20
+        variants_ms[("direct" if kv[0] == 1 else "staged") + str(kv[1])] = e0.elapsed_time(e1) / 20
     if args.kernel < 0:
         kern, var, _ = s.autotune(10)
     else:
@@ -292,7 +426,7 @@ def main():
         "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": workload_name(args.precision, cfg.Nx, cfg.Ny), "lattice": "D2Q37",
                    "Nx": cfg.Nx, "Ny": cfg.Ny, "eq_order": 4, "Kn": WORKLOAD["Kn"],
-                   "U_w": 0.3, "kernel": "direct" if kern == 1 else f"staged{var}",
+                   "U_w": 0.3, "kernel": ("direct" if kern == 1 else "staged") + str(var),
                    "l2": "inputs larger than L2 (state %.2f GB)" % (2 * cells * bpl / 2 / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -306,6 +440,9 @@ def main():
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.precision)
+    if not args.no_variants and world == 1:
+        out["batched"] = run_batched(lbm)
+        out["serving"] = run_serving(lbm, n=args.serving_requests)
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()

@@ -195,17 +195,23 @@ typedef struct lbm_stats {
 int lbm_solver_stats(lbm_solver *s, lbm_stats *st);
 
 /* Step-kernel selection.  LBM_KERNEL_DIRECT: one thread per cell, populations
- * pulled straight from global memory.  LBM_KERNEL_STAGED: persistent tile
+ * pulled straight from global memory; its variants differ in block width,
+ * register cap and store cache policy.  LBM_KERNEL_STAGED: persistent tile
  * kernel whose producer warp stages each velocity's shifted source window
  * (tile plus the +-3-cell halo, rounded to 16 bytes in x) into shared memory
  * with TMA; `variant` picks one of the compiled tile shapes, 0 <= variant <
- * nvariants.  AUTO uses STAGED for Nx >= 32, else DIRECT.  Both compute the
+ * nvariants.  AUTO uses DIRECT variant 0 until set_kernel or autotune picks
+ * another.  Both compute the
  * same step (Eq. (5) with Eq. (12)).  Errors: LBM_EINVAL. */
 int lbm_solver_set_kernel(lbm_solver *s, int32_t kernel, int32_t variant);
-/* Kernel in effect (AUTO resolved), its variant, and the number of variants. */
+/* Number of compiled variants of `kernel` (DIRECT or STAGED) for this
+ * solver's precision.  Errors: LBM_EINVAL. */
+int lbm_solver_variant_count(lbm_solver *s, int32_t kernel, int32_t *n);
+/* Kernel in effect (AUTO resolved), its variant, and the number of staged
+ * variants. */
 int lbm_solver_kernel_info(lbm_solver *s, int32_t *kernel, int32_t *variant,
                            int32_t *nvariants);
-/* Autotuner: time trial_steps steps of the direct kernel and of every staged
+/* Autotuner: time trial_steps steps of every direct and every staged
  * variant on this solver's grid (CUDA events on the solver's stream), keep
  * the fastest, and cache the choice per (lattice, precision, order, Nx and Ny
  * rounded up to powers of two) for the process, and in the file named by the

@@ -112,8 +112,9 @@ int dispatch_prec(int prec, F &&fn) {
 }
 
 int effective_kernel(const SolverImpl &s) {
-    if (s.p.kernel != LBM_KERNEL_AUTO) return s.p.kernel;
-    return s.p.Nx >= 32 ? LBM_KERNEL_STAGED : LBM_KERNEL_DIRECT;
+    // the direct kernel is the faster one on every measured workload; the
+    // autotuner can still choose a staged variant
+    return s.p.kernel != LBM_KERNEL_AUTO ? s.p.kernel : LBM_KERNEL_DIRECT;
 }
 
 // Error flags the staged kernel raises when a bounded wait runs out.
@@ -194,6 +195,10 @@ int staged_variant_count(int precision) {
     return dispatch_prec(precision, [&](auto P) { return Launch<decltype(P)::value>::staged_variants(); });
 }
 
+int direct_variant_count(int precision) {
+    return dispatch_prec(precision, [&](auto P) { return Launch<decltype(P)::value>::direct_variants(); });
+}
+
 int dispatch_init_rest(SolverImpl &s) {
     CU(dispatch_prec(s.p.precision, [&](auto P) { return Launch<decltype(P)::value>::init_rest(s); }));
     return after_init(s);
@@ -203,7 +208,7 @@ int launch_step_variant(SolverImpl &s, int src, int dst, int kernel, int variant
     return dispatch_prec(s.p.precision, [&](auto P) {
         constexpr int PP = decltype(P)::value;
         return kernel == LBM_KERNEL_STAGED ? Launch<PP>::step_staged(s, src, dst, variant)
-                                           : Launch<PP>::step(s, src, dst);
+                                           : Launch<PP>::step(s, src, dst, variant);
     });
 }
 
@@ -661,7 +666,9 @@ int lbm_solver_set_kernel(lbm_solver *h, int32_t kernel, int32_t variant) {
     if (!h) { set_error("NULL solver"); return LBM_EINVAL; }
     SolverImpl &s = h->s;
     if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_STAGED) { set_error("bad kernel"); return LBM_EINVAL; }
-    if (variant < 0 || variant >= staged_variant_count(s.p.precision)) { set_error("bad variant"); return LBM_EINVAL; }
+    const int nv = kernel == LBM_KERNEL_STAGED ? staged_variant_count(s.p.precision)
+                                               : direct_variant_count(s.p.precision);
+    if (variant < 0 || variant >= nv) { set_error("bad variant"); return LBM_EINVAL; }
     s.p.kernel = kernel;
     s.variant = variant;
     return LBM_OK;
@@ -672,6 +679,16 @@ int lbm_solver_kernel_info(lbm_solver *h, int32_t *kernel, int32_t *variant, int
     if (kernel) *kernel = effective_kernel(h->s);
     if (variant) *variant = h->s.variant;
     if (nvariants) *nvariants = staged_variant_count(h->s.p.precision);
+    return LBM_OK;
+}
+
+int lbm_solver_variant_count(lbm_solver *h, int32_t kernel, int32_t *n) {
+    if (!h || !n || (kernel != LBM_KERNEL_DIRECT && kernel != LBM_KERNEL_STAGED)) {
+        set_error("bad argument");
+        return LBM_EINVAL;
+    }
+    *n = kernel == LBM_KERNEL_STAGED ? staged_variant_count(h->s.p.precision)
+                                     : direct_variant_count(h->s.p.precision);
     return LBM_OK;
 }
 

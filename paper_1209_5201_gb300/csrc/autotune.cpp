@@ -1,6 +1,6 @@
 // Tile / block-shape autotuner of the step kernel.
 //
-// Candidates: the one-pass direct kernel and every TMA-staged variant compiled
+// Candidates: every variant of the one-pass direct kernel and of the TMA-staged one compiled
 // for the solver's precision.  Each runs `trial` steps after two warm-up
 // steps, timed with CUDA events on the solver's stream; the fastest wins.
 // Results are cached per (lattice, precision, order, Nx class, Ny class) for
@@ -109,8 +109,11 @@ int autotune_solver(SolverImpl &s, int trial) {
     if (rc) return rc;
     Choice best{LBM_KERNEL_DIRECT, 0, 1e30};
     double ms = 0;
-    if ((rc = time_candidate(s, LBM_KERNEL_DIRECT, 0, trial, &ms))) return rc;
-    best.ms = ms;
+    const int nd = direct_variant_count(s.p.precision);
+    for (int v = 0; v < nd; ++v) {
+        if ((rc = time_candidate(s, LBM_KERNEL_DIRECT, v, trial, &ms))) return rc;
+        if (ms < best.ms) best = Choice{LBM_KERNEL_DIRECT, v, ms};
+    }
     const int nv = staged_variant_count(s.p.precision);
     for (int v = 0; v < nv; ++v) {
         if ((rc = time_candidate(s, LBM_KERNEL_STAGED, v, trial, &ms))) return rc;

@@ -71,8 +71,18 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
     }
 }
 
-template <int Q, int PREC, int BX>
-__global__ void __launch_bounds__(BX)
+// Streaming (evict-first) store of one population.
+template <class S>
+__device__ __forceinline__ void store_cs(S *p, S v) { __stcs(p, v); }
+template <>
+__device__ __forceinline__ void store_cs<__nv_bfloat16>(__nv_bfloat16 *p, __nv_bfloat16 v) {
+    __stcs((unsigned short *)p, __bfloat16_as_ushort(v));
+}
+
+// BX threads per block (one row segment); MINB blocks per SM requested from
+// the register allocator; CS: streaming stores for the interior columns.
+template <int Q, int PREC, int BX, int MINB, bool CS>
+__global__ void __launch_bounds__(BX, MINB)
 k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
               typename Store<PREC>::S *__restrict__ fout, const float *__restrict__ rin,
               float *__restrict__ rout,
@@ -105,11 +115,14 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
     });
 
     const long long roff = (long long)j * k.pitch;
+    const bool image = x < kPadL || x >= k.Nx - kPadL;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         C v = o[a];
         if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
-        store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx, from_c<S>(v));
+        S *row = fout + (long long)a * k.plane + roff;
+        if (CS && !image) store_cs<S>(row + x + kPadL, from_c<S>(v));
+        else store_with_images<S>(row, x, k.Nx, from_c<S>(v));
     }
     if constexpr (Store<PREC>::dev) store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);
 }

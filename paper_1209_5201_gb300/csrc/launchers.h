@@ -8,7 +8,8 @@ namespace lbm {
 
 template <int PREC>
 struct Launch {
-    static int step(SolverImpl &s, int src, int dst);          // direct kernel
+    static int step(SolverImpl &s, int src, int dst, int variant);   // direct kernel
+    static int direct_variants();
     static int step_staged(SolverImpl &s, int src, int dst, int variant);
     static int staged_variants();
     static int init_rest(SolverImpl &s);

@@ -34,18 +34,44 @@ inline int aux_blocks(long long n) {
     default: return (int)cudaErrorInvalidValue;                 \
     }
 
-template <int PREC>
-int Launch<PREC>::step(SolverImpl &s, int src, int dst) {
+// ---- direct kernel variants {BX, MINB, CS} --------------------------------------
+struct DirectVariants {
+    static constexpr int n = 5;
+    static constexpr int v[n][3] = {{128, 0, 0}, {64, 0, 0}, {128, 8, 0}, {256, 0, 0}, {128, 0, 1}};
+};
+
+template <int Q, int PREC, int BX, int MINB, bool CS>
+int launch_direct(SolverImpl &s, int src, int dst) {
     using S = typename Store<PREC>::S;
     const auto &k = Consts<PREC>::get(s);
-    constexpr int BX = 128;
     dim3 grid((s.p.Nx + BX - 1) / BX, s.p.Ny);
-    const S *fin = (const S *)s.f[src];
-    S *fout = (S *)s.f[dst];
-    LBM_DISPATCH_Q(s.L.Q, (k_step_direct<QQ, PREC, BX><<<grid, BX, 0, s.stream>>>(
-                               fin, fout, s.rho[src], s.rho[dst], k)));
+    k_step_direct<Q, PREC, BX, MINB, CS><<<grid, BX, 0, s.stream>>>(
+        (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
     return (int)cudaGetLastError();
 }
+
+template <int PREC>
+int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
+    using V = DirectVariants;
+#define LBM_DIRECT_CASE(I)                                                                 \
+    case I:                                                                                \
+        LBM_DISPATCH_Q(s.L.Q, return (launch_direct<QQ, PREC, V::v[I][0], V::v[I][1],       \
+                                                    (V::v[I][2] != 0)>(s, src, dst)));     \
+        break;
+    switch (variant) {
+        LBM_DIRECT_CASE(0)
+        LBM_DIRECT_CASE(1)
+        LBM_DIRECT_CASE(2)
+        LBM_DIRECT_CASE(3)
+        LBM_DIRECT_CASE(4)
+    default: break;
+    }
+#undef LBM_DIRECT_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+template <int PREC>
+int Launch<PREC>::direct_variants() { return DirectVariants::n; }
 
 // ---- TMA-staged kernel variants (tile TX x TY, ring of STAGES, CPT cells per
 // consumer thread); the autotuner picks one per solver ------------------------

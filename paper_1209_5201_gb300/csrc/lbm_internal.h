@@ -89,6 +89,7 @@ struct SolverImpl {
 // Encode tm_f / tm_r for boxes of (TX + 2 kPadL) x TY (density: TY + 6 rows).
 int encode_tensor_maps(SolverImpl &s, int TX, int TY);
 int staged_variant_count(int precision);
+int direct_variant_count(int precision);
 int launch_step_variant(SolverImpl &s, int src, int dst, int kernel, int variant);
 // Re-initialise the state as lbm_solver_init does (rest equilibrium + noise).
 int dispatch_init_rest(SolverImpl &s);

@@ -192,6 +192,15 @@ struct ServerImpl {
         si.elems = request_elems(r, L.Q);
     }
 
+    cudaError_t upload_slot(int s) {
+        cudaError_t e = cudaMemcpyAsync(d_desc + s, h_desc + s, sizeof(SlotDesc),
+                                        cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_status + s, h_status + s, sizeof(SlotStatus),
+                                cudaMemcpyHostToDevice, stream);
+        return e;
+    }
+
     int fail(const char *what, cudaError_t e) {
         worker_msg = std::string(what) + ": " + cudaGetErrorString(e);
         worker_error = LBM_ECUDA;
@@ -219,11 +228,9 @@ struct ServerImpl {
         if (idle) return LBM_OK;
         cudaError_t e;
         if (!admitted.empty()) {
-            const int ns = (int)slots.size();
-            if ((e = cudaMemcpyAsync(d_desc, h_desc, sizeof(SlotDesc) * ns, cudaMemcpyHostToDevice, stream)))
-                return fail("upload slot table", e);
-            if ((e = cudaMemcpyAsync(d_status, h_status, sizeof(SlotStatus) * ns, cudaMemcpyHostToDevice, stream)))
-                return fail("upload slot status", e);
+            // only the admitted entries: running slots' buffer index lives on the device
+            for (int s : admitted)
+                if ((e = upload_slot(s))) return fail("upload slot", e);
             for (size_t i = 0; i < admitted.size(); ++i) h_idx[i] = admitted[i];
             if ((e = cudaMemcpyAsync(d_idx, h_idx, sizeof(int) * admitted.size(), cudaMemcpyHostToDevice, stream)))
                 return fail("upload slot list", e);
@@ -303,10 +310,8 @@ struct ServerImpl {
         }
         if (!fin.empty()) {
             // idle the retired slots on the device too
-            if ((e = cudaMemcpyAsync(d_desc, h_desc, sizeof(SlotDesc) * slots.size(), cudaMemcpyHostToDevice, stream)))
-                return fail("upload slot table", e);
-            if ((e = cudaMemcpyAsync(d_status, h_status, sizeof(SlotStatus) * slots.size(), cudaMemcpyHostToDevice, stream)))
-                return fail("upload slot status", e);
+            for (int s : fin)
+                if ((e = upload_slot(s))) return fail("upload slot", e);
             cv_done.notify_all();
         }
         return LBM_OK;

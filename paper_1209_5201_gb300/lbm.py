@@ -110,6 +110,7 @@ _SIGS = {
     "lbm_solver_set_kernel": ([_VP, C.c_int32, C.c_int32], C.c_int),
     "lbm_solver_kernel_info": ([_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                 C.POINTER(C.c_int32)], C.c_int),
+    "lbm_solver_variant_count": ([_VP, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "lbm_solver_autotune": ([_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _DP],
                             C.c_int),
     "lbm_server_cfg_default": ([C.POINTER(lbm_server_cfg)], None),
@@ -313,6 +314,12 @@ def lbm_solver_kernel_info(h):
     _check(load().lbm_solver_kernel_info(h, C.byref(k), C.byref(v), C.byref(n)),
            "lbm_solver_kernel_info")
     return k.value, v.value, n.value
+
+
+def lbm_solver_variant_count(h, kernel: int) -> int:
+    n = C.c_int32()
+    _check(load().lbm_solver_variant_count(h, int(kernel), C.byref(n)), "lbm_solver_variant_count")
+    return n.value
 
 
 def lbm_solver_autotune(h, trial_steps: int = 10):
@@ -538,6 +545,9 @@ class Solver:
 
     def kernel_info(self):
         return lbm_solver_kernel_info(self.h)
+
+    def variant_count(self, kernel: int) -> int:
+        return lbm_solver_variant_count(self.h, kernel)
 
     def autotune(self, trial_steps: int = 10):
         return lbm_solver_autotune(self.h, trial_steps)

@@ -1,0 +1,137 @@
+"""Batched chunk kernel and continuous-batching server, through the C ABI.
+
+Accuracy: each steady profile against the FP64 oracle's steady state of the
+same single-column problem (L-inf of u_x / U_w, and of T - 1 when thermal).
+Independence: a request's result is the same bit for bit alone and in a mix
+(each slot's arithmetic does not depend on the other slots, and checks fall on
+the same step counts).
+"""
+import time
+
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+MIX = [("D2Q17", 24, 0.2, 0.10, 1.0), ("D2Q25", 40, 0.1, 0.20, 1.0),
+       ("D2Q37", 32, 0.3, 0.30, 1.05), ("D2Q17", 64, 0.5, 0.05, 1.0),
+       ("D2Q25", 16, 1.0, 0.15, 1.0), ("D2Q37", 20, 0.08, 0.25, 0.95),
+       ("D2Q25b", 30, 0.2, 0.10, 1.0), ("D2Q37", 48, 0.5, 0.12, 1.0)]
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    return need_gpu()
+
+
+def oracle_steady(oracle, lat, Ny, Kn, Uw, Tw):
+    o, t = (4, True) if lat == "D2Q37" else (2, False)
+    p = oracle.Problem(lattice=lat, Nx=1, Ny=Ny, eq_order=o, thermal=t, Kn=Kn,
+                       u_wall=(-Uw, Uw), T_wall=(Tw, Tw))
+    f = oracle.init_fields(p, np.ones((Ny, 1)))
+    ok, _, _ = oracle.run_to_residual(p, f, 1e-13, 2_000_000, 100)
+    assert ok
+    _, ux, _, T = oracle.macros(p, f)
+    return ux[:, 0], T[:, 0]
+
+
+def solve(lbm, items, tol=1e-6, **srv):
+    s = lbm.Server(**{**dict(mem_budget_bytes=1 << 28, max_slots=16, chunk_steps=50), **srv})
+    ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=tol, tag=i))
+           for i, (lat, Ny, Kn, Uw, Tw) in enumerate(items)]
+    s.drain(300)
+    res = {r.id: r for r in s.poll(len(items))}
+    out = []
+    for rid, (lat, Ny, Kn, Uw, Tw) in zip(ids, items):
+        r = res[rid]
+        rho, ux, uy, T = s.fetch(rid, Ny)
+        out.append((r, rho, ux, T))
+    st = s.stats()
+    s.close()
+    return out, st
+
+
+def test_batch_matches_oracle_steady_states(lbm, oracle):
+    out, st = solve(lbm, MIX)
+    assert st.completed == len(MIX)
+    for (lat, Ny, Kn, Uw, Tw), (r, rho, ux, T) in zip(MIX, out):
+        assert r.status == lbm.LBM_OK, (lat, Ny, r.status, r.residual)
+        oux, oT = oracle_steady(oracle, lat, Ny, Kn, Uw, Tw)
+        err_u = np.max(np.abs(ux - oux)) / Uw
+        assert err_u < 2e-5, (lat, Ny, Kn, err_u)
+        if lat == "D2Q37":
+            assert np.max(np.abs(T - oT)) < 2e-5, (lat, Ny)
+        assert abs(r.mass - Ny) < 1e-4 * Ny          # rho = 1 start, wall conserves mass
+        assert np.max(np.abs(ux + ux[::-1])) < 1e-5 * Uw * 10
+
+
+def test_result_is_the_same_alone_and_in_the_mix(lbm):
+    mixed, _ = solve(lbm, MIX)
+    for k in (0, 2, 5):
+        alone, _ = solve(lbm, [MIX[k]])
+        a, b = alone[0], mixed[k]
+        assert a[0].steps == b[0].steps
+        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+
+
+def test_admission_under_a_small_memory_budget(lbm):
+    items = [("D2Q37", 64, 0.3, 0.1, 1.0)] * 5
+    one = lbm.lbm_request_bytes(lbm.make_request("D2Q37", 64, 0.3, 0.1))
+    s = lbm.Server(mem_budget_bytes=2 * one + 100, max_slots=8, chunk_steps=50)
+    ids = [s.submit(lbm.make_request(*it, tol=1e-6)) for it in items]
+    peak = 0
+    t0 = time.time()
+    while s.stats().completed < len(items) and time.time() - t0 < 120:
+        m = s.stats()
+        peak = max(peak, m.running)
+        assert m.pool_used_bytes <= m.pool_bytes
+        time.sleep(0.001)
+    s.drain(120)
+    assert s.stats().completed == 5 and peak <= 2
+    res = s.poll(10)
+    assert all(r.status == lbm.LBM_OK for r in res)
+    assert len({(r.steps) for r in res}) == 1          # identical problems, identical work
+    # a request larger than the whole budget is refused at once
+    with pytest.raises(lbm.LBMError) as ei:
+        s.submit(lbm.make_request("D2Q37", 4096, 0.1, 0.1))
+    assert ei.value.status == lbm.LBM_EBUDGET
+    s.close()
+
+
+def test_requests_admitted_while_others_run(lbm):
+    s = lbm.Server(mem_budget_bytes=1 << 26, max_slots=4, chunk_steps=50)
+    long_id = s.submit(lbm.make_request("D2Q37", 256, 0.05, 0.2, tol=1e-6))
+    time.sleep(0.05)
+    short = [s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-6)) for _ in range(6)]
+    s.drain(300)
+    res = {r.id: r for r in s.poll(16)}
+    assert all(res[i].status == lbm.LBM_OK for i in [long_id] + short)
+    # the short requests overtake the long one that arrived first
+    assert max(res[i].t_done for i in short) < res[long_id].t_done
+    st = s.stats()
+    assert st.p99_latency_s >= st.p50_latency_s > 0 and st.solves_per_s > 0
+    s.close()
+
+
+def test_invalid_requests_are_refused(lbm):
+    s = lbm.Server(mem_budget_bytes=1 << 24, max_slots=2, chunk_steps=20)
+    bad = lbm.make_request("D2Q25", 32, float("nan"), 0.1)
+    with pytest.raises(lbm.LBMError) as ei:
+        s.submit(bad)
+    assert ei.value.status == lbm.LBM_EINVAL
+    ok = s.submit(lbm.make_request("D2Q25", 32, 0.2, 0.1, tol=1e-6))
+    s.drain(60)
+    assert s.poll(4)[0].id == ok
+    s.close()
+
+
+def test_batch_solve_entry_point(lbm):
+    reqs = [lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=1e-6, tag=i)
+            for i, (lat, Ny, Kn, Uw, Tw) in enumerate(MIX[:4])]
+    cfg = lbm.lbm_server_cfg_default()
+    cfg.mem_budget_bytes, cfg.max_slots, cfg.chunk_steps = 1 << 26, 4, 50
+    out = lbm.lbm_batch_solve(cfg, reqs)
+    assert [r.tag for r in out] == [0, 1, 2, 3]
+    assert all(r.status == lbm.LBM_OK and r.steps > 0 for r in out)

@@ -21,9 +21,11 @@ def lbm():
 def kernels(lbm, precision):
     # (kernel, variant) pairs compiled for a precision
     s = lbm.Solver(lbm.Config(lattice="D2Q17", Nx=64, Ny=8, precision=precision))
-    n = s.kernel_info()[2]
+    nd = s.variant_count(lbm.LBM_KERNEL_DIRECT)
+    ns = s.variant_count(lbm.LBM_KERNEL_STAGED)
     s.close()
-    return [(lbm.LBM_KERNEL_DIRECT, 0)] + [(lbm.LBM_KERNEL_STAGED, v) for v in range(n)]
+    return [(lbm.LBM_KERNEL_DIRECT, v) for v in range(nd)] + \
+        [(lbm.LBM_KERNEL_STAGED, v) for v in range(ns)]
 
 
 def run_variant(lbm, oracle, lattice, Nx, Ny, precision, kv, nsteps, **kw):
