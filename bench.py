@@ -298,6 +298,8 @@ def main():
                     help="grid: the D2Q37 4096x2048 line (default, also runs the batched "
                          "workload and a shortened serving run); batched / serving: only that")
     ap.add_argument("--serving-requests", type=int, default=1000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="grid line only (skip the batched and serving runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -440,7 +442,7 @@ def main():
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.precision)
-    if not args.no_variants and world == 1:
+    if not args.no_extras and world == 1:
         out["batched"] = run_batched(lbm)
         out["serving"] = run_serving(lbm, n=args.serving_requests)
     print(json.dumps(out))

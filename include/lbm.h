@@ -233,10 +233,12 @@ int lbm_solver_wall_mass(lbm_solver *s, double *m_in);
  * lattice, height, Kn (or tau), wall speeds and temperatures, FP32 storage
  * and arithmetic, FP64 wall-flux and residual reductions.  The solve starts
  * from rest (rho = 1, u = 0, T = 1) and stops when the extrapolated distance
- * to the steady state, res q / (1 - q) with res the relative change of u_x
- * (and T - T_ref when thermal) over one check and q the ratio of successive
- * residuals, is at most `tol`; checks run about four times per e-folding time
- * of the slowest shear mode, 0.127 Ny r / Kn steps. */
+ * to the steady state, res q / (1 - q), is at most `tol`: res is the
+ * relative change over one check, max(||u_x - u_x'|| / ||u_x||, thermal:
+ * ||T - T'|| / ||T||), and q the ratio of successive residuals; checks run
+ * about four times per e-folding time of the slowest shear mode,
+ * 0.127 Ny r / Kn steps.  A request whose residual has not improved for 50
+ * checks (the FP32 round-off floor) ends with LBM_ENOTCONVERGED. */
 typedef struct lbm_request {
     int32_t lattice;      /* LBM_LATTICE_*                                     */
     int32_t Ny;           /* rows, 6 <= Ny <= 8192                             */

@@ -54,8 +54,8 @@ int check_params(const LatticeHost &L, const lbm_params &p) {
         set_error("need Nx >= 1 and Ny >= 2 * ghost depth");
         return LBM_EINVAL;
     }
-    if ((long long)p.Nx * p.Ny > (1LL << 31) - 1) {
-        set_error("grid too large (Nx * Ny must fit in 31 bits)");
+    if ((long long)L.Q * p.Ny * padded_pitch(p.Nx, p.precision) > (1LL << 31) - 1) {
+        set_error("grid too large (Q * Ny * padded row must fit in 31 bits)");
         return LBM_EINVAL;
     }
     if (p.eq_order < 2 || p.eq_order > 4) { set_error("eq_order must be 2, 3 or 4"); return LBM_EINVAL; }
@@ -174,6 +174,9 @@ void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int p
     for (int a = 0; a < L.Q; ++a) {
         k.w[a] = (C)L.w[a];
         k.wsh[L.shell[a]] = (C)L.w[a];
+        k.c2sh[L.shell[a]] = (C)(L.r * L.r * (L.ex[a] * L.ex[a] + L.ey[a] * L.ey[a]));
+        k.off_src[a] = (int)((long long)a * k.plane - (long long)L.ey[a] * pitch - L.ex[a]);
+        k.off_dst[a] = (int)((long long)a * k.plane);
     }
     // Eq. (11)-(12): g^w_a / sum_{l<N} sum_{e.n>l} g^w = g^w_a / sum_{e.n>0} |e.n| g^w
     for (int wall = 0; wall < 2; ++wall) {

@@ -19,11 +19,20 @@ struct SlotDesc {
     int Ny;
     int cur;                  // buffer holding the current state (0 / 1)
     int check_every;          // residual every check_every chunks
+    int chunk_steps;          // steps this slot runs per chunk launch
+    int pad0;
     long long f_off;          // element offset of buffer 0 in the pool
     long long prev_off;       // element offset of the previous-check u_x, T
     double tol;               // target of the extrapolated distance to steady state
     long long max_steps;
     double T_ref;             // mean wall temperature
+    // incoming terms of Eq. (12)'s numerator, built on the host: wall w (0
+    // bottom, 1 top), term l < nterm is velocity term_a[w][l] at distance
+    // term_row[w][l] from the wall
+    int nterm;
+    int pad1;
+    signed char term_a[2][32];
+    signed char term_row[2][32];
     KConsts<float> k;         // per-instance constants (Nx = 1, pitch = 1)
 };
 
@@ -40,11 +49,15 @@ struct SlotStatus {
     int chunks;               // chunks run since admission
 };
 
+int preload_batch_kernels();
+// dbg: 8 device ints; dbg[0] != 0 records the first invalid descriptor or
+// read-out offset a kernel met (and skipped).
 int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, float *pool,
-                       int nslots, int chunk);
+                       int nslots, int chunk, long long pool_elems, int *dbg);
 int launch_batch_init(cudaStream_t st, SlotDesc *desc, float *pool, const int *slots, int n,
-                      float rho0);
+                      float rho0, int nslots, long long pool_elems, int *dbg);
 int launch_batch_macros(cudaStream_t st, const SlotDesc *desc, const float *pool,
-                        const int *slots, const long long *out_off, double *out, int n);
+                        const int *slots, const long long *out_off, double *out, int n,
+                        int nslots, long long pool_elems, long long out_elems, int *dbg);
 
 }  // namespace lbm

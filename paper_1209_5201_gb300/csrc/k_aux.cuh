@@ -24,30 +24,13 @@ template <int Q, class C>
 __device__ __forceinline__ void equilibrium_all(C rho, C ux, C uy, C T, const KConsts<C> &k,
                                                 C (&o)[Q]) {
     // A collision with omega = 1 from f = 0 leaves exactly rho g^eq.
-    using L = Lat<Q>;
     Collision<Q, C> col;
     const C u2 = ux * ux + uy * uy;
-    const C th = T - C(1);
     col.omc = C(0);
     col.sx = k.r * ux;
     col.sy = k.r * uy;
     col.rho = rho;
-    col.A3 = k.eq_order >= 3 ? C(1) / C(6) : C(0);
-    col.A4 = k.eq_order >= 4 ? C(1) / C(24) : C(0);
-#pragma unroll
-    for (int s = 0; s < L::NSH; ++s) {
-        const C c2 = k.r2 * C(L::shell_e2(s));
-        C a0 = C(1) - C(0.5) * u2 + C(0.5) * th * (c2 - C(2));
-        C a1 = C(1), a2 = C(0.5);
-        if (k.eq_order >= 3) a1 += C(-0.5) * u2 + C(0.5) * th * (c2 - C(4));
-        if (k.eq_order >= 4) {
-            a0 += C(0.125) * u2 * u2 - C(0.25) * th * (c2 - C(4)) * u2 +
-                  C(0.125) * th * th * (c2 * c2 - C(8) * c2 + C(8));
-            a2 += C(-0.25) * u2 + C(0.25) * th * (c2 - C(6));
-        }
-        col.A0[s] = a0; col.A1[s] = a1; col.A2[s] = a2;
-        col.cw[s] = rho * k.wsh[s];
-    }
+    col.set_coefficients(u2, T - C(1), rho, k);
     o[0] = col.rest(C(0));
     PairLoop<1, Q>::run([&](auto ic) {
         constexpr int A = decltype(ic)::value;
@@ -144,40 +127,42 @@ __global__ void k_plane_from_f64(typename Store<PREC>::S *f, const float *rplane
 }
 
 // Eq. (3) fields of every cell of the stored state; T is the kinetic
-// temperature sum f |c - u|^2 / (2 rho).  Any output may be NULL.
+// temperature sum f |c - u|^2 / (2 rho).  Per-cell arithmetic in the storage's
+// compute type (FP32 or FP64), outputs FP64.  Any output may be NULL.
 template <int Q, int PREC>
 __global__ void k_macros(const typename Store<PREC>::S *f, const float *rplane,
                          const __grid_constant__ KConsts<typename Store<PREC>::C> k,
                          double *rho, double *ux, double *uy, double *T) {
     using L = Lat<Q>;
+    using C = typename Store<PREC>::C;
     const long long n = (long long)k.Nx * k.Ny;
-    const double r = (double)k.r;
+    const C r = k.r;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
         const long long ro = (long long)j * k.pitch + x + kPadL;
-        double fv[Q];
-        double s0 = 0, sx = 0, sy = 0;
+        C fv[Q];
+        C s0 = 0, sx = 0, sy = 0;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            auto v = to_c(f[(long long)a * k.plane + ro]);
+            C v = to_c(f[(long long)a * k.plane + ro]);
             if constexpr (Store<PREC>::dev) v += k.w[a] * rplane[ro];
-            fv[a] = (double)v;
-            s0 += fv[a];
-            sx += L::ex(a) * fv[a];
-            sy += L::ey(a) * fv[a];
+            fv[a] = v;
+            s0 += v;
+            sx += C(L::ex(a)) * v;
+            sy += C(L::ey(a)) * v;
         }
-        const double u = r * sx / s0, v = r * sy / s0;
-        double e = 0;
+        const C u = r * sx / s0, v = r * sy / s0;
+        C e = 0;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const double Cx = r * L::ex(a) - u, Cy = r * L::ey(a) - v;
-            e += fv[a] * (Cx * Cx + Cy * Cy);
+            const C cx = r * C(L::ex(a)) - u, cy = r * C(L::ey(a)) - v;
+            e += fv[a] * (cx * cx + cy * cy);
         }
-        if (rho) rho[c] = s0;
-        if (ux) ux[c] = u;
-        if (uy) uy[c] = v;
-        if (T) T[c] = e / (2.0 * s0);
+        if (rho) rho[c] = (double)s0;
+        if (ux) ux[c] = (double)u;
+        if (uy) uy[c] = (double)v;
+        if (T) T[c] = (double)(e / (C(2) * s0));
     }
 }
 

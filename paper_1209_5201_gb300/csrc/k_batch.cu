@@ -7,6 +7,33 @@ namespace lbm {
 
 constexpr int kBatchThreads = 256;
 
+// A slot descriptor is used only if its buffers lie inside the pool; a bad
+// one is recorded in dbg[0..7] (code, slot, Q, Ny, f_off, prev_off, chunk,
+// check interval) by the first CTA that meets it, and skipped.
+__device__ __forceinline__ bool desc_ok(const SlotDesc &d, long long pool_elems, int slot,
+                                        int code, int *dbg) {
+    const bool q_ok = d.Q == 17 || d.Q == 25 || d.Q == 37;
+    const long long need = 2LL * d.Q * d.Ny + 2LL * d.Ny;
+    bool terms_ok = d.nterm >= 1 && d.nterm <= 32;
+    for (int w = 0; w < 2 && terms_ok; ++w)
+        for (int l = 0; l < d.nterm; ++l)
+            terms_ok = terms_ok && d.term_a[w][l] >= 0 && d.term_a[w][l] < d.Q &&
+                       d.term_row[w][l] >= 0 && d.term_row[w][l] < 3;
+    const bool ok = q_ok && terms_ok && d.Ny >= 6 && d.Ny <= 8192 && d.f_off >= 0 &&
+                    d.f_off + need <= pool_elems && d.prev_off == d.f_off + 2LL * d.Q * d.Ny &&
+                    (d.cur == 0 || d.cur == 1) && d.chunk_steps >= 1 && d.check_every >= 1;
+    if (!ok && threadIdx.x == 0 && atomicCAS(dbg, 0, code) == 0) {
+        dbg[1] = slot;
+        dbg[2] = d.Q;
+        dbg[3] = d.Ny;
+        dbg[4] = (int)d.f_off;
+        dbg[5] = (int)d.prev_off;
+        dbg[6] = d.chunk_steps;
+        dbg[7] = d.check_every;
+    }
+    return ok;
+}
+
 // Stage the slot descriptor in shared memory (broadcast reads afterwards).
 __device__ __forceinline__ void load_desc(const SlotDesc *g, SlotDesc *s) {
     const int n = (int)(sizeof(SlotDesc) / sizeof(int));
@@ -17,21 +44,22 @@ __device__ __forceinline__ void load_desc(const SlotDesc *g, SlotDesc *s) {
 
 __global__ void __launch_bounds__(kBatchThreads, 2)
 k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
-              float *__restrict__ pool, int chunk) {
+              float *__restrict__ pool, int chunk, long long pool_elems, int *dbg) {
     __shared__ SlotDesc sd;
     __shared__ double s_min[2];
-    __shared__ int s_term[128];
     const int slot = blockIdx.x;
     load_desc(desc + slot, &sd);
     __syncthreads();
     if (sd.Q == 0 || status[slot].state != kSlotRunning) return;
+    if (!desc_ok(sd, pool_elems, slot, 1, dbg)) return;
     switch (sd.Q) {
-    case 17: batch_slot<17>(sd, pool, status + slot, chunk, s_min, s_term); break;
-    case 25: batch_slot<25>(sd, pool, status + slot, chunk, s_min, s_term); break;
-    case 37: batch_slot<37>(sd, pool, status + slot, chunk, s_min, s_term); break;
+    case 17: batch_slot<17>(sd, pool, status + slot, s_min); break;
+    case 25: batch_slot<25>(sd, pool, status + slot, s_min); break;
+    case 37: batch_slot<37>(sd, pool, status + slot, s_min); break;
     default: break;
     }
-    if (threadIdx.x == 0) desc[slot].cur = (sd.cur + chunk) & 1;
+    if (threadIdx.x == 0) desc[slot].cur = (sd.cur + sd.chunk_steps) & 1;
+    (void)chunk;
 }
 
 // Rest equilibrium f~* = rho0 w_a of newly admitted slots; previous-check
@@ -49,10 +77,17 @@ __device__ void init_slot(const SlotDesc &d, float *pool, float rho0) {
 }
 
 __global__ void k_batch_init(SlotDesc *__restrict__ desc, float *__restrict__ pool,
-                             const int *__restrict__ slots, float rho0) {
+                             const int *__restrict__ slots, float rho0, int nslots,
+                             long long pool_elems, int *dbg) {
     __shared__ SlotDesc sd;
-    load_desc(desc + slots[blockIdx.x], &sd);
+    const int slot = slots[blockIdx.x];
+    if (slot < 0 || slot >= nslots) {
+        if (threadIdx.x == 0 && atomicCAS(dbg, 0, 2) == 0) dbg[1] = slot;
+        return;
+    }
+    load_desc(desc + slot, &sd);
     __syncthreads();
+    if (!desc_ok(sd, pool_elems, slot, 3, dbg)) return;
     switch (sd.Q) {
     case 17: init_slot<17>(sd, pool, rho0); break;
     case 25: init_slot<25>(sd, pool, rho0); break;
@@ -92,10 +127,25 @@ __device__ void macros_slot(const SlotDesc &d, const float *pool, double *out) {
 
 __global__ void k_batch_macros(const SlotDesc *__restrict__ desc, const float *__restrict__ pool,
                                const int *__restrict__ slots, const long long *__restrict__ out_off,
-                               double *__restrict__ out) {
+                               double *__restrict__ out, int nslots, long long pool_elems,
+                               long long out_elems, int *dbg) {
     __shared__ SlotDesc sd;
-    load_desc(desc + slots[blockIdx.x], &sd);
+    const int slot = slots[blockIdx.x];
+    if (slot < 0 || slot >= nslots) {
+        if (threadIdx.x == 0 && atomicCAS(dbg, 0, 4) == 0) dbg[1] = slot;
+        return;
+    }
+    load_desc(desc + slot, &sd);
     __syncthreads();
+    if (!desc_ok(sd, pool_elems, slot, 5, dbg)) return;
+    if (out_off[blockIdx.x] < 0 || out_off[blockIdx.x] + 4LL * sd.Ny > out_elems) {
+        if (threadIdx.x == 0 && atomicCAS(dbg, 0, 6) == 0) {
+            dbg[1] = slot;
+            dbg[3] = sd.Ny;
+            dbg[4] = (int)out_off[blockIdx.x];
+        }
+        return;
+    }
     double *o = out + out_off[blockIdx.x];
     switch (sd.Q) {
     case 17: macros_slot<17>(sd, pool, o); break;
@@ -105,24 +155,35 @@ __global__ void k_batch_macros(const SlotDesc *__restrict__ desc, const float *_
     }
 }
 
+// Load the batch kernels' module now (not lazily during a stream capture).
+int preload_batch_kernels() {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_batch_chunk);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_batch_init);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_batch_macros);
+    return (int)e;
+}
+
 int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, float *pool,
-                       int nslots, int chunk) {
+                       int nslots, int chunk, long long pool_elems, int *dbg) {
     if (nslots <= 0) return 0;
-    k_batch_chunk<<<nslots, kBatchThreads, 0, st>>>(desc, status, pool, chunk);
+    k_batch_chunk<<<nslots, kBatchThreads, 0, st>>>(desc, status, pool, chunk, pool_elems, dbg);
     return (int)cudaGetLastError();
 }
 
 int launch_batch_init(cudaStream_t st, SlotDesc *desc, float *pool, const int *slots, int n,
-                      float rho0) {
+                      float rho0, int nslots, long long pool_elems, int *dbg) {
     if (n <= 0) return 0;
-    k_batch_init<<<n, kBatchThreads, 0, st>>>(desc, pool, slots, rho0);
+    k_batch_init<<<n, kBatchThreads, 0, st>>>(desc, pool, slots, rho0, nslots, pool_elems, dbg);
     return (int)cudaGetLastError();
 }
 
 int launch_batch_macros(cudaStream_t st, const SlotDesc *desc, const float *pool,
-                        const int *slots, const long long *out_off, double *out, int n) {
+                        const int *slots, const long long *out_off, double *out, int n,
+                        int nslots, long long pool_elems, long long out_elems, int *dbg) {
     if (n <= 0) return 0;
-    k_batch_macros<<<n, kBatchThreads, 0, st>>>(desc, pool, slots, out_off, out);
+    k_batch_macros<<<n, kBatchThreads, 0, st>>>(desc, pool, slots, out_off, out, nslots,
+                                                pool_elems, out_elems, dbg);
     return (int)cudaGetLastError();
 }
 

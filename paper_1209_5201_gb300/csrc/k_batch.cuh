@@ -6,7 +6,8 @@
 // With Nx = 1 the pull of Eq. (5) only shifts in y: f_in(j, a) =
 // f~*(j - e_ay, a).  Per step one warp sums the incoming mass of each wall
 // (numerator of Eq. (12)): lane l loads the l-th (velocity, row) term of the
-// wall's list, then a warp-shuffle FP64 reduction in a fixed lane order gives
+// wall's list (built on the host, carried in the slot descriptor), then a
+// warp-shuffle FP64 reduction in a fixed lane order gives
 // M_in; every slot's arithmetic is independent of the slot index, the grid
 // and the other slots.
 #pragma once
@@ -17,38 +18,15 @@
 namespace lbm {
 
 template <int Q>
-struct WallTerms {
-    // incoming (velocity, row-from-wall) terms of the bottom wall; the top wall
-    // uses the mirrored velocity and row Ny-1-k
-    static constexpr int count() {
-        int n = 0;
-        for (int a = 0; a < Q; ++a) if (Lat<Q>::ey(a) < 0) n += -Lat<Q>::ey(a);
-        return n;
-    }
-};
-
-template <int Q>
 __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict__ pool,
-                                           SlotStatus *__restrict__ st, int chunk,
-                                           double *s_min, int *s_term) {
+                                           SlotStatus *__restrict__ st, double *s_min) {
+    const int chunk = d.chunk_steps;
     using L = Lat<Q>;
     const KConsts<float> &k = d.k;
     const int Ny = d.Ny;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
-    constexpr int NT = WallTerms<Q>::count();
-    static_assert(NT <= 32, "wall terms must fit a warp");
-
-    // term tables: bottom wall (velocity with e_y < 0, row k < |e_y|); the top
-    // wall's l-th term is velocity with e_y > 0 at row Ny - 1 - k
-    if (tid == 0) {
-        int n = 0, m = 0;
-        for (int a = 0; a < Q; ++a) {
-            for (int kk = 0; kk < -L::ey(a); ++kk) { s_term[n] = a; s_term[32 + n] = kk; ++n; }
-            for (int kk = 0; kk < L::ey(a); ++kk) { s_term[64 + m] = a; s_term[96 + m] = kk; ++m; }
-        }
-    }
-    __syncthreads();
+    const int NT = d.nterm;                // <= 32, checked with the descriptor
 
     float *buf0 = pool + d.f_off;
     float *buf1 = buf0 + (long long)Q * Ny;
@@ -59,8 +37,8 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         if (warp < 2) {
             double v = 0.0;
             if (lane < NT) {
-                const int a = s_term[64 * warp + lane];
-                const int kk = s_term[64 * warp + 32 + lane];
+                const int a = d.term_a[warp][lane];
+                const int kk = d.term_row[warp][lane];
                 const int row = warp == 0 ? kk : Ny - 1 - kk;
                 v = (double)src[(long long)a * Ny + row];
             }
@@ -129,11 +107,11 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
             e += f[a] * (cx * cx + cy * cy);
         }
         const double T = e / (2.0 * s0);
-        const double du = u - prev_u[j], dT = T - prev_T[j], tr = T - d.T_ref;
+        const double du = u - prev_u[j], dT = T - prev_T[j];
         acc[0] += du * du;
         acc[1] += u * u;
         acc[2] += dT * dT;
-        acc[3] += tr * tr;
+        acc[3] += T * T;
         acc[4] += s0;
         if (!isfinite(u) || !isfinite(T)) acc[5] += 1.0;
         prev_u[j] = (float)u;

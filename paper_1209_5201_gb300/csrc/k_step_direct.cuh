@@ -54,18 +54,20 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
                                      const double *s_min, typename Store<PREC>::C (&f)[Q]) {
     using L = Lat<Q>;
     using C = typename Store<PREC>::C;
+    // the cell's own index; velocity a reads at cell + off_src[a]
+    const int cell = j * k.pitch + x + kPadL;
+    const typename Store<PREC>::S *__restrict__ src = fin + cell;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int sj = j - L::ey(a);
-        const int sx = x - L::ex(a) + kPadL;
         if (WALL && sj < 0) {
             f[a] = (C)(s_min[threadIdx.x + 3 - L::ex(a)] * k.wcoef[0][a]);
         } else if (WALL && sj >= k.Ny) {
             f[a] = (C)(s_min[threadIdx.x + 3 - L::ex(a)] * k.wcoef[1][a]);
         } else {
-            const long long ridx = (long long)sj * k.pitch + sx;
-            C v = to_c(fin[(long long)a * k.plane + ridx]);
-            if constexpr (Store<PREC>::dev) v += k.w[a] * rin[ridx];
+            C v = to_c(src[k.off_src[a]]);
+            if constexpr (Store<PREC>::dev)
+                v += k.w[a] * rin[cell - L::ey(a) * k.pitch - L::ex(a)];
             f[a] = v;
         }
     }
@@ -114,17 +116,27 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
         col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
     });
 
-    const long long roff = (long long)j * k.pitch;
     const bool image = x < kPadL || x >= k.Nx - kPadL;
+    if (!image) {
+        S *__restrict__ dst = fout + (j * k.pitch + x + kPadL);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        C v = o[a];
-        if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
-        S *row = fout + (long long)a * k.plane + roff;
-        if (CS && !image) store_cs<S>(row + x + kPadL, from_c<S>(v));
-        else store_with_images<S>(row, x, k.Nx, from_c<S>(v));
+        for (int a = 0; a < Q; ++a) {
+            C v = o[a];
+            if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
+            if (CS) store_cs<S>(dst + k.off_dst[a], from_c<S>(v));
+            else dst[k.off_dst[a]] = from_c<S>(v);
+        }
+        if constexpr (Store<PREC>::dev) rout[j * k.pitch + x + kPadL] = (float)col.rho;
+    } else {
+        const long long roff = (long long)j * k.pitch;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            C v = o[a];
+            if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
+            store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx, from_c<S>(v));
+        }
+        if constexpr (Store<PREC>::dev) store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);
     }
-    if constexpr (Store<PREC>::dev) store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);
 }
 
 }  // namespace lbm

@@ -87,12 +87,18 @@ struct Collision {
     C rho;
 
     __device__ __forceinline__ void setup(const C (&f)[Q], const KConsts<C> &k) {
-        C r0 = 0, jx = 0, jy = 0;
+        // moments from the sums and differences of opposite pairs
+        C r0 = f[0], jx = 0, jy = 0;
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            r0 += f[a];
-            if (L::ex(a) != 0) jx += C(L::ex(a)) * f[a];
-            if (L::ey(a) != 0) jy += C(L::ey(a)) * f[a];
+        for (int a = 1; a < Q; a += 2) {
+            const C sum = f[a] + f[a + 1], dif = f[a] - f[a + 1];
+            r0 += sum;
+            if (L::ex(a) == 1) jx += dif;
+            else if (L::ex(a) == -1) jx -= dif;
+            else if (L::ex(a) != 0) jx += C(L::ex(a)) * dif;
+            if (L::ey(a) == 1) jy += dif;
+            else if (L::ey(a) == -1) jy -= dif;
+            else if (L::ey(a) != 0) jy += C(L::ey(a)) * dif;
         }
         rho = r0;
         const C inv = C(1) / r0;
@@ -102,7 +108,7 @@ struct Collision {
         if (k.thermal) {
             C e2 = 0;
 #pragma unroll
-            for (int a = 1; a < Q; ++a) e2 += C(L::e2(a)) * f[a];
+            for (int a = 1; a < Q; a += 2) e2 += C(L::e2(a)) * (f[a] + f[a + 1]);
             T = (k.r2 * e2 * inv - u2) * C(0.5);
             th = T - C(1);
         }
@@ -114,21 +120,34 @@ struct Collision {
         omc = C(1) - om;
         sx = k.r * ux;
         sy = k.r * uy;
-        A3 = k.eq_order >= 3 ? C(1) / C(6) : C(0);
-        A4 = k.eq_order >= 4 ? C(1) / C(24) : C(0);
-        const C orho = om * r0;
+        set_coefficients(u2, th, om * r0, k);
+    }
+
+    // A0 = a00 + a01 c2 + a02 c2^2, A1 = a10 + a11 c2, A2 = a20 + a21 c2: the
+    // Eq. (4) coefficients above, collected in powers of c2 (D = 2)
+    __device__ __forceinline__ void set_coefficients(C u2, C th, C orho, const KConsts<C> &k) {
+        const bool o3 = k.eq_order >= 3, o4 = k.eq_order >= 4;
+        C a00 = C(1) - C(0.5) * u2 - th, a01 = C(0.5) * th, a02 = C(0);
+        C a10 = C(1), a11 = C(0), a20 = C(0.5), a21 = C(0);
+        if (o3) {
+            a10 += C(-0.5) * u2 - C(2) * th;
+            a11 = C(0.5) * th;
+        }
+        if (o4) {
+            a00 += C(0.125) * u2 * u2 + th * u2 + th * th;
+            a01 += C(-0.25) * th * u2 - th * th;
+            a02 = C(0.125) * th * th;
+            a20 += C(-0.25) * u2 - C(1.5) * th;
+            a21 = C(0.25) * th;
+        }
+        A3 = o3 ? C(1) / C(6) : C(0);
+        A4 = o4 ? C(1) / C(24) : C(0);
 #pragma unroll
         for (int s = 0; s < L::NSH; ++s) {
-            const C c2 = k.r2 * C(L::shell_e2(s));
-            C a0 = C(1) - C(0.5) * u2 + C(0.5) * th * (c2 - C(2));
-            C a1 = C(1), a2 = C(0.5);
-            if (k.eq_order >= 3) a1 += C(-0.5) * u2 + C(0.5) * th * (c2 - C(4));
-            if (k.eq_order >= 4) {
-                a0 += C(0.125) * u2 * u2 - C(0.25) * th * (c2 - C(4)) * u2 +
-                      C(0.125) * th * th * (c2 * c2 - C(8) * c2 + C(8));
-                a2 += C(-0.25) * u2 + C(0.25) * th * (c2 - C(6));
-            }
-            A0[s] = a0; A1[s] = a1; A2[s] = a2;
+            const C c2 = k.c2sh[s];
+            A0[s] = (a02 * c2 + a01) * c2 + a00;
+            A1[s] = a11 * c2 + a10;
+            A2[s] = a21 * c2 + a20;
             cw[s] = orho * k.wsh[s];
         }
     }

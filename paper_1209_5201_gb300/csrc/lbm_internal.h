@@ -45,7 +45,10 @@ struct KConsts {
     C tau_lat;                // constant tau / dt
     C mu_m1;                  // mu_exp - 1
     C wsh[kMaxShells];        // shell weights
+    C c2sh[kMaxShells];       // |c|^2 = r^2 |e|^2 of each shell
     C w[kMaxQ];               // per-velocity weights
+    int off_src[kMaxQ];       // a * plane - e_ay * pitch - e_ax: pull source offset
+    int off_dst[kMaxQ];       // a * plane: store offset
     double wcoef[2][kMaxQ];   // g^w_a / D_w (0 unless a leaves the wall)
 };
 

@@ -19,6 +19,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -77,6 +78,8 @@ struct ServerImpl {
     SlotStatus *d_status = nullptr;
     int *d_idx = nullptr;                    // slot lists for init / read-out
     long long *d_off = nullptr;
+    int *d_dbg = nullptr;                    // kernels' record of a rejected descriptor
+    int *h_dbg = nullptr;
     double *d_out = nullptr;                 // read-out staging
     long long out_elems = 0;
     // host mirrors (pinned)
@@ -167,17 +170,41 @@ struct ServerImpl {
         d.Q = L.Q;
         d.Ny = r.Ny;
         d.cur = 0;
+        // Steps per chunk launch: cheaper slots run more steps, so that every
+        // CTA of a launch takes about as long as the costliest one (a Q = 37
+        // column of 2048 rows runs chunk_steps); the cost model is the velocity
+        // count times the cells per thread plus a latency floor.
+        const double cost = L.Q * std::ceil(r.Ny / 256.0) + 37.0;
+        const double cost_ref = 37.0 * 8.0 + 37.0;
+        d.chunk_steps = (int)std::min<double>(32.0 * cfg.chunk_steps,
+                                              std::max<double>(cfg.chunk_steps,
+                                                               std::round(cfg.chunk_steps * cost_ref / cost)));
         // residual every ~quarter of the slowest e-folding time of the start-up
         // (0.127 Ny r / Kn steps for the fundamental shear mode), in chunks
         const double efold = r.tau > 0 ? r.Ny * r.Ny / (9.8696 * r.tau * L.r * r.Ny)
                                        : 0.127 * r.Ny * L.r / r.Kn;
-        d.check_every = std::max(1, (int)std::lround(efold / (4.0 * cfg.chunk_steps)));
+        d.check_every = std::max(1, (int)std::lround(efold / (4.0 * d.chunk_steps)));
         d.f_off = off;
         d.prev_off = off + 2LL * L.Q * r.Ny;
         d.tol = r.tol;
         d.max_steps = r.max_steps;
         d.T_ref = r.thermal ? 0.5 * (r.T_wall[0] + r.T_wall[1]) : 1.0;
+        // incoming terms per wall (Sec. III: at layer l the velocities with
+        // e.n < -l); the bottom list takes e_y < 0 at rows 0..|e_y|-1, the top
+        // list e_y > 0 at rows Ny-1.. (distance from the wall)
+        int nb = 0, nt = 0;
+        for (int a = 0; a < L.Q; ++a) {
+            for (int kk = 0; kk < -L.ey[a]; ++kk) { d.term_a[0][nb] = (signed char)a; d.term_row[0][nb] = (signed char)kk; ++nb; }
+            for (int kk = 0; kk < L.ey[a]; ++kk) { d.term_a[1][nt] = (signed char)a; d.term_row[1][nt] = (signed char)kk; ++nt; }
+        }
+        if (nb != nt || nb > 32) std::abort();   // lattices are symmetric, <= 26 terms
+        d.nterm = nb;
         fill_consts(d.k, L, p, 1);
+        // the kernels reject anything else; the host must never produce it
+        if (!(d.Ny >= 6 && d.Ny <= kMaxNy && d.f_off >= 0 &&
+              d.f_off + 2LL * d.Q * d.Ny + 2LL * d.Ny <= pool_elems &&
+              d.chunk_steps >= 1 && d.check_every >= 1))
+            std::abort();
         SlotStatus &st = h_status[s];
         std::memset(&st, 0, sizeof(st));
         st.state = kSlotRunning;
@@ -199,6 +226,17 @@ struct ServerImpl {
             e = cudaMemcpyAsync(d_status + s, h_status + s, sizeof(SlotStatus),
                                 cudaMemcpyHostToDevice, stream);
         return e;
+    }
+
+    int reject_desc() {
+        char buf[256];
+        std::snprintf(buf, sizeof buf,
+                      "batch kernel rejected a slot descriptor: code %d slot %d Q %d Ny %d "
+                      "f_off %d prev_off %d chunk %d check %d",
+                      h_dbg[0], h_dbg[1], h_dbg[2], h_dbg[3], h_dbg[4], h_dbg[5], h_dbg[6], h_dbg[7]);
+        worker_msg = buf;
+        worker_error = LBM_EINVAL;
+        return LBM_EINVAL;
     }
 
     int fail(const char *what, cudaError_t e) {
@@ -234,19 +272,24 @@ struct ServerImpl {
             for (size_t i = 0; i < admitted.size(); ++i) h_idx[i] = admitted[i];
             if ((e = cudaMemcpyAsync(d_idx, h_idx, sizeof(int) * admitted.size(), cudaMemcpyHostToDevice, stream)))
                 return fail("upload slot list", e);
-            if ((e = (cudaError_t)launch_batch_init(stream, d_desc, pool, d_idx, (int)admitted.size(), 1.0f)))
+            if ((e = (cudaError_t)launch_batch_init(stream, d_desc, pool, d_idx, (int)admitted.size(), 1.0f,
+                                                     (int)slots.size(), pool_elems, d_dbg)))
                 return fail("init kernel", e);
         }
         // chunk launch + status read-back
         if (graph) {
             if ((e = cudaGraphLaunch(graph, stream))) return fail("graph launch", e);
         } else {
-            if ((e = (cudaError_t)launch_batch_chunk(stream, d_desc, d_status, pool, (int)slots.size(), cfg.chunk_steps)))
+            if ((e = (cudaError_t)launch_batch_chunk(stream, d_desc, d_status, pool, (int)slots.size(), cfg.chunk_steps,
+                                                      pool_elems, d_dbg)))
                 return fail("chunk kernel", e);
             if ((e = cudaMemcpyAsync(h_status, d_status, sizeof(SlotStatus) * slots.size(), cudaMemcpyDeviceToHost, stream)))
                 return fail("status read-back", e);
+            if ((e = cudaMemcpyAsync(h_dbg, d_dbg, sizeof(int) * 8, cudaMemcpyDeviceToHost, stream)))
+                return fail("check read-back", e);
         }
         if ((e = cudaStreamSynchronize(stream))) return fail("chunk", e);
+        if (h_dbg[0]) return reject_desc();
         ++chunks;
         occupancy_sum += running;
         // retire finished slots
@@ -268,11 +311,15 @@ struct ServerImpl {
                 return fail("upload read-out list", e);
             if ((e = cudaMemcpyAsync(d_off, h_off, sizeof(long long) * n, cudaMemcpyHostToDevice, stream)))
                 return fail("upload read-out offsets", e);
-            if ((e = (cudaError_t)launch_batch_macros(stream, d_desc, pool, d_idx, d_off, d_out, (int)n)))
+            if ((e = (cudaError_t)launch_batch_macros(stream, d_desc, pool, d_idx, d_off, d_out, (int)n,
+                                                       (int)slots.size(), pool_elems, out_elems, d_dbg)))
                 return fail("read-out kernel", e);
             if ((e = cudaMemcpyAsync(h_out, d_out, sizeof(double) * o, cudaMemcpyDeviceToHost, stream)))
                 return fail("read-out copy", e);
+            if ((e = cudaMemcpyAsync(h_dbg, d_dbg, sizeof(int) * 8, cudaMemcpyDeviceToHost, stream)))
+                return fail("check read-back", e);
             if ((e = cudaStreamSynchronize(stream))) return fail("read-out", e);
+            if (h_dbg[0]) return reject_desc();
             const double t = now();
             std::unique_lock<std::mutex> lk(mu);
             for (size_t i = 0; i < n; ++i) {
@@ -415,6 +462,8 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
         ck(cudaMallocAsync((void **)&S.d_idx, sizeof(int) * ns, S.stream));
         ck(cudaMallocAsync((void **)&S.d_off, sizeof(long long) * ns, S.stream));
         ck(cudaMallocAsync((void **)&S.d_out, sizeof(double) * S.out_elems, S.stream));
+        ck(cudaMallocAsync((void **)&S.d_dbg, sizeof(int) * 8, S.stream));
+        ck(cudaMallocHost((void **)&S.h_dbg, sizeof(int) * 8));
         ck(cudaMallocHost((void **)&S.h_desc, sizeof(SlotDesc) * ns));
         ck(cudaMallocHost((void **)&S.h_status, sizeof(SlotStatus) * ns));
         ck(cudaMallocHost((void **)&S.h_idx, sizeof(int) * ns));
@@ -425,16 +474,21 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
             std::memset(S.h_status, 0, sizeof(SlotStatus) * ns);
             ck(cudaMemcpyAsync(S.d_desc, S.h_desc, sizeof(SlotDesc) * ns, cudaMemcpyHostToDevice, S.stream));
             ck(cudaMemcpyAsync(S.d_status, S.h_status, sizeof(SlotStatus) * ns, cudaMemcpyHostToDevice, S.stream));
+            ck(cudaMemsetAsync(S.d_dbg, 0, sizeof(int) * 8, S.stream));
+            std::memset(S.h_dbg, 0, sizeof(int) * 8);
             ck(cudaStreamSynchronize(S.stream));
         }
+        if (e == cudaSuccess) ck((cudaError_t)preload_batch_kernels());
         if (e == cudaSuccess && cfg->use_graph) {
             // capture: chunk kernel over every slot, then the status read-back
             cudaStream_t cs;
             ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
             cudaGraph_t g;
             ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            ck((cudaError_t)launch_batch_chunk(cs, S.d_desc, S.d_status, S.pool, ns, cfg->chunk_steps));
+            ck((cudaError_t)launch_batch_chunk(cs, S.d_desc, S.d_status, S.pool, ns, cfg->chunk_steps,
+                                               S.pool_elems, S.d_dbg));
             ck(cudaMemcpyAsync(S.h_status, S.d_status, sizeof(SlotStatus) * ns, cudaMemcpyDeviceToHost, cs));
+            ck(cudaMemcpyAsync(S.h_dbg, S.d_dbg, sizeof(int) * 8, cudaMemcpyDeviceToHost, cs));
             ck(cudaStreamEndCapture(cs, &g));
             if (e == cudaSuccess) ck(cudaGraphInstantiate(&S.graph, g, 0));
             cudaGraphDestroy(g);
@@ -563,12 +617,14 @@ int lbm_server_destroy(lbm_server *h) {
     if (S.d_idx) cudaFreeAsync(S.d_idx, S.stream);
     if (S.d_off) cudaFreeAsync(S.d_off, S.stream);
     if (S.d_out) cudaFreeAsync(S.d_out, S.stream);
+    if (S.d_dbg) cudaFreeAsync(S.d_dbg, S.stream);
     cudaStreamSynchronize(S.stream);
     if (S.h_desc) cudaFreeHost(S.h_desc);
     if (S.h_status) cudaFreeHost(S.h_status);
     if (S.h_idx) cudaFreeHost(S.h_idx);
     if (S.h_off) cudaFreeHost(S.h_off);
     if (S.h_out) cudaFreeHost(S.h_out);
+    if (S.h_dbg) cudaFreeHost(S.h_dbg);
     delete h;
     return LBM_OK;
 }
