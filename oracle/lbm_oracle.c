@@ -310,6 +310,18 @@ void orc_macros(const orc_lattice *L, const orc_params *P, const double *f,
         orc_moments(L, P->thermal, f + c, plane, rho + c, ux + c, uy + c, T + c);
 }
 
+/* Eq. (3) fields with the kinetic temperature sum f |c - u|^2 / (D rho) for
+ * every run, isothermal ones included (there it is a diagnostic only: the
+ * collision of an isothermal run uses T = 1). */
+void orc_macros_kinetic(const orc_lattice *L, const orc_params *P, const double *f,
+                        double *rho, double *ux, double *uy, double *T)
+{
+    const long plane = (long)P->Nx * P->Ny;
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < plane; ++c)
+        orc_moments(L, 1, f + c, plane, rho + c, ux + c, uy + c, T + c);
+}
+
 /* Steady-state driver: run in chunks of check_every steps until the relative
  * change of u_x over one chunk (and, when thermal, of T - T_ref) drops to
  * tol.  Returns 0 when converged, 1 when max_steps ran out, < 0 on error. */

@@ -65,6 +65,8 @@ def _load():
         lib.orc_init_fields.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp,
                                         dp, dp]
         lib.orc_macros.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp, dp, dp]
+        lib.orc_macros_kinetic.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp,
+                                           dp, dp]
         lib.orc_run_to_residual.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp,
                                             C.c_double, C.c_long, C.c_int,
                                             C.POINTER(C.c_long), dp]
@@ -171,6 +173,14 @@ def macros(p: Problem, f: np.ndarray):
     out = [np.empty((p.Ny, p.Nx)) for _ in range(4)]
     _load().orc_macros(C.byref(p._cl), C.byref(p._cp), _dp(np.ascontiguousarray(f)),
                        *[_dp(a) for a in out])
+    return tuple(out)
+
+
+def macros_kinetic(p: Problem, f: np.ndarray):
+    """Like macros(), with the kinetic temperature also for isothermal runs."""
+    out = [np.empty((p.Ny, p.Nx)) for _ in range(4)]
+    _load().orc_macros_kinetic(C.byref(p._cl), C.byref(p._cp), _dp(np.ascontiguousarray(f)),
+                               *[_dp(a) for a in out])
     return tuple(out)
 
 

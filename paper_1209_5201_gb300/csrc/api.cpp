@@ -178,6 +178,9 @@ void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int p
         k.off_src[a] = (int)((long long)a * k.plane - (long long)L.ey[a] * pitch - L.ex[a]);
         k.off_dst[a] = (int)((long long)a * k.plane);
     }
+    double e2w = 0;
+    for (int a = 0; a < L.Q; ++a) e2w += (double)(C)L.w[a] * (L.ex[a] * L.ex[a] + L.ey[a] * L.ey[a]);
+    k.e2w = (C)e2w;
     // Eq. (11)-(12): g^w_a / sum_{l<N} sum_{e.n>l} g^w = g^w_a / sum_{e.n>0} |e.n| g^w
     for (int wall = 0; wall < 2; ++wall) {
         double g[kMaxQ];
@@ -409,6 +412,7 @@ int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
 int lbm_solver_destroy(lbm_solver *h) {
     if (!h) return LBM_OK;
     SolverImpl &s = h->s;
+    if (s.step_graph) cudaGraphExecDestroy(s.step_graph);
     if (s.owns_mem && s.dmem) cudaFreeAsync(s.dmem, s.stream);
     cudaStreamSynchronize(s.stream);
     if (s.pinned) cudaFreeHost(s.pinned);
@@ -445,16 +449,65 @@ int lbm_solver_init_fields(lbm_solver *h, const double *rho, const double *ux, c
     API_END
 }
 
+namespace lbm {
+namespace {
+// A CUDA graph of kGraphSteps step launches starting from buffer 0, captured
+// once per kernel choice on a private stream and replayed on the solver's.
+int ensure_step_graph(SolverImpl &s, int kern) {
+    if (s.step_graph && s.graph_kernel == kern && s.graph_variant == s.variant) return LBM_OK;
+    if (s.step_graph) {
+        cudaGraphExecDestroy(s.step_graph);
+        s.step_graph = nullptr;
+    }
+    cudaStream_t cs;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t keep = s.stream;
+    s.stream = cs;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i)
+        e = (cudaError_t)launch_step_variant(s, i & 1, (i & 1) ^ 1, kern, s.variant);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    s.stream = keep;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s.step_graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        s.step_graph = nullptr;
+        set_error(std::string("step graph: ") + cudaGetErrorString(e));
+        return LBM_ECUDA;
+    }
+    s.graph_kernel = kern;
+    s.graph_variant = s.variant;
+    return LBM_OK;
+}
+}  // namespace
+}  // namespace lbm
+
 int lbm_solver_step(lbm_solver *h, int64_t n) {
     API_BEGIN
     if (!h || n < 0) { set_error("NULL solver or negative step count"); return LBM_EINVAL; }
     SolverImpl &s = h->s;
     const int kern = effective_kernel(s);
-    for (int64_t i = 0; i < n; ++i) {
+    auto one = [&]() -> int {
         CU(launch_step_variant(s, s.cur, s.cur ^ 1, kern, s.variant));
         s.cur ^= 1;
         ++s.steps;
+        return LBM_OK;
+    };
+    int rc;
+    if (n >= 2 * kGraphSteps) {
+        if ((rc = ensure_step_graph(s, kern))) return rc;
+        if (s.cur == 1) { if ((rc = one())) return rc; --n; }
+        while (n >= kGraphSteps) {
+            CU(cudaGraphLaunch(s.step_graph, s.stream));
+            s.steps += kGraphSteps;
+            n -= kGraphSteps;
+        }
     }
+    for (int64_t i = 0; i < n; ++i)
+        if ((rc = one())) return rc;
     return LBM_OK;
     API_END
 }

@@ -19,18 +19,20 @@ __device__ __forceinline__ double splitmix_u01(uint64_t seed, uint64_t k) {
     return (double)(z >> 11) * 0x1.0p-53;
 }
 
-// Equilibrium f~* = rho g^eq(u, T) (Eq. (4)) of every velocity.
-template <int Q, class C>
-__device__ __forceinline__ void equilibrium_all(C rho, C ux, C uy, C T, const KConsts<C> &k,
-                                                C (&o)[Q]) {
+// Equilibrium f~* = rho g^eq(u, T) (Eq. (4)) of every velocity, or its
+// deviation w (rho g - 1) when SHIFT (drho = rho - 1 given separately so that
+// it carries no cancellation error).
+template <int Q, class C, bool SHIFT>
+__device__ __forceinline__ void equilibrium_all(C rho, C drho, C ux, C uy, C T,
+                                                const KConsts<C> &k, C (&o)[Q]) {
     // A collision with omega = 1 from f = 0 leaves exactly rho g^eq.
-    Collision<Q, C> col;
+    Collision<Q, C, SHIFT> col;
     const C u2 = ux * ux + uy * uy;
     col.omc = C(0);
     col.sx = k.r * ux;
     col.sy = k.r * uy;
     col.rho = rho;
-    col.set_coefficients(u2, T - C(1), rho, k);
+    col.set_coefficients(u2, T - C(1), rho, drho / rho, k);
     o[0] = col.rest(C(0));
     PairLoop<1, Q>::run([&](auto ic) {
         constexpr int A = decltype(ic)::value;
@@ -68,7 +70,7 @@ __global__ void k_init_rest(typename Store<PREC>::S *f, float *rplane,
         double rho = rho0;
         if (amp != 0.0) rho = rho0 * (1.0 + amp * (2.0 * splitmix_u01(seed, (uint64_t)c) - 1.0));
         C o[Q];
-        equilibrium_all<Q, C>((C)rho, C(0), C(0), C(1), k, o);
+        equilibrium_all<Q, C, Store<PREC>::shifted>((C)rho, (C)(rho - 1.0), C(0), C(0), C(1), k, o);
         store_cell<Q, PREC>(f, rplane, k, x, j, o, (C)rho);
     }
 }
@@ -85,8 +87,9 @@ __global__ void k_init_fields(typename Store<PREC>::S *f, float *rplane,
          c += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
         C o[Q];
-        equilibrium_all<Q, C>((C)rho[c], ux ? (C)ux[c] : C(0), uy ? (C)uy[c] : C(0),
-                              T ? (C)T[c] : C(1), k, o);
+        equilibrium_all<Q, C, Store<PREC>::shifted>((C)rho[c], (C)(rho[c] - 1.0),
+                                                    ux ? (C)ux[c] : C(0), uy ? (C)uy[c] : C(0),
+                                                    T ? (C)T[c] : C(1), k, o);
         store_cell<Q, PREC>(f, rplane, k, x, j, o, (C)rho[c]);
     }
 }
@@ -101,9 +104,10 @@ __global__ void k_plane_to_f64(const typename Store<PREC>::S *f, const float *rp
          c += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
         const long long r = (long long)j * k.pitch + x + kPadL;
-        auto v = to_c(f[(long long)a * k.plane + r]);
-        if constexpr (Store<PREC>::dev) v += k.w[a] * rplane[r];
-        out[c] = (double)v;
+        double v = (double)to_c(f[(long long)a * k.plane + r]);
+        if constexpr (Store<PREC>::dev) v = (double)(to_c(f[(long long)a * k.plane + r]) + k.w[a] * rplane[r]);
+        if constexpr (Store<PREC>::shifted) v += (double)k.w[a];
+        out[c] = v;
     }
 }
 
@@ -121,6 +125,7 @@ __global__ void k_plane_from_f64(typename Store<PREC>::S *f, const float *rplane
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
         C v = (C)in[c];
         if constexpr (Store<PREC>::dev) v -= k.w[a] * rplane[(long long)j * k.pitch + x + kPadL];
+        if constexpr (Store<PREC>::shifted) v = (C)(in[c] - (double)k.w[a]);
         store_with_images<S>(f + (long long)a * k.plane + (long long)j * k.pitch, x, k.Nx,
                              from_c<S>(v));
     }
@@ -142,7 +147,7 @@ __global__ void k_macros(const typename Store<PREC>::S *f, const float *rplane,
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
         const long long ro = (long long)j * k.pitch + x + kPadL;
         C fv[Q];
-        C s0 = 0, sx = 0, sy = 0;
+        C s0 = 0, sx = 0, sy = 0, se = 0;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             C v = to_c(f[(long long)a * k.plane + ro]);
@@ -151,18 +156,19 @@ __global__ void k_macros(const typename Store<PREC>::S *f, const float *rplane,
             s0 += v;
             sx += C(L::ex(a)) * v;
             sy += C(L::ey(a)) * v;
+            se += C(L::e2(a)) * v;
         }
-        const C u = r * sx / s0, v = r * sy / s0;
-        C e = 0;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const C cx = r * C(L::ex(a)) - u, cy = r * C(L::ey(a)) - v;
-            e += fv[a] * (cx * cx + cy * cy);
-        }
-        if (rho) rho[c] = (double)s0;
+        // shifted storage: the sums are of deviations; sum w = 1, sum e w = 0
+        const C rh = Store<PREC>::shifted ? C(1) + s0 : s0;
+        const C u = r * sx / rh, v = r * sy / rh;
+        if constexpr (Store<PREC>::shifted) se += k.e2w;
+        // rho D T = sum f |c - u|^2 = r^2 sum e^2 f - rho u^2
+        const C e = k.r2 * se - rh * (u * u + v * v);
+        if (rho) rho[c] = (double)rh;
         if (ux) ux[c] = (double)u;
         if (uy) uy[c] = (double)v;
-        if (T) T[c] = (double)(e / (C(2) * s0));
+        if (T) T[c] = (double)(e / (C(2) * rh));
+        (void)fv;
     }
 }
 
@@ -187,6 +193,7 @@ __global__ void k_wall_mass(const typename Store<PREC>::S *f, const float *rplan
                 double v = (double)to_c(f[(long long)b * k.plane + (long long)row * k.pitch + xs]);
                 if constexpr (Store<PREC>::dev)
                     v += (double)k.w[b] * (double)rplane[(long long)row * k.pitch + xs];
+                if constexpr (Store<PREC>::shifted) v += (double)k.w[b];
                 m += v;
             }
         }
@@ -226,7 +233,7 @@ __global__ void k_mass_partials(const typename Store<PREC>::S *f, const float *r
          c += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
         const long long ro = (long long)j * k.pitch + x + kPadL;
-        double s = 0.0;
+        double s = Store<PREC>::shifted ? 1.0 : 0.0;     // sum of the weights
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             auto v = to_c(f[(long long)a * k.plane + ro]);

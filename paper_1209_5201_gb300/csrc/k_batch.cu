@@ -5,7 +5,7 @@
 
 namespace lbm {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 512;
 
 // A slot descriptor is used only if its buffers lie inside the pool; a bad
 // one is recorded in dbg[0..7] (code, slot, Q, Ny, f_off, prev_off, chunk,
@@ -42,7 +42,7 @@ __device__ __forceinline__ void load_desc(const SlotDesc *g, SlotDesc *s) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2)
+__global__ void __launch_bounds__(kBatchThreads, 1)
 k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
               float *__restrict__ pool, int chunk, long long pool_elems, int *dbg) {
     __shared__ SlotDesc sd;
@@ -62,14 +62,14 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
     (void)chunk;
 }
 
-// Rest equilibrium f~* = rho0 w_a of newly admitted slots; previous-check
-// fields u_x = 0, T = 1.
+// Rest equilibrium f~* = rho0 w_a of newly admitted slots, stored as the
+// deviation (rho0 - 1) w_a; previous-check fields u_x = 0, T = 1.
 template <int Q>
 __device__ void init_slot(const SlotDesc &d, float *pool, float rho0) {
     float *f = pool + d.f_off + (d.cur ? (long long)Q * d.Ny : 0);
     for (int j = threadIdx.x; j < d.Ny; j += blockDim.x) {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) f[(long long)a * d.Ny + j] = rho0 * d.k.w[a];
+        for (int a = 0; a < Q; ++a) f[(long long)a * d.Ny + j] = (rho0 - 1.0f) * d.k.w[a];
         float *pu = pool + d.prev_off;
         pu[j] = 0.0f;
         pu[d.Ny + j] = 1.0f;
@@ -103,25 +103,22 @@ __device__ void macros_slot(const SlotDesc &d, const float *pool, double *out) {
     const float *f = pool + d.f_off + (d.cur ? (long long)Q * d.Ny : 0);
     const double r = (double)d.k.r;
     for (int j = threadIdx.x; j < d.Ny; j += blockDim.x) {
-        double fv[Q], s0 = 0, sx = 0, sy = 0;
+        // stored deviations d = f - w
+        double s0 = 0, sx = 0, sy = 0, se = (double)d.k.e2w;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            fv[a] = f[(long long)a * d.Ny + j];
-            s0 += fv[a];
-            sx += L::ex(a) * fv[a];
-            sy += L::ey(a) * fv[a];
+            const double fa = (double)f[(long long)a * d.Ny + j];
+            s0 += fa;
+            sx += L::ex(a) * fa;
+            sy += L::ey(a) * fa;
+            se += L::e2(a) * fa;
         }
-        const double u = r * sx / s0, v = r * sy / s0;
-        double e = 0;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const double cx = r * L::ex(a) - u, cy = r * L::ey(a) - v;
-            e += fv[a] * (cx * cx + cy * cy);
-        }
-        out[j] = s0;
+        const double rh = 1.0 + s0;
+        const double u = r * sx / rh, v = r * sy / rh;
+        out[j] = rh;
         out[d.Ny + j] = u;
         out[2 * d.Ny + j] = v;
-        out[3 * d.Ny + j] = e / (2.0 * s0);
+        out[3 * d.Ny + j] = ((double)d.k.r2 * se - rh * (u * u + v * v)) / (2.0 * rh);
     }
 }
 

@@ -40,7 +40,8 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
                 const int a = d.term_a[warp][lane];
                 const int kk = d.term_row[warp][lane];
                 const int row = warp == 0 ? kk : Ny - 1 - kk;
-                v = (double)src[(long long)a * Ny + row];
+                // stored deviations: f = d + w
+                v = (double)src[(long long)a * Ny + row] + (double)k.w[a];
             }
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0) s_min[warp] = v;
@@ -52,11 +53,11 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const int sj = j - L::ey(a);
-                if (sj < 0) f[a] = (float)(mb * k.wcoef[0][a]);
-                else if (sj >= Ny) f[a] = (float)(mt * k.wcoef[1][a]);
+                if (sj < 0) f[a] = (float)(mb * k.wcoef[0][a] - (double)k.w[a]);
+                else if (sj >= Ny) f[a] = (float)(mt * k.wcoef[1][a] - (double)k.w[a]);
                 else f[a] = src[(long long)a * Ny + sj];
             }
-            Collision<Q, float> col;
+            Collision<Q, float, true> col;
             col.setup(f, k);
             float o[Q];
             o[0] = col.rest(f[0]);
@@ -90,29 +91,25 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const double r = (double)k.r;
     for (int j = tid; j < Ny; j += nth) {
-        double s0 = 0, sx = 0, sy = 0;
-        float f[Q];
+        // deviations d = f - w: rho = 1 + sum d, sum e w = 0, sum e^2 w = e2w
+        double s0 = 0, sx = 0, sy = 0, se = (double)k.e2w;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            f[a] = src[(long long)a * Ny + j];
-            s0 += f[a];
-            sx += L::ex(a) * (double)f[a];
-            sy += L::ey(a) * (double)f[a];
+            const double fa = (double)src[(long long)a * Ny + j];
+            s0 += fa;
+            sx += L::ex(a) * fa;
+            sy += L::ey(a) * fa;
+            se += L::e2(a) * fa;
         }
-        const double u = r * sx / s0, v = r * sy / s0;
-        double e = 0;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const double cx = r * L::ex(a) - u, cy = r * L::ey(a) - v;
-            e += f[a] * (cx * cx + cy * cy);
-        }
-        const double T = e / (2.0 * s0);
+        const double rh = 1.0 + s0;
+        const double u = r * sx / rh, v = r * sy / rh;
+        const double T = ((double)k.r2 * se - rh * (u * u + v * v)) / (2.0 * rh);
         const double du = u - prev_u[j], dT = T - prev_T[j];
         acc[0] += du * du;
         acc[1] += u * u;
         acc[2] += dT * dT;
         acc[3] += T * T;
-        acc[4] += s0;
+        acc[4] += rh;
         if (!isfinite(u) || !isfinite(T)) acc[5] += 1.0;
         prev_u[j] = (float)u;
         prev_T[j] = (float)T;
@@ -137,14 +134,18 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         // geometric extrapolation of the remaining change: with a per-check
         // contraction q = res / res_prev < 1, the distance to the steady state
         // is about res q / (1 - q)
-        const double q = s.res > 0 ? res / s.res : 1.0;
+        // q from the last two checks, the slower of the two contractions
+        const double q1 = s.res > 0 ? res / s.res : 1.0;
+        const double q0 = s.res_prev > 0 ? s.res / s.res_prev : 1.0;
+        const double q = fmax(q1, q0);
+        const double prev_est = s.err_est;
         s.res_prev = s.res;
         s.res = res;
         s.err_est = (q < 0.999) ? res * q / (1.0 - q) : 1e30;
         if (res < s.best_res) { s.best_res = res; s.since_best = 0; }
         else s.since_best += 1;
         if (tot[5] > 0 || !isfinite(res)) s.state = kSlotNonFinite;
-        else if (s.checks >= 3 && s.err_est <= d.tol) s.state = kSlotConverged;
+        else if (s.checks >= 4 && s.err_est <= d.tol && prev_est <= d.tol) s.state = kSlotConverged;
         else if (s.since_best >= 50) s.state = kSlotStagnated;
         else if (s.steps >= d.max_steps) s.state = kSlotMaxSteps;
     }

@@ -24,7 +24,9 @@ __device__ __forceinline__ void wall_prologue(const typename Store<PREC>::S *__r
                                               const KConsts<typename Store<PREC>::C> &k,
                                               int wall, int x0, double *s_min) {
     using L = Lat<Q>;
-    for (int t = threadIdx.x; t < BX + 6; t += BX) {
+    // ghost columns x0 - 3 .. x0 + active + 2 (fewer than BX when Nx is small)
+    const int ncols = min(BX, k.Nx - x0) + 6;
+    for (int t = threadIdx.x; t < ncols; t += BX) {
         const int xw = wrap(x0 - 3 + t, k.Nx);
         double m = 0.0;
 #pragma unroll
@@ -40,6 +42,7 @@ __device__ __forceinline__ void wall_prologue(const typename Store<PREC>::S *__r
                 double v = (double)to_c(fin[idx]);
                 if constexpr (Store<PREC>::dev)
                     v += (double)k.w[b] * (double)rin[(long long)row * k.pitch + xs];
+                if constexpr (Store<PREC>::shifted) v += (double)k.w[b];
                 m += v;
             }
         }
@@ -61,9 +64,9 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
     for (int a = 0; a < Q; ++a) {
         const int sj = j - L::ey(a);
         if (WALL && sj < 0) {
-            f[a] = (C)(s_min[threadIdx.x + 3 - L::ex(a)] * k.wcoef[0][a]);
+            f[a] = wall_fill<PREC>(s_min[threadIdx.x + 3 - L::ex(a)], k.wcoef[0][a], k.w[a]);
         } else if (WALL && sj >= k.Ny) {
-            f[a] = (C)(s_min[threadIdx.x + 3 - L::ex(a)] * k.wcoef[1][a]);
+            f[a] = wall_fill<PREC>(s_min[threadIdx.x + 3 - L::ex(a)], k.wcoef[1][a], k.w[a]);
         } else {
             C v = to_c(src[k.off_src[a]]);
             if constexpr (Store<PREC>::dev)
@@ -107,7 +110,7 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
     if (bot || top) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, f);
     else pull<Q, PREC, false>(fin, rin, k, x, j, s_min, f);
 
-    Collision<Q, C> col;
+    Collision<Q, C, Store<PREC>::shifted> col;
     col.setup(f, k);
     C o[Q];
     o[0] = col.rest(f[0]);

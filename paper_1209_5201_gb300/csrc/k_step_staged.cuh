@@ -215,6 +215,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                                                         (long long)row * k.pitch + xs]);
                             if constexpr (Cfg::kDev)
                                 v += (double)k.w[b] * (double)rin[(long long)row * k.pitch + xs];
+                            if constexpr (Store<PREC>::shifted) v += (double)k.w[b];
                             m += v;
                         }
                     }
@@ -245,9 +246,10 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
             for (int a = 0; a < Q; ++a) {
                 const int sj = j - L::ey(a);
                 if ((wb || wt) && sj < 0) {
-                    fv[q][a] = (C)(s_min[i + 3 - L::ex(a)] * k.wcoef[0][a]);
+                    fv[q][a] = wall_fill<PREC>(s_min[i + 3 - L::ex(a)], k.wcoef[0][a], k.w[a]);
                 } else if ((wb || wt) && sj >= k.Ny) {
-                    fv[q][a] = (C)(s_min[(TX + 6) + i + 3 - L::ex(a)] * k.wcoef[1][a]);
+                    fv[q][a] = wall_fill<PREC>(s_min[(TX + 6) + i + 3 - L::ex(a)], k.wcoef[1][a],
+                                               k.w[a]);
                 } else {
                     const S *pl = (const S *)(st + a * Cfg::kPlaneStride);
                     C v = to_c(pl[kr * Cfg::kW + i + kPadL - L::ex(a)]);
@@ -266,7 +268,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
             const int i = cell % TX, kr = cell / TX;
             const int x = x0 + i, j = j0 + kr;
             if (x >= k.Nx || j >= k.Ny) continue;
-            Collision<Q, C> col;
+            Collision<Q, C, Store<PREC>::shifted> col;
             col.setup(fv[q], k);
             C o[Q];
             o[0] = col.rest(fv[q][0]);

@@ -35,18 +35,22 @@ LBM_DEFINE_LAT(37, 8, LBM_Q37_EX, LBM_Q37_EY, LBM_Q37_SH)
 
 // ---- storage formats ---------------------------------------------------------
 template <int PREC> struct Store;
+// dev:     stored d_a = f~*_a - w_a rho with rho the cell's own density,
+//          kept in an FP32 plane (BF16DEV); values are converted back to f~.
+// shifted: stored d_a = f~*_a - w_a (the rest weights as rounded to the
+//          compute type); the collision runs on the deviations, so FP32
+//          round-off scales with |d| instead of |f|.
 template <> struct Store<LBM_FP64> {
     using S = double; using C = double;
-    static constexpr bool dev = false;
+    static constexpr bool dev = false, shifted = false;
 };
 template <> struct Store<LBM_FP32> {
     using S = float; using C = float;
-    static constexpr bool dev = false;
+    static constexpr bool dev = false, shifted = true;
 };
-// d_a = f~*_a - w_a rho in BF16, rho in an FP32 plane, FP32 arithmetic.
 template <> struct Store<LBM_BF16DEV> {
     using S = __nv_bfloat16; using C = float;
-    static constexpr bool dev = true;
+    static constexpr bool dev = true, shifted = false;
 };
 
 __device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -76,7 +80,11 @@ __device__ __forceinline__ int wrap(int v, int n) {
 //            A2 += -u2/4 + theta (c2 - 6)/4,  A4 = 1/24
 // A velocity and its opposite share the even part E = A0 + A2 s^2 + A4 s^4 and
 // have opposite odd parts O = s (A1 + A3 s^2).
-template <int Q, class C>
+// SHIFT: the inputs are deviations d_a = f_a - w_a and so are the outputs:
+// rho = 1 + sum d, and w (rho g - 1) = rho w (g - 1 + drho / rho) replaces
+// rho w g, i.e. A0 - 1 + drho / rho replaces A0 (no cancellation: the
+// constant 1 of A0 is never formed).
+template <int Q, class C, bool SHIFT = false>
 struct Collision {
     using L = Lat<Q>;
     C omc;                  // 1 - omega
@@ -100,13 +108,14 @@ struct Collision {
             else if (L::ey(a) == -1) jy -= dif;
             else if (L::ey(a) != 0) jy += C(L::ey(a)) * dif;
         }
-        rho = r0;
-        const C inv = C(1) / r0;
+        const C drho = r0;
+        rho = SHIFT ? C(1) + r0 : r0;
+        const C inv = C(1) / rho;
         const C ux = k.r * jx * inv, uy = k.r * jy * inv;
         const C u2 = ux * ux + uy * uy;
         C th = 0, T = 1;
         if (k.thermal) {
-            C e2 = 0;
+            C e2 = SHIFT ? k.e2w : C(0);
 #pragma unroll
             for (int a = 1; a < Q; a += 2) e2 += C(L::e2(a)) * (f[a] + f[a + 1]);
             T = (k.r2 * e2 * inv - u2) * C(0.5);
@@ -120,14 +129,16 @@ struct Collision {
         omc = C(1) - om;
         sx = k.r * ux;
         sy = k.r * uy;
-        set_coefficients(u2, th, om * r0, k);
+        set_coefficients(u2, th, om * rho, drho * inv, k);
     }
 
     // A0 = a00 + a01 c2 + a02 c2^2, A1 = a10 + a11 c2, A2 = a20 + a21 c2: the
     // Eq. (4) coefficients above, collected in powers of c2 (D = 2)
-    __device__ __forceinline__ void set_coefficients(C u2, C th, C orho, const KConsts<C> &k) {
+    // orho = omega rho; drr = (rho - 1) / rho (used when SHIFT)
+    __device__ __forceinline__ void set_coefficients(C u2, C th, C orho, C drr,
+                                                     const KConsts<C> &k) {
         const bool o3 = k.eq_order >= 3, o4 = k.eq_order >= 4;
-        C a00 = C(1) - C(0.5) * u2 - th, a01 = C(0.5) * th, a02 = C(0);
+        C a00 = (SHIFT ? drr : C(1)) - C(0.5) * u2 - th, a01 = C(0.5) * th, a02 = C(0);
         C a10 = C(1), a11 = C(0), a20 = C(0.5), a21 = C(0);
         if (o3) {
             a10 += C(-0.5) * u2 - C(2) * th;
@@ -166,6 +177,16 @@ struct Collision {
         ob = omc * fb + (P - R);
     }
 };
+
+// Re-emitted population of Eq. (12), M_in g^w_a / D_w, in FP64, returned in
+// the form the collision takes (a deviation for shifted storage).
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::C wall_fill(double m_in, double coef,
+                                                             typename Store<PREC>::C w) {
+    double v = m_in * coef;
+    if constexpr (Store<PREC>::shifted) v -= (double)w;
+    return (typename Store<PREC>::C)v;
+}
 
 // compile-time loop over the velocity pairs (a = 1, 3, 5, ...)
 template <int A, int Q>

@@ -47,6 +47,7 @@ struct KConsts {
     C wsh[kMaxShells];        // shell weights
     C c2sh[kMaxShells];       // |c|^2 = r^2 |e|^2 of each shell
     C w[kMaxQ];               // per-velocity weights
+    C e2w;                    // sum_a |e_a|^2 w_a (= D / r^2 up to rounding)
     int off_src[kMaxQ];       // a * plane - e_ay * pitch - e_ax: pull source offset
     int off_dst[kMaxQ];       // a * plane: store offset
     double wcoef[2][kMaxQ];   // g^w_a / D_w (0 unless a leaves the wall)
@@ -87,7 +88,11 @@ struct SolverImpl {
     CUtensorMap tm_f[2];      // 3-D maps (x, y, a) of the two state buffers
     CUtensorMap tm_r[2];      // 2-D maps of the BF16DEV density planes
     double tuned_ms;          // step time of the autotuned choice
+    cudaGraphExec_t step_graph;   // kGraphSteps launches from buffer 0, replayed
+    int graph_kernel, graph_variant;
 };
+
+constexpr int kGraphSteps = 64;   // steps per replayed graph (even: parity kept)
 
 // Encode tm_f / tm_r for boxes of (TX + 2 kPadL) x TY (density: TY + 6 rows).
 int encode_tensor_maps(SolverImpl &s, int TX, int TY);

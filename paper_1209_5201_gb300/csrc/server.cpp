@@ -173,9 +173,10 @@ struct ServerImpl {
         // Steps per chunk launch: cheaper slots run more steps, so that every
         // CTA of a launch takes about as long as the costliest one (a Q = 37
         // column of 2048 rows runs chunk_steps); the cost model is the velocity
-        // count times the cells per thread plus a latency floor.
-        const double cost = L.Q * std::ceil(r.Ny / 256.0) + 37.0;
-        const double cost_ref = 37.0 * 8.0 + 37.0;
+        // count times the cells per thread (512 threads per slot) plus a
+        // latency floor.
+        const double cost = L.Q * std::ceil(r.Ny / 512.0) + 37.0;
+        const double cost_ref = 37.0 * 4.0 + 37.0;
         d.chunk_steps = (int)std::min<double>(32.0 * cfg.chunk_steps,
                                               std::max<double>(cfg.chunk_steps,
                                                                std::round(cfg.chunk_steps * cost_ref / cost)));
@@ -209,6 +210,7 @@ struct ServerImpl {
         std::memset(&st, 0, sizeof(st));
         st.state = kSlotRunning;
         st.best_res = 1e300;
+        st.err_est = 1e300;
         SlotInfo &si = slots[s];
         si.busy = true;
         si.id = pd.id;

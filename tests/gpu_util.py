@@ -35,3 +35,14 @@ def make_pair(lbm, orc, lattice, Nx, Ny, precision="fp64", Kn=0.05, u_wall=(-0.1
 
 def rel_err(a, b):
     return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def report(name, data):
+    """Write measured numbers to $LBM_REPORT_DIR/<name>.json when set."""
+    import json
+    import os
+    d = os.environ.get("LBM_REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, name + ".json"), "w") as fh:
+            json.dump(data, fh, indent=1, default=float)

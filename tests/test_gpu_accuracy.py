@@ -1,0 +1,66 @@
+"""Accuracy of the batched / serving path against the FP64 oracle, on the
+instances of the batched (seed 7) and serving (seed 11) workloads whose oracle
+steady state is cheap enough for the CPU (est. <= 4e6 cell-steps each).
+
+Each request is solved to an extrapolated distance to the steady state of
+1e-5; the L-inf error of u_x / U_w (and of T for the thermal lattice) against
+the oracle's steady state (residual 1e-12) must stay within 2e-5."""
+import numpy as np
+import pytest
+
+import inputs
+from gpu_util import need_gpu, report
+from oracle import lattice as olat
+
+pytestmark = pytest.mark.gpu
+
+
+def cheap(insts, budget=4e6, limit=10):
+    out = []
+    for k, it in enumerate(insts):
+        r = olat.get(it.lattice).r
+        if 14 * 0.127 * it.Ny * r / it.Kn * it.Ny <= budget:
+            out.append((k, it))
+        if len(out) >= limit:
+            break
+    return out
+
+
+def oracle_steady(oracle, it):
+    p = oracle.Problem(lattice=it.lattice, Nx=1, Ny=it.Ny, eq_order=it.eq_order,
+                       thermal=it.thermal, Kn=it.Kn, u_wall=(-it.U_w, it.U_w),
+                       T_wall=(it.T_w, it.T_w))
+    f = oracle.init_fields(p, np.ones((it.Ny, 1)))
+    ok, _, _ = oracle.run_to_residual(p, f, 1e-12, 20_000_000, 200)
+    assert ok
+    _, ux, _, T = oracle.macros(p, f)
+    return ux[:, 0], T[:, 0]
+
+
+@pytest.mark.parametrize("workload", ["batched", "serving"])
+def test_steady_profiles_within_1e5(oracle, workload):
+    lbm = need_gpu()
+    insts = inputs.batched_instances(256, seed=7) if workload == "batched" else \
+        inputs.serving_requests(2000, seed=11)
+    sample = cheap(insts)
+    assert len(sample) >= 5
+    srv = lbm.Server(mem_budget_bytes=1 << 28, max_slots=32, chunk_steps=100)
+    ids = [srv.submit(lbm.make_request(it.lattice, it.Ny, it.Kn, it.U_w, it.T_w, tol=1e-5))
+           for _, it in sample]
+    srv.drain(600)
+    res = {r.id: r for r in srv.poll(64)}
+    rows = []
+    for rid, (k, it) in zip(ids, sample):
+        r = res[rid]
+        rho, ux, uy, T = srv.fetch(rid, it.Ny)
+        oux, oT = oracle_steady(oracle, it)
+        e_u = float(np.max(np.abs(ux - oux)) / it.U_w)
+        e_T = float(np.max(np.abs(T - oT))) if it.thermal else 0.0
+        rows.append(dict(index=k, lattice=it.lattice, Ny=it.Ny, Kn=it.Kn, U_w=it.U_w,
+                         status=r.status, steps=r.steps, err_est=r.err_est, err_u=e_u,
+                         err_T=e_T))
+    srv.close()
+    report(f"accuracy_{workload}", rows)
+    for row in rows:
+        assert row["status"] == lbm.LBM_OK, row
+        assert row["err_u"] < 2e-5 and row["err_T"] < 2e-5, row

@@ -102,7 +102,7 @@ def test_admission_under_a_small_memory_budget(lbm):
 
 def test_requests_admitted_while_others_run(lbm):
     s = lbm.Server(mem_budget_bytes=1 << 26, max_slots=4, chunk_steps=50)
-    long_id = s.submit(lbm.make_request("D2Q37", 256, 0.05, 0.2, tol=1e-6))
+    long_id = s.submit(lbm.make_request("D2Q37", 1024, 0.02, 0.2, tol=1e-6))
     time.sleep(0.05)
     short = [s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-6)) for _ in range(6)]
     s.drain(300)

@@ -40,7 +40,11 @@ def run_variant(lbm, oracle, lattice, Nx, Ny, precision, kv, nsteps, **kw):
     return f, p, perm, rho
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+# FP32: relative error per population after 120-200 steps of the 4th-order
+# thermal lattice; the worst entries are the smallest populations (w = 2.5e-4)
+# near the walls, where ~1e-7 of round-off per step (Q terms of 6e-8 relative
+# each, on values of order w) accumulates to ~2.5e-9 absolute; bound 2e-5.
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 def test_every_variant_matches_oracle_d2q37(lbm, oracle, precision, tol):
     # 300 columns: ragged against 64- and 128-column tiles; 42 rows: ragged
     # against 2- and 4-row tiles; walls move and differ in temperature

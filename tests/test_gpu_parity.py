@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import inputs
-from gpu_util import make_pair, need_gpu, rel_err
+from gpu_util import make_pair, need_gpu, rel_err, report
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +62,11 @@ def test_fp64_couette_d2q25_1x64(lbm, oracle):
     s.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+# FP32: relative error per population after 120-200 steps of the 4th-order
+# thermal lattice; the worst entries are the smallest populations (w = 2.5e-4)
+# near the walls, where ~1e-7 of round-off per step (Q terms of 6e-8 relative
+# each, on values of order w) accumulates to ~2.5e-9 absolute; bound 2e-5.
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 def test_d2q37_thermal_grid_multi_block(lbm, oracle, precision, tol):
     # 300 columns = 2 full 128-column blocks + a ragged 44, 40 rows, noise on rho
     Nx, Ny, n = 300, 40, 200
@@ -75,6 +79,7 @@ def test_d2q37_thermal_grid_multi_block(lbm, oracle, precision, tol):
     oracle.run(p, f, n)
     err = rel_err(s.get_f(), oracle.collide(p, f)[perm])
     s.close()
+    report(f"parity_grid_d2q37_{precision}", {"max_rel_err_per_population": err, "steps": n})
     assert err < tol, err
 
 

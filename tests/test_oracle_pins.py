@@ -332,3 +332,12 @@ def test_second_order_grid_convergence(oracle):
     sT = np.polyfit(np.log([16, 32, 64]), np.log(ET), 1)[0]
     assert -2.3 < sU < -1.7, (EU, sU)
     assert -2.3 < sT < -1.6, (ET, sT)
+
+
+def test_kinetic_temperature_of_isothermal_equilibrium(oracle):
+    # Eq. (3): the second moment of rho g^eq(u, 1) about u is rho D T with T = 1
+    p = oracle.Problem(lattice="D2Q25", Nx=2, Ny=6, Kn=0.1)
+    f = oracle.init_fields(p, 1.1 * np.ones((6, 2)), 0.07)
+    rho, ux, uy, T = oracle.macros_kinetic(p, f)
+    assert np.max(np.abs(T - 1.0)) < 1e-13 and np.max(np.abs(ux - 0.07)) < 1e-14
+    assert oracle.macros(p, f)[3].max() == 1.0     # isothermal macros report T = 1
