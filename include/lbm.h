@@ -227,6 +227,35 @@ int lbm_solver_autotune(lbm_solver *s, int32_t trial_steps, int32_t *kernel,
  * N ghost layers (Sec. III).  Synchronous. */
 int lbm_solver_wall_mass(lbm_solver *s, double *m_in);
 
+/* ---- residual reduction without allocation -------------------------------
+ * The paper has no counterpart to this call: it is a service of the library.
+ * It computes the steady-state residual that lbm_solver_run_to_residual
+ * checks,
+ *   res = max( ||ux - ux_prev||_2 / ||ux||_2 ,
+ *              thermal: ||T - T_prev||_2 / ||T - T_ref||_2 ),
+ * on caller-owned device arrays of n FP64 values, writes res to the device
+ * double *res (NaN if any value is not finite), and then copies ux into
+ * ux_prev and T into T_prev, as the solver does at each check.  All pointers
+ * are device pointers; the work is enqueued on `stream` (asynchronous).
+ *
+ * It allocates nothing, for callers that cannot: code running while a CUDA
+ * stream is being captured into a graph (where allocation calls are not
+ * allowed), hosts that hand the whole device memory to another allocator or
+ * run under a fixed memory budget, and embedding frameworks that forbid
+ * libraries from allocating on their own.  Its scratch (1024 block partials
+ * of 5 FP64 sums plus the totals, 41 KB) is a file-scope device array of the
+ * library, created on every GPU that loads the library and kept until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with that device current); make this first
+ * call before any stream capture begins.  All calls on a device share the
+ * array and it keeps the last call's contents: calls whose kernels overlap on
+ * the GPU (different streams, no ordering between them) race and return
+ * garbage; calls ordered on one stream are safe.
+ * Errors: LBM_EINVAL for a NULL pointer or n outside [1, 2^31 - 1] (nothing
+ * is launched), LBM_ECUDA if the address look-up or a launch fails. */
+int lbm_residual_noalloc(const double *ux, const double *T, double *ux_prev, double *T_prev,
+                         int64_t n, double T_ref, int32_t thermal, double *res, void *stream);
+
 /* ---- batched steady-state solves and the continuous-batching server ------
  * Each request is one steady Couette solve on a single periodic column
  * (Nx = 1) between the paper's two diffuse walls (Sec. IV set-up): its own

@@ -124,6 +124,8 @@ _SIGS = {
     "lbm_server_destroy": ([_VP], C.c_int),
     "lbm_batch_solve": ([C.POINTER(lbm_server_cfg), _VP, C.POINTER(lbm_request), C.c_int32,
                          C.POINTER(lbm_result), C.c_double], C.c_int),
+    "lbm_residual_noalloc": ([_VP, _VP, _VP, _VP, C.c_int64, C.c_double, C.c_int32, _VP, _VP],
+                             C.c_int),
 }
 
 
@@ -389,6 +391,19 @@ def lbm_batch_solve(cfg: lbm_server_cfg, reqs, stream: int = 0, timeout_s: float
     _check(load().lbm_batch_solve(C.byref(cfg), _VP(stream or None), arr, len(reqs), out,
                                   float(timeout_s)), "lbm_batch_solve")
     return [out[i] for i in range(len(reqs))]
+
+
+def _devptr(a) -> int:
+    return a.data_ptr() if hasattr(a, "data_ptr") else int(a)
+
+
+def lbm_residual_noalloc(ux, T, ux_prev, T_prev, n: int, T_ref: float, thermal: bool, res,
+                         stream: int = 0) -> None:
+    """Device arrays (torch tensors or raw pointers); see include/lbm.h."""
+    _check(load().lbm_residual_noalloc(_VP(_devptr(ux)), _VP(_devptr(T)), _VP(_devptr(ux_prev)),
+                                       _VP(_devptr(T_prev)), int(n), float(T_ref), int(thermal),
+                                       _VP(_devptr(res)), _VP(stream or None)),
+           "lbm_residual_noalloc")
 
 
 def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
