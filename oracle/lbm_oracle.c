@@ -57,6 +57,8 @@ typedef struct {
     double mu_exp;      /* viscosity law mu = T^mu_exp */
     double u_wall[2];   /* x-velocity of the bottom (y=0) and top (y=1) wall */
     double T_wall[2];   /* temperature of the bottom and top wall */
+    double accom[2];    /* accommodation of the scattering kernel per wall:
+                           R = accom R_D + (1 - accom) R_S (1: diffuse) */
 } orc_params;
 
 typedef struct {
@@ -231,12 +233,29 @@ static int orc_one_step(const orc_lattice *L, const orc_params *P, double *f,
                         m_in += ext[a * eplane + (long)(grow + N) * Nx + xw];
             }
             tot_in[wall] += m_in;
-            /* Eq. (12): same f^O on every layer the velocity leaves from. */
+            /* Eq. (9) with R = accom R_D + (1 - accom) R_S.  R_D is Eq. (11),
+             * giving Eq. (12): the same diffuse f^O on every layer the velocity
+             * leaves from.  R_S (specular) sends the incoming population of
+             * the mirrored velocity (e_x, -e_y) at the same ghost node and
+             * layer to the outgoing velocity.  Both satisfy Eq. (10). */
+            const double acc = P->accom[wall];
+            double fspec[64 * 3];
+            for (int l = 0; l < N; ++l) {
+                int grow = wall == 0 ? -1 - l : Ny + l;
+                for (int a = 0; a < Q; ++a) {
+                    fspec[a * N + l] = 0.0;
+                    if (!(nsgn * L->ey[a] > l)) continue;
+                    for (int b = 0; b < Q; ++b)
+                        if (L->ex[b] == L->ex[a] && L->ey[b] == -L->ey[a])
+                            fspec[a * N + l] = ext[b * eplane + (long)(grow + N) * Nx + xw];
+                }
+            }
             for (int l = 0; l < N; ++l) {
                 int grow = wall == 0 ? -1 - l : Ny + l;
                 for (int a = 0; a < Q; ++a) {
                     if (!(nsgn * L->ey[a] > l)) continue;   /* outgoing */
-                    double fo = m_in * gw[wall][a] / den[wall];
+                    double fo = acc * (m_in * gw[wall][a] / den[wall]) +
+                                (1.0 - acc) * fspec[a * N + l];
                     tot_out[wall] += fo;
                     int tj = grow + L->ey[a];
                     int tx = ((xw + L->ex[a]) % Nx + Nx) % Nx;
@@ -270,7 +289,7 @@ static int orc_one_step(const orc_lattice *L, const orc_params *P, double *f,
 int orc_run(const orc_lattice *L, const orc_params *P, double *f, long nsteps,
             orc_wallstats *st)
 {
-    if (L->Q > 64 || P->Nx < 1 || P->Ny < 1) return -3;
+    if (L->Q > 64 || P->Nx < 1 || P->Ny < 1 || orc_ghost_depth(L) > 3) return -3;
     const int N = orc_ghost_depth(L);
     const long plane = (long)P->Nx * P->Ny;
     double *ext = malloc(sizeof(double) * (long)P->Nx * (P->Ny + 2 * N) * L->Q);

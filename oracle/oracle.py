@@ -40,7 +40,7 @@ class _Params(C.Structure):
     _fields_ = [("Nx", C.c_int), ("Ny", C.c_int), ("eq_order", C.c_int),
                 ("thermal", C.c_int), ("Kn", C.c_double), ("tau", C.c_double),
                 ("mu_exp", C.c_double), ("u_wall", C.c_double * 2),
-                ("T_wall", C.c_double * 2)]
+                ("T_wall", C.c_double * 2), ("accom", C.c_double * 2)]
 
 
 class _WallStats(C.Structure):
@@ -95,6 +95,7 @@ class Problem:
     mu_exp: float = 1.0
     u_wall: tuple = (-0.1, 0.1)
     T_wall: tuple = (1.0, 1.0)
+    accom: tuple = (1.0, 1.0)
     lat: _lat.OracleLattice = field(init=False, repr=False)
 
     def __post_init__(self):
@@ -107,7 +108,7 @@ class Problem:
                             self._ey.ctypes.data_as(ip), _dp(self._w), float(self.lat.r))
         self._cp = _Params(self.Nx, self.Ny, self.eq_order, int(self.thermal), self.Kn,
                            self.tau, self.mu_exp, (C.c_double * 2)(*self.u_wall),
-                           (C.c_double * 2)(*self.T_wall))
+                           (C.c_double * 2)(*self.T_wall), (C.c_double * 2)(*self.accom))
 
     @property
     def Q(self) -> int:

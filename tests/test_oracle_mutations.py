@@ -49,6 +49,11 @@ MUTATIONS = {
         "double Cx = L->r * L->ex[a] - u, Cy = L->r * L->ey[a] - v;",
         "double Cx = L->r * L->ex[a], Cy = L->r * L->ey[a];",
         lambda o: pins.test_moments_recover_fields(o)),
+    # specular kernel reversing both components (bounce-back) instead of mirroring e_y
+    "specular_is_bounce_back": (
+        "if (L->ex[b] == L->ex[a] && L->ey[b] == -L->ey[a])",
+        "if (L->ex[b] == -L->ex[a] && L->ey[b] == -L->ey[a])",
+        lambda o: pins.test_specular_walls_exchange_no_tangential_momentum(o)),
     # wall distribution evaluated at the wrong wall's velocity
     "wall_velocity_swapped": (
         "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[wall], 0.0, Tw, gw);",

@@ -341,3 +341,64 @@ def test_kinetic_temperature_of_isothermal_equilibrium(oracle):
     rho, ux, uy, T = oracle.macros_kinetic(p, f)
     assert np.max(np.abs(T - 1.0)) < 1e-13 and np.max(np.abs(ux - 0.07)) < 1e-14
     assert oracle.macros(p, f)[3].max() == 1.0     # isothermal macros report T = 1
+
+
+# --------------------------------------------------------------------------
+# General scattering kernel (Sec. III, Eq. (9)-(10)) as Maxwell's model
+# R = accom R_D + (1 - accom) R_S, R_S the specular kernel.
+
+def test_specular_walls_exchange_no_tangential_momentum(oracle):
+    # specular reflection keeps c_x: moving walls cannot set a gas at rest moving
+    p = oracle.Problem(lattice="D2Q37", Nx=3, Ny=12, eq_order=4, thermal=True, Kn=0.05,
+                       u_wall=(-0.3, 0.2), T_wall=(1.1, 0.9), accom=(0.0, 0.0))
+    f = oracle.init_fields(p, inputs.rho_field(3, 12, 1e-2, seed=4))
+    c = p.lat.r * p.lat.e.astype(np.float64)
+    px0 = float(np.tensordot(c[:, 0], f, 1).sum())
+    m0 = f.sum()
+    for _ in range(4):
+        st = oracle.run(p, f, 25, stats=True)
+        assert st["holes_unfilled"] == 0 and st["slots_doubled"] == 0
+    assert abs(float(np.tensordot(c[:, 0], f, 1).sum()) - px0) < 1e-13
+    assert abs(f.sum() - m0) < 1e-13 * m0
+
+
+@pytest.mark.parametrize("accom", [0.0, 0.3, 0.7])
+def test_partial_accommodation_conserves_mass_per_step(oracle, accom):
+    p = oracle.Problem(lattice="D2Q25", Nx=5, Ny=10, Kn=0.1, u_wall=(-0.2, 0.1),
+                       accom=(accom, 1.0 - accom / 2))
+    f = oracle.init_fields(p, inputs.rho_field(5, 10, 0.05, seed=2))
+    m0 = f.sum()
+    for _ in range(3):
+        st = oracle.run(p, f, 10, stats=True)
+        for w in (0, 1):
+            assert abs(st["m_in"][w] - st["m_out"][w]) <= 1e-14 * st["m_in"][w]
+    assert abs(f.sum() - m0) <= 1e-13 * m0
+
+
+def test_full_accommodation_is_the_diffuse_wall(oracle):
+    kw = dict(lattice="D2Q17", Nx=4, Ny=9, Kn=0.07, u_wall=(-0.1, 0.15))
+    a = oracle.Problem(**kw)
+    b = oracle.Problem(**kw, accom=(1.0, 1.0))
+    fa = oracle.init_fields(a, inputs.rho_field(4, 9, 0.01, seed=1))
+    fb = fa.copy()
+    oracle.run(a, fa, 30)
+    oracle.run(b, fb, 30)
+    assert np.array_equal(fa, fb)
+
+
+def test_maxwell_slip_length(oracle):
+    # first-order Maxwell slip: slip length Kn (2 - accom) / accom, so
+    # U = (2y - 1) U_w / (1 + 2 Kn (2 - accom) / accom)  (Eq. (13) at accom = 1)
+    Ny, Uw, Kn, acc = 32, 0.05, 0.01, 0.5
+    p = oracle.Problem(lattice="D2Q37", Nx=1, Ny=Ny, eq_order=4, thermal=True, Kn=Kn,
+                       u_wall=(-Uw, Uw), accom=(acc, acc))
+    f = oracle.init_fields(p, np.ones((Ny, 1)))
+    ok, _, _ = oracle.run_to_residual(p, f, 1e-11, 500000, 100)
+    assert ok
+    ux = oracle.macros(p, f)[1][:, 0]
+    y = (np.arange(Ny) + 0.5) / Ny
+    ref = (2 * y - 1) * Uw / (1 + 2 * Kn * (2 - acc) / acc)
+    assert np.max(np.abs(ux - ref)) / Uw < 0.02
+    # and the diffuse-wall profile is measurably different (less slip)
+    diffuse = (2 * y - 1) * Uw / (1 + 2 * Kn)
+    assert np.max(np.abs(ux - diffuse)) / Uw > 0.03
