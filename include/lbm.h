@@ -111,10 +111,16 @@ typedef struct lbm_params {
     double rho0;         /* initial density of lbm_solver_init                 */
     double noise_amp;    /* initial rho = rho0 (1 + noise_amp (2U - 1))        */
     uint64_t seed;       /* U = SplitMix64 draw at counter j*Nx + x            */
+    double accom[2];     /* accommodation per wall (bottom, top) of the
+                            scattering kernel R = a R_D + (1 - a) R_S of Sec.
+                            III, Eq. (9)-(10): 1 = diffuse (Eq. (11)-(12)),
+                            0 = specular (the incoming population of the
+                            mirrored velocity at the same ghost node), in [0, 1] */
 } lbm_params;
 
 /* Defaults: Nx = 1, Ny = 64, eq_order 2, isothermal, Kn 0.1, tau 0, mu_exp 1,
- * walls -0.1 / +0.1 at T 1, FP64, AUTO kernel, rho0 1, no noise, seed 7. */
+ * walls -0.1 / +0.1 at T 1, FP64, AUTO kernel, rho0 1, no noise, seed 7,
+ * diffuse walls (accom 1). */
 void lbm_params_default(lbm_params *p);
 
 /* ---- single-domain solver ----------------------------------------------- */
@@ -266,8 +272,10 @@ int lbm_residual_noalloc(const double *ux, const double *T, double *ux_prev, dou
  * relative change over one check, max(||u_x - u_x'|| / ||u_x||, thermal:
  * ||T - T'|| / ||T||), and q the ratio of successive residuals; checks run
  * about four times per e-folding time of the slowest shear mode,
- * 0.127 Ny r / Kn steps.  A request whose residual has not improved for 50
- * checks (the FP32 round-off floor) ends with LBM_ENOTCONVERGED. */
+ * 0.127 Ny r / Kn steps.  A residual that has stopped improving for 8 checks
+ * at no more than tol / 20 also counts as converged (the FP32 round-off
+ * floor); one that has not improved for 50 checks above that ends the request
+ * with LBM_ENOTCONVERGED. */
 typedef struct lbm_request {
     int32_t lattice;      /* LBM_LATTICE_*                                     */
     int32_t Ny;           /* rows, 6 <= Ny <= 8192                             */
@@ -281,6 +289,7 @@ typedef struct lbm_request {
     double tol;           /* target distance to the steady state, e.g. 1e-5    */
     int64_t max_steps;    /* give up after this many steps                     */
     uint64_t tag;         /* caller's tag, returned in the result              */
+    double accom[2];      /* wall accommodation, as in lbm_params (1: diffuse) */
 } lbm_request;
 
 typedef struct lbm_result {

@@ -71,6 +71,10 @@ int check_params(const LatticeHost &L, const lbm_params &p) {
     if (p.thermal && (p.T_wall[0] <= 0 || p.T_wall[1] <= 0)) { set_error("T_wall must be > 0"); return LBM_EINVAL; }
     if (!(p.rho0 > 0)) { set_error("rho0 must be > 0"); return LBM_EINVAL; }
     if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_STAGED) { set_error("bad kernel"); return LBM_EINVAL; }
+    if (!(p.accom[0] >= 0 && p.accom[0] <= 1 && p.accom[1] >= 0 && p.accom[1] <= 1)) {
+        set_error("accom must lie in [0, 1]");
+        return LBM_EINVAL;
+    }
     return LBM_OK;
 }
 
@@ -181,6 +185,13 @@ void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int p
     double e2w = 0;
     for (int a = 0; a < L.Q; ++a) e2w += (double)(C)L.w[a] * (L.ex[a] * L.ex[a] + L.ey[a] * L.ey[a]);
     k.e2w = (C)e2w;
+    for (int a = 0; a < L.Q; ++a) {
+        k.mirror[a] = a;
+        for (int b = 0; b < L.Q; ++b)
+            if (L.ex[b] == L.ex[a] && L.ey[b] == -L.ey[a]) k.mirror[a] = b;
+    }
+    k.accom[0] = p.accom[0];
+    k.accom[1] = p.accom[1];
     // Eq. (11)-(12): g^w_a / sum_{l<N} sum_{e.n>l} g^w = g^w_a / sum_{e.n>0} |e.n| g^w
     for (int wall = 0; wall < 2; ++wall) {
         double g[kMaxQ];
@@ -326,6 +337,7 @@ void lbm_params_default(lbm_params *p) {
     p->rho0 = 1.0;
     p->noise_amp = 0.0;
     p->seed = 7;
+    p->accom[0] = p->accom[1] = 1.0;
 }
 
 int lbm_solver_required_bytes(const lbm_lattice *lat, const lbm_params *p, size_t *bytes) {

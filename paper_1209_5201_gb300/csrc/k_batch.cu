@@ -5,7 +5,7 @@
 
 namespace lbm {
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 256;
 
 // A slot descriptor is used only if its buffers lie inside the pool; a bad
 // one is recorded in dbg[0..7] (code, slot, Q, Ny, f_off, prev_off, chunk,
@@ -19,7 +19,10 @@ __device__ __forceinline__ bool desc_ok(const SlotDesc &d, long long pool_elems,
         for (int l = 0; l < d.nterm; ++l)
             terms_ok = terms_ok && d.term_a[w][l] >= 0 && d.term_a[w][l] < d.Q &&
                        d.term_row[w][l] >= 0 && d.term_row[w][l] < 3;
-    const bool ok = q_ok && terms_ok && d.Ny >= 6 && d.Ny <= 8192 && d.f_off >= 0 &&
+    bool mirror_ok = true;
+    for (int a = 0; a < d.Q && q_ok; ++a)
+        mirror_ok = mirror_ok && d.k.mirror[a] >= 0 && d.k.mirror[a] < d.Q;
+    const bool ok = q_ok && terms_ok && mirror_ok && d.Ny >= 6 && d.Ny <= 8192 && d.f_off >= 0 &&
                     d.f_off + need <= pool_elems && d.prev_off == d.f_off + 2LL * d.Q * d.Ny &&
                     (d.cur == 0 || d.cur == 1) && d.chunk_steps >= 1 && d.check_every >= 1;
     if (!ok && threadIdx.x == 0 && atomicCAS(dbg, 0, code) == 0) {
@@ -42,7 +45,7 @@ __device__ __forceinline__ void load_desc(const SlotDesc *g, SlotDesc *s) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 1)
+__global__ void __launch_bounds__(kBatchThreads, 2)
 k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
               float *__restrict__ pool, int chunk, long long pool_elems, int *dbg) {
     __shared__ SlotDesc sd;

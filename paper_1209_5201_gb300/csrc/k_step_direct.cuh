@@ -63,10 +63,12 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int sj = j - L::ey(a);
-        if (WALL && sj < 0) {
-            f[a] = wall_fill<PREC>(s_min[threadIdx.x + 3 - L::ex(a)], k.wcoef[0][a], k.w[a]);
-        } else if (WALL && sj >= k.Ny) {
-            f[a] = wall_fill<PREC>(s_min[threadIdx.x + 3 - L::ex(a)], k.wcoef[1][a], k.w[a]);
+        if (WALL && (sj < 0 || sj >= k.Ny)) {
+            const int wall = sj < 0 ? 0 : 1;
+            const C spec = k.accom[wall] != 1.0
+                               ? specular_source<PREC>(fin, rin, k, a, L::ex(a), x, j) : C(0);
+            f[a] = wall_mix<PREC>(s_min[threadIdx.x + 3 - L::ex(a)], k.wcoef[wall][a], k.w[a],
+                                  k.accom[wall], spec);
         } else {
             C v = to_c(src[k.off_src[a]]);
             if constexpr (Store<PREC>::dev)

@@ -245,11 +245,13 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const int sj = j - L::ey(a);
-                if ((wb || wt) && sj < 0) {
-                    fv[q][a] = wall_fill<PREC>(s_min[i + 3 - L::ex(a)], k.wcoef[0][a], k.w[a]);
-                } else if ((wb || wt) && sj >= k.Ny) {
-                    fv[q][a] = wall_fill<PREC>(s_min[(TX + 6) + i + 3 - L::ex(a)], k.wcoef[1][a],
-                                               k.w[a]);
+                if ((wb || wt) && (sj < 0 || sj >= k.Ny)) {
+                    const int wall = sj < 0 ? 0 : 1;
+                    const C spec = (k.accom[wall] != 1.0 && x0 + i < k.Nx && j < k.Ny)
+                                       ? specular_source<PREC>(fin, rin, k, a, L::ex(a), x0 + i, j)
+                                       : C(0);
+                    fv[q][a] = wall_mix<PREC>(s_min[wall * (TX + 6) + i + 3 - L::ex(a)],
+                                              k.wcoef[wall][a], k.w[a], k.accom[wall], spec);
                 } else {
                     const S *pl = (const S *)(st + a * Cfg::kPlaneStride);
                     C v = to_c(pl[kr * Cfg::kW + i + kPadL - L::ex(a)]);

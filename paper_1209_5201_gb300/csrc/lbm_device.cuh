@@ -188,6 +188,33 @@ __device__ __forceinline__ typename Store<PREC>::C wall_fill(double m_in, double
     return (typename Store<PREC>::C)v;
 }
 
+// Eq. (9) with R = accom R_D + (1 - accom) R_S: the diffuse re-emission mixed
+// with the specular one, `spec` being the mirrored population in the form the
+// collision takes (a deviation for shifted storage; the mirror shares w_a).
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::C wall_mix(double m_in, double coef,
+                                                            typename Store<PREC>::C w,
+                                                            double accom,
+                                                            typename Store<PREC>::C spec) {
+    using C = typename Store<PREC>::C;
+    const C diffuse = wall_fill<PREC>(m_in, coef, w);
+    return accom == 1.0 ? diffuse : (C)(accom * (double)diffuse + (1.0 - accom) * (double)spec);
+}
+
+// Specular partner of velocity a for fluid cell (x, j) next to a wall: the
+// mirrored velocity b = (e_x, -e_y) reaching the ghost node from which a leaves
+// came from the same row, 2 e_x columns back (periodic), in the collision's form.
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::C
+specular_source(const typename Store<PREC>::S *__restrict__ fin, const float *__restrict__ rin,
+                const KConsts<typename Store<PREC>::C> &k, int a, int ex, int x, int j) {
+    const int b = k.mirror[a];
+    const long long ro = (long long)j * k.pitch + wrap(x - 2 * ex, k.Nx) + kPadL;
+    auto v = to_c(fin[(long long)b * k.plane + ro]);
+    if constexpr (Store<PREC>::dev) v += k.w[b] * rin[ro];
+    return v;
+}
+
 // compile-time loop over the velocity pairs (a = 1, 3, 5, ...)
 template <int A, int Q>
 struct PairLoop {

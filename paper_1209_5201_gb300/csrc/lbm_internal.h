@@ -50,6 +50,8 @@ struct KConsts {
     C e2w;                    // sum_a |e_a|^2 w_a (= D / r^2 up to rounding)
     int off_src[kMaxQ];       // a * plane - e_ay * pitch - e_ax: pull source offset
     int off_dst[kMaxQ];       // a * plane: store offset
+    int mirror[kMaxQ];        // velocity with (e_x, -e_y): specular partner
+    double accom[2];          // wall accommodation (1: diffuse)
     double wcoef[2][kMaxQ];   // g^w_a / D_w (0 unless a leaves the wall)
 };
 

@@ -164,6 +164,8 @@ struct ServerImpl {
         p.u_wall[1] = r.u_wall[1];
         p.T_wall[0] = r.T_wall[0];
         p.T_wall[1] = r.T_wall[1];
+        p.accom[0] = r.accom[0];
+        p.accom[1] = r.accom[1];
         p.precision = LBM_FP32;
         SlotDesc &d = h_desc[s];
         std::memset(&d, 0, sizeof(d));
@@ -173,10 +175,10 @@ struct ServerImpl {
         // Steps per chunk launch: cheaper slots run more steps, so that every
         // CTA of a launch takes about as long as the costliest one (a Q = 37
         // column of 2048 rows runs chunk_steps); the cost model is the velocity
-        // count times the cells per thread (512 threads per slot) plus a
+        // count times the cells per thread (256 threads per slot) plus a
         // latency floor.
-        const double cost = L.Q * std::ceil(r.Ny / 512.0) + 37.0;
-        const double cost_ref = 37.0 * 4.0 + 37.0;
+        const double cost = L.Q * std::ceil(r.Ny / 256.0) + 37.0;
+        const double cost_ref = 37.0 * 8.0 + 37.0;
         d.chunk_steps = (int)std::min<double>(32.0 * cfg.chunk_steps,
                                               std::max<double>(cfg.chunk_steps,
                                                                std::round(cfg.chunk_steps * cost_ref / cost)));
@@ -423,6 +425,10 @@ static int check_request(const lbm_request *r) {
     }
     if (r->thermal && (r->T_wall[0] <= 0 || r->T_wall[1] <= 0)) { set_error("T_wall <= 0"); return LBM_EINVAL; }
     if (r->max_steps < 1) { set_error("max_steps < 1"); return LBM_EINVAL; }
+    if (!(r->accom[0] >= 0 && r->accom[0] <= 1 && r->accom[1] >= 0 && r->accom[1] <= 1)) {
+        set_error("accom must lie in [0, 1]");
+        return LBM_EINVAL;
+    }
     return LBM_OK;
 }
 

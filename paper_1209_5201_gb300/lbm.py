@@ -38,7 +38,7 @@ class lbm_params(C.Structure):
                 ("thermal", C.c_int32), ("Kn", C.c_double), ("tau", C.c_double),
                 ("mu_exp", C.c_double), ("u_wall", C.c_double * 2), ("T_wall", C.c_double * 2),
                 ("precision", C.c_int32), ("kernel", C.c_int32), ("rho0", C.c_double),
-                ("noise_amp", C.c_double), ("seed", C.c_uint64)]
+                ("noise_amp", C.c_double), ("seed", C.c_uint64), ("accom", C.c_double * 2)]
 
 
 class lbm_stats(C.Structure):
@@ -51,7 +51,8 @@ class lbm_request(C.Structure):
     _fields_ = [("lattice", C.c_int32), ("Ny", C.c_int32), ("eq_order", C.c_int32),
                 ("thermal", C.c_int32), ("Kn", C.c_double), ("tau", C.c_double),
                 ("mu_exp", C.c_double), ("u_wall", C.c_double * 2), ("T_wall", C.c_double * 2),
-                ("tol", C.c_double), ("max_steps", C.c_int64), ("tag", C.c_uint64)]
+                ("tol", C.c_double), ("max_steps", C.c_int64), ("tag", C.c_uint64),
+                ("accom", C.c_double * 2)]
 
 
 class lbm_result(C.Structure):
@@ -409,7 +410,7 @@ def lbm_residual_noalloc(ux, T, ux_prev, T_prev, n: int, T_ref: float, thermal: 
 def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
                  tol: float = 1e-5, max_steps: int = 10_000_000, tag: int = 0,
                  eq_order: int | None = None, thermal: bool | None = None,
-                 tau: float = 0.0) -> lbm_request:
+                 tau: float = 0.0, accom: tuple = (1.0, 1.0)) -> lbm_request:
     """A Couette request: walls at -U_w (bottom) and +U_w (top), both at T_w."""
     o, t = (4, True) if lattice == "D2Q37" else (2, False)
     r = lbm_request()
@@ -421,6 +422,7 @@ def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
     r.u_wall[0], r.u_wall[1] = -U_w, U_w
     r.T_wall[0] = r.T_wall[1] = T_w
     r.tol, r.max_steps, r.tag = tol, max_steps, tag
+    r.accom[0], r.accom[1] = accom
     return r
 
 
@@ -459,6 +461,7 @@ class Config:
     rho0: float = 1.0
     noise_amp: float = 0.0
     seed: int = 7
+    accom: tuple = (1.0, 1.0)
 
     def params(self) -> lbm_params:
         p = lbm_params_default()
@@ -468,6 +471,7 @@ class Config:
         p.T_wall[0], p.T_wall[1] = self.T_wall
         p.precision, p.kernel = PRECISION[self.precision], self.kernel
         p.rho0, p.noise_amp, p.seed = self.rho0, self.noise_amp, self.seed
+        p.accom[0], p.accom[1] = self.accom
         return p
 
 

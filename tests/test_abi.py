@@ -129,3 +129,19 @@ def test_server_request_validation(lbm):
         assert ei.value.status == lbm.LBM_EINVAL
     c = lbm.lbm_server_cfg_default()
     assert (c.max_slots, c.chunk_steps, c.mem_budget_bytes) == (256, 100, 40 << 30)
+
+
+def test_accommodation_parameter_checks(lbm):
+    h = lbm.lbm_lattice_create(25)
+    try:
+        p = lbm.lbm_params_default()
+        assert (p.accom[0], p.accom[1]) == (1.0, 1.0)
+        for bad in (-0.1, 1.5, float("nan")):
+            p.accom[0] = bad
+            with pytest.raises(lbm.LBMError):
+                lbm.lbm_solver_required_bytes(h, p)
+    finally:
+        lbm.lbm_lattice_destroy(h)
+    r = lbm.make_request("D2Q25", 32, 0.1, 0.1, accom=(0.5, 2.0))
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_request_bytes(r)

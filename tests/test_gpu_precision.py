@@ -10,10 +10,14 @@ from gpu_util import need_gpu, report
 
 pytestmark = pytest.mark.gpu
 
+# BF16 keeps 8 significant bits of d = f - w rho (|d| up to ~0.3 w here); the
+# steady state carries that round-off amplified by the relaxation time, a
+# floor measured at 4.4e-2 U_w in u_x and 2e-4 in rho; its residual stalls
+# near 5e-5, so the 1e-6 target is not reached (ENOTCONVERGED is expected).
 BOUNDS = {          # rho, u_x / U_w, T
     "fp64": (1e-9, 1e-7, 1e-9),
     "fp32": (2e-6, 5e-6, 2e-6),
-    "bf16dev": (5e-3, 3e-2, 5e-3),
+    "bf16dev": (1e-3, 6e-2, 5e-3),
 }
 TOL = {"fp64": 1e-8, "fp32": 1e-6, "bf16dev": 1e-6}
 
