@@ -18,4 +18,9 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                             (Eq. (13)), NS temperature profile (Eq. (14), read
                             with U_w^2), second-order grid convergence
   orc_run_to_residual       pinned through the steady Couette profiles above
+  orc_fluxes                pinned: sigma = q = 0 at equilibrium, traceless
+                            thermal stress, Newtonian stress and Fourier heat
+                            flux in the slow-shear bulk, uniform bulk shear
+                            stress, energy balance q_y = -u_x sigma_xy under
+                            grid refinement
 """

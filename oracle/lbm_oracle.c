@@ -131,19 +131,27 @@ void orc_moments(const orc_lattice *L, int thermal, const double *fa,
     *rho = s0; *ux = u; *uy = v; *T = t;
 }
 
+/* Time step dt = dx / r with dx = 1 / Ny. */
+static double orc_dt(const orc_lattice *L, const orc_params *P)
+{
+    return 1.0 / (L->r * P->Ny);
+}
+
+/* Local relaxation time tau = sqrt(2/pi) Kn mu / (rho T) (Sec. II, Eq. (15)),
+ * or the constant one. */
+static double orc_tau(const orc_params *P, double rho, double T)
+{
+    if (P->tau > 0.0) return P->tau;
+    double mu = pow(T, P->mu_exp);
+    return sqrt(2.0 / M_PI) * P->Kn * mu / (rho * T);
+}
+
 /* Relaxation factor dt / (tau + dt/2) of Eq. (5). */
 static double orc_omega(const orc_lattice *L, const orc_params *P, double rho,
                         double T)
 {
-    double dt = 1.0 / (L->r * P->Ny);
-    double tau;
-    if (P->tau > 0.0) {
-        tau = P->tau;
-    } else {
-        double mu = pow(T, P->mu_exp);
-        tau = sqrt(2.0 / M_PI) * P->Kn * mu / (rho * T);
-    }
-    return dt / (tau + 0.5 * dt);
+    double dt = orc_dt(L, P);
+    return dt / (orc_tau(P, rho, T) + 0.5 * dt);
 }
 
 /* Collision half of Eq. (5), in place on every fluid cell:
@@ -339,6 +347,47 @@ void orc_macros_kinetic(const orc_lattice *L, const orc_params *P, const double 
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < plane; ++c)
         orc_moments(L, 1, f + c, plane, rho + c, ux + c, uy + c, T + c);
+}
+
+/* Stress and heat flux of every cell from its pre-collision f~.  The
+ * transformed variable of Sec. II is f~ = f + dt/(2 tau) (f - f^eq), so the
+ * distribution itself is f = (f~ + dt/(2 tau) f^eq) / (1 + dt/(2 tau)); its
+ * central moments give
+ *   sigma_ij = sum_a (c_i - u_i)(c_j - u_j) f_a - rho T delta_ij,
+ *   q_i      = 1/2 sum_a |c - u|^2 (c_i - u_i) f_a,
+ * with rho, u, T the conserved moments of f~ (equal to those of f) and T = 1
+ * in an isothermal run (the temperature its equilibrium and tau use).
+ * Outputs are [Ny][Nx] planes; any may be NULL. */
+void orc_fluxes(const orc_lattice *L, const orc_params *P, const double *f,
+                double *sxx, double *sxy, double *syy, double *qx, double *qy)
+{
+    const long plane = (long)P->Nx * P->Ny;
+    const double dt = orc_dt(L, P);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < plane; ++c) {
+        double feq[64];
+        double rho, ux, uy, T;
+        orc_moments(L, P->thermal, f + c, plane, &rho, &ux, &uy, &T);
+        if (!P->thermal) T = 1.0;
+        orc_equilibrium(L, P->eq_order, rho, ux, uy, T, feq);
+        double h = dt / (2.0 * orc_tau(P, rho, T));
+        double pxx = 0.0, pxy = 0.0, pyy = 0.0, hx = 0.0, hy = 0.0;
+        for (int a = 0; a < L->Q; ++a) {
+            double fa = (f[a * plane + c] + h * feq[a]) / (1.0 + h);
+            double Cx = L->r * L->ex[a] - ux, Cy = L->r * L->ey[a] - uy;
+            double C2 = Cx * Cx + Cy * Cy;
+            pxx += Cx * Cx * fa;
+            pxy += Cx * Cy * fa;
+            pyy += Cy * Cy * fa;
+            hx += 0.5 * C2 * Cx * fa;
+            hy += 0.5 * C2 * Cy * fa;
+        }
+        if (sxx) sxx[c] = pxx - rho * T;
+        if (sxy) sxy[c] = pxy;
+        if (syy) syy[c] = pyy - rho * T;
+        if (qx) qx[c] = hx;
+        if (qy) qy[c] = hy;
+    }
 }
 
 /* Steady-state driver: run in chunks of check_every steps until the relative

@@ -67,6 +67,8 @@ def _load():
         lib.orc_macros.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp, dp, dp]
         lib.orc_macros_kinetic.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp,
                                            dp, dp]
+        lib.orc_fluxes.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp, dp, dp,
+                                   dp]
         lib.orc_run_to_residual.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp,
                                             C.c_double, C.c_long, C.c_int,
                                             C.POINTER(C.c_long), dp]
@@ -182,6 +184,15 @@ def macros_kinetic(p: Problem, f: np.ndarray):
     out = [np.empty((p.Ny, p.Nx)) for _ in range(4)]
     _load().orc_macros_kinetic(C.byref(p._cl), C.byref(p._cp), _dp(np.ascontiguousarray(f)),
                                *[_dp(a) for a in out])
+    return tuple(out)
+
+
+def fluxes(p: Problem, f: np.ndarray):
+    """Stress (sigma_xx, sigma_xy, sigma_yy) and heat flux (q_x, q_y) planes
+    [Ny][Nx] of the distribution behind the pre-collision f~ (Sec. II)."""
+    out = [np.empty((p.Ny, p.Nx)) for _ in range(5)]
+    _load().orc_fluxes(C.byref(p._cl), C.byref(p._cp), _dp(np.ascontiguousarray(f)),
+                       *[_dp(a) for a in out])
     return tuple(out)
 
 

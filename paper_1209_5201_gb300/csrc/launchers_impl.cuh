@@ -36,8 +36,9 @@ inline int aux_blocks(long long n) {
 
 // ---- direct kernel variants {BX, MINB, CS} --------------------------------------
 struct DirectVariants {
-    static constexpr int n = 5;
-    static constexpr int v[n][3] = {{128, 0, 0}, {64, 0, 0}, {128, 8, 0}, {256, 0, 0}, {128, 0, 1}};
+    static constexpr int n = 7;
+    static constexpr int v[n][3] = {{128, 0, 0}, {64, 0, 0}, {128, 8, 0}, {256, 0, 0}, {128, 0, 1},
+                                    {512, 2, 0}, {1024, 1, 0}};
 };
 
 template <int Q, int PREC, int BX, int MINB, bool CS>
@@ -64,6 +65,8 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
         LBM_DIRECT_CASE(2)
         LBM_DIRECT_CASE(3)
         LBM_DIRECT_CASE(4)
+        LBM_DIRECT_CASE(5)
+        LBM_DIRECT_CASE(6)
     default: break;
     }
 #undef LBM_DIRECT_CASE

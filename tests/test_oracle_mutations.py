@@ -38,7 +38,7 @@ MUTATIONS = {
         lambda o: pins.test_wall_zero_net_mass_flux_and_bookkeeping(o, "D2Q17")),
     # relaxation factor of Eq. (5) without the dt/2 shift
     "omega_without_half_dt": (
-        "return dt / (tau + 0.5 * dt);", "return dt / tau;",
+        "return dt / (orc_tau(P, rho, T) + 0.5 * dt);", "return dt / orc_tau(P, rho, T);",
         lambda o: pins.test_ns_slip_limit(o, "D2Q25")),
     # x-momentum moment with the wrong velocity component
     "moment_transposed": (
@@ -59,6 +59,23 @@ MUTATIONS = {
         "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[wall], 0.0, Tw, gw);",
         "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[1 - wall], 0.0, Tw, gw);",
         lambda o: pins.test_couette_antisymmetry(o)),
+    # f taken as f~: the Sec. II conversion of the stress moments dropped
+    "flux_conversion_dropped": (
+        "double fa = (f[a * plane + c] + h * feq[a]) / (1.0 + h);", "double fa = f[a * plane + c];",
+        lambda o: pins.test_stress_newtonian_limit(o, "D2Q25")),
+    # heat flux from raw instead of peculiar velocities
+    "heat_flux_not_central": (
+        "double Cx = L->r * L->ex[a] - ux, Cy = L->r * L->ey[a] - uy;",
+        "double Cx = L->r * L->ex[a], Cy = L->r * L->ey[a];",
+        lambda o: pins.test_fluxes_vanish_at_equilibrium(o)),
+    # isotropic part of the pressure tensor taken as rho instead of rho T
+    "stress_trace_rho_only": (
+        "if (sxx) sxx[c] = pxx - rho * T;", "if (sxx) sxx[c] = pxx - rho;",
+        lambda o: pins.test_thermal_stress_is_traceless(o)),
+    # heat flux without its factor 1/2
+    "heat_flux_factor": (
+        "hy += 0.5 * C2 * Cy * fa;", "hy += C2 * Cy * fa;",
+        lambda o: pins.test_heat_flux_fourier_limit_and_energy_balance(o)),
 }
 
 

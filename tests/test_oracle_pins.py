@@ -402,3 +402,79 @@ def test_maxwell_slip_length(oracle):
     # and the diffuse-wall profile is measurably different (less slip)
     diffuse = (2 * y - 1) * Uw / (1 + 2 * Kn)
     assert np.max(np.abs(ux - diffuse)) / Uw > 0.03
+
+
+# ---- stress and heat flux (Sec. II: f recovered from f~) ------------------------
+
+def _steady_couette(oracle, name, Ny, Kn, Uw):
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    p = oracle.Problem(lattice=name, Nx=1, Ny=Ny, eq_order=order, thermal=thermal, Kn=Kn,
+                       u_wall=(-Uw, Uw))
+    f = oracle.init_fields(p, np.ones((Ny, 1)))
+    ok, _, _ = oracle.run_to_residual(p, f, 1e-12, 800000, 100)
+    assert ok
+    return p, f
+
+
+def test_fluxes_vanish_at_equilibrium(oracle):
+    # f~ = f^eq(rho, u, T) is its own f; the thermal lattice reproduces the
+    # Maxwellian's central moments through third order, where sigma and q are 0
+    p = oracle.Problem(lattice="D2Q37", Nx=3, Ny=4, eq_order=4, thermal=True, Kn=0.1)
+    g = np.random.default_rng(5)
+    rho = 1 + 0.1 * g.uniform(-1, 1, (4, 3))
+    ux, uy = 0.3 * g.uniform(-1, 1, (2, 4, 3))
+    T = 1 + 0.05 * g.uniform(-1, 1, (4, 3))
+    f = oracle.init_fields(p, rho, ux, uy, T)
+    for a in oracle.fluxes(p, f):
+        assert np.max(np.abs(a)) < 1e-13
+
+
+def test_thermal_stress_is_traceless(oracle):
+    # energy is a collision invariant, so f and f~ carry the same D rho T:
+    # sigma_xx + sigma_yy = 0 for any state of a thermal run
+    p = oracle.Problem(lattice="D2Q37", Nx=5, Ny=12, eq_order=4, thermal=True, Kn=0.05,
+                       u_wall=(-0.3, 0.2), T_wall=(1.05, 0.95))
+    f = oracle.init_fields(p, inputs.rho_field(5, 12, 1e-2, seed=9))
+    oracle.run(p, f, 30)
+    sxx, _, syy, _, _ = oracle.fluxes(p, f)
+    assert np.max(np.abs(sxx)) > 1e-5
+    assert np.max(np.abs(sxx + syy)) < 1e-13
+
+
+@pytest.mark.parametrize("name", ["D2Q25", "D2Q37"])
+def test_stress_newtonian_limit(oracle, name):
+    # slow shear in the bulk: the BGK stress is Newtonian, sigma_xy = -mu du/dy
+    # with mu = p tau = sqrt(2/pi) Kn T (tau of Sec. II with mu = T)
+    Ny, Kn, Uw = 40, 0.01, 0.1
+    p, f = _steady_couette(oracle, name, Ny, Kn, Uw)
+    _, ux, _, T = [a[:, 0] for a in oracle.macros(p, f)]
+    sxy = oracle.fluxes(p, f)[1][:, 0]
+    y = (np.arange(Ny) + 0.5) / Ny
+    mu = math.sqrt(2 / math.pi) * Kn * T
+    ratio = sxy / (-mu * np.gradient(ux, y))
+    mid = slice(Ny // 4, 3 * Ny // 4)
+    assert np.max(np.abs(ratio[mid] - 1)) < 2e-3, ratio[mid]
+    # steady momentum balance: the shear stress is uniform across the bulk (the
+    # wall rows carry a discretisation error that shrinks with the grid)
+    assert np.ptp(sxy[mid]) < 1e-4 * np.max(np.abs(sxy))
+
+
+def test_heat_flux_fourier_limit_and_energy_balance(oracle):
+    # Fourier's law with the BGK conductivity C_p mu (Pr = 1, C_p = 2 in 2-D),
+    # and the steady energy balance of symmetric Couette flow q_y = -u_x sigma_xy
+    # (a uniform total energy flux that is odd about the mid-plane), which the
+    # lattice approaches as the grid is refined
+    p, f = _steady_couette(oracle, "D2Q37", 32, 0.02, 0.3)
+    _, ux, _, T = [a[:, 0] for a in oracle.macros(p, f)]
+    _, sxy, _, _, qy = [a[:, 0] for a in oracle.fluxes(p, f)]
+    y = (np.arange(32) + 0.5) / 32
+    mu = math.sqrt(2 / math.pi) * 0.02 * T
+    ratio = qy / (-2 * mu * np.gradient(T, y))
+    assert np.max(np.abs(ratio[8:24] - 1)) < 0.01, ratio[8:24]
+    rel = []
+    for Ny in (32, 64):
+        p, f = _steady_couette(oracle, "D2Q37", Ny, 0.05, 0.3)
+        ux = oracle.macros(p, f)[1][:, 0]
+        _, sxy, _, _, qy = [a[:, 0] for a in oracle.fluxes(p, f)]
+        rel.append(np.max(np.abs(qy + ux * sxy)) / np.max(np.abs(qy)))
+    assert rel[0] < 0.04 and rel[1] < 0.6 * rel[0], rel
