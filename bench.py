@@ -292,6 +292,35 @@ def run_reference(args):
     return 0
 
 
+# kernel sources whose change invalidates recorded DRAM counters
+TRAFFIC_SOURCES = ["k_step_direct.cuh", "k_step_staged.cuh", "lbm_device.cuh", "lbm_internal.h"]
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1209_5201_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def step_traffic(key: str):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch recorded by an ncu
+    capture (profiles/step_traffic.json), or None when there is no capture of
+    this configuration or the kernel sources changed since it was taken."""
+    tf = os.path.join(ROOT, "profiles", "step_traffic.json")
+    try:
+        with open(tf) as fh:
+            d = json.load(fh)
+        e = d["entries"].get(key)
+        if e is None or d.get("kernel_sources_sha256") != kernel_sources_sha256():
+            return None
+        return e["dram_bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,16 +445,7 @@ def main():
     peak, peak_kind = measured_peaks()
     bpl = BYTES_PER_LU[args.precision]
     achieved = bpl * cells / (ms_step * 1e-3) / 1e9
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "step_traffic.json")
-    if os.path.exists(tf):
-        try:
-            with open(tf) as fh:
-                d = json.load(fh)
-            key = f"{args.precision}:{kern}:{var}:{cfg.Nx}x{cfg.Ny}"
-            traffic = d.get(key)
-        except Exception:
-            traffic = None
+    traffic = step_traffic(f"{args.precision}:{kern}:{var}:{cfg.Nx}x{cfg.Ny}")
     out = {
         "metric": "D2Q37 MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,

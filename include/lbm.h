@@ -168,6 +168,17 @@ int lbm_solver_set_f(lbm_solver *s, const double *f);
 int lbm_solver_macros(lbm_solver *s, double *rho, double *ux, double *uy,
                       double *T);
 
+/* Stress and heat flux (Sec. II: f~ = f + dt/(2 tau) (f - f^eq), so
+ * f = (f~ + dt/(2 tau) f^eq) / (1 + dt/(2 tau))) of the pre-collision f~ that
+ * the next step's streaming and wall fill produce from the current state:
+ *   sigma_ij = sum (c_i - u_i)(c_j - u_j) f - rho T delta_ij,
+ *   q_i      = 1/2 sum |c - u|^2 (c_i - u_i) f,
+ * T = 1 in an isothermal run.  Computed in FP64 on the device from the stored
+ * state (any precision).  Host FP64 outputs [Ny][Nx] each, caller-owned; any
+ * may be NULL.  Synchronous.  Errors: LBM_EINVAL (NULL solver), LBM_ECUDA. */
+int lbm_solver_fluxes(lbm_solver *s, double *sxx, double *sxy, double *syy,
+                      double *qx, double *qy);
+
 /* Checkpoint: the exact stored bytes plus the step counter.  get_state
  * writes state_bytes bytes to host memory; set_state restores them; a resumed
  * run is bit-identical to an uninterrupted one.  Errors: LBM_EINVAL if bytes

@@ -42,7 +42,7 @@ Layout layout_of(const LatticeHost &L, const lbm_params &p) {
     const size_t cells = (size_t)p.Nx * p.Ny;
     lo.f_bytes = align_up((size_t)L.Q * p.Ny * pitch * storage_elem_bytes(p.precision));
     lo.rho_bytes = p.precision == LBM_BF16DEV ? align_up((size_t)p.Ny * pitch * 4) : 0;
-    lo.stage_bytes = align_up(4 * cells * 8);
+    lo.stage_bytes = align_up(5 * cells * 8);
     lo.prev_bytes = align_up(2 * cells * 8);
     lo.red_bytes = align_up((1024 * 8 + 64) * 8);
     lo.total = 2 * lo.f_bytes + 2 * lo.rho_bytes + lo.stage_bytes + lo.prev_bytes + lo.red_bytes;
@@ -579,6 +579,25 @@ int lbm_solver_macros(lbm_solver *h, double *rho, double *ux, double *uy, double
                                                   hst[2] ? d[2] : nullptr, hst[3] ? d[3] : nullptr);
     }));
     for (int i = 0; i < 4; ++i)
+        if (hst[i]) CU(cudaMemcpyAsync(hst[i], d[i], n * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
+    CU(cudaStreamSynchronize(s.stream));
+    return LBM_OK;
+    API_END
+}
+
+int lbm_solver_fluxes(lbm_solver *h, double *sxx, double *sxy, double *syy, double *qx,
+                      double *qy) {
+    API_BEGIN
+    if (!h) { set_error("NULL solver"); return LBM_EINVAL; }
+    SolverImpl &s = h->s;
+    const size_t n = (size_t)s.p.Nx * s.p.Ny;
+    double *hst[5] = {sxx, sxy, syy, qx, qy};
+    double *d[5];
+    for (int i = 0; i < 5; ++i) d[i] = hst[i] ? s.stage + i * n : nullptr;
+    CU(dispatch_prec(s.p.precision, [&](auto P) {
+        return Launch<decltype(P)::value>::fluxes(s, d[0], d[1], d[2], d[3], d[4]);
+    }));
+    for (int i = 0; i < 5; ++i)
         if (hst[i]) CU(cudaMemcpyAsync(hst[i], d[i], n * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
     CU(cudaStreamSynchronize(s.stream));
     return LBM_OK;

@@ -18,6 +18,8 @@ struct Launch {
     static int plane_to_f64(SolverImpl &s, int a, double *out);
     static int plane_from_f64(SolverImpl &s, int a, const double *in);
     static int macros(SolverImpl &s, double *rho, double *ux, double *uy, double *T);
+    static int fluxes(SolverImpl &s, double *sxx, double *sxy, double *syy, double *qx,
+                      double *qy);
     static int wall_mass(SolverImpl &s, double *m_in);
     static int mass_partials(SolverImpl &s, double *partials, int nblocks);
 };

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "k_aux.cuh"
+#include "k_fluxes.cuh"
 #include "k_step_direct.cuh"
 #include "k_step_staged.cuh"
 #include "launchers.h"
@@ -36,9 +37,8 @@ inline int aux_blocks(long long n) {
 
 // ---- direct kernel variants {BX, MINB, CS} --------------------------------------
 struct DirectVariants {
-    static constexpr int n = 7;
-    static constexpr int v[n][3] = {{128, 0, 0}, {64, 0, 0}, {128, 8, 0}, {256, 0, 0}, {128, 0, 1},
-                                    {512, 2, 0}, {1024, 1, 0}};
+    static constexpr int n = 5;
+    static constexpr int v[n][3] = {{128, 0, 0}, {64, 0, 0}, {128, 8, 0}, {256, 0, 0}, {128, 0, 1}};
 };
 
 template <int Q, int PREC, int BX, int MINB, bool CS>
@@ -65,8 +65,6 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
         LBM_DIRECT_CASE(2)
         LBM_DIRECT_CASE(3)
         LBM_DIRECT_CASE(4)
-        LBM_DIRECT_CASE(5)
-        LBM_DIRECT_CASE(6)
     default: break;
     }
 #undef LBM_DIRECT_CASE
@@ -190,6 +188,18 @@ int Launch<PREC>::macros(SolverImpl &s, double *rho, double *ux, double *uy, dou
     const long long n = (long long)s.p.Nx * s.p.Ny;
     LBM_DISPATCH_Q(s.L.Q, (k_macros<QQ, PREC><<<aux_blocks(n), kAuxThreads, 0, s.stream>>>(
                                (const S *)s.f[s.cur], s.rho[s.cur], k, rho, ux, uy, T)));
+    return (int)cudaGetLastError();
+}
+
+template <int PREC>
+int Launch<PREC>::fluxes(SolverImpl &s, double *sxx, double *sxy, double *syy, double *qx,
+                         double *qy) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    dim3 grid((s.p.Nx + kFluxThreads - 1) / kFluxThreads, s.p.Ny);
+    LBM_DISPATCH_Q(s.L.Q, (k_fluxes<QQ, PREC><<<grid, kFluxThreads, 0, s.stream>>>(
+                               (const S *)s.f[s.cur], s.rho[s.cur], k, s.kd, sxx, sxy, syy, qx,
+                               qy)));
     return (int)cudaGetLastError();
 }
 

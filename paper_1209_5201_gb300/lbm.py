@@ -101,6 +101,7 @@ _SIGS = {
     "lbm_solver_get_f": ([_VP, _DP], C.c_int),
     "lbm_solver_set_f": ([_VP, _DP], C.c_int),
     "lbm_solver_macros": ([_VP, _DP, _DP, _DP, _DP], C.c_int),
+    "lbm_solver_fluxes": ([_VP, _DP, _DP, _DP, _DP, _DP], C.c_int),
     "lbm_solver_state_bytes": ([_VP, C.POINTER(C.c_size_t)], C.c_int),
     "lbm_solver_get_state": ([_VP, _VP, C.c_size_t], C.c_int),
     "lbm_solver_set_state": ([_VP, _VP, C.c_size_t], C.c_int),
@@ -268,6 +269,11 @@ def lbm_solver_set_f(h, f: np.ndarray) -> None:
 
 def lbm_solver_macros(h, rho=None, ux=None, uy=None, T=None) -> None:
     _check(load().lbm_solver_macros(h, _dp(rho), _dp(ux), _dp(uy), _dp(T)), "lbm_solver_macros")
+
+
+def lbm_solver_fluxes(h, sxx=None, sxy=None, syy=None, qx=None, qy=None) -> None:
+    _check(load().lbm_solver_fluxes(h, _dp(sxx), _dp(sxy), _dp(syy), _dp(qx), _dp(qy)),
+           "lbm_solver_fluxes")
 
 
 def lbm_solver_state_bytes(h) -> int:
@@ -557,6 +563,13 @@ class Solver:
         shp = (self.cfg.Ny, self.cfg.Nx)
         out = [np.empty(shp) for _ in range(4)]
         lbm_solver_macros(self.h, *out)
+        return tuple(out)
+
+    def fluxes(self):
+        """(sigma_xx, sigma_xy, sigma_yy, q_x, q_y), each FP64 [Ny][Nx]."""
+        shp = (self.cfg.Ny, self.cfg.Nx)
+        out = [np.empty(shp) for _ in range(5)]
+        lbm_solver_fluxes(self.h, *out)
         return tuple(out)
 
     def set_kernel(self, kernel: int, variant: int = 0):
