@@ -1,9 +1,11 @@
 """Stress and heat flux read-out (Sec. II conversion of f~) on the GPU, through
 the C ABI, against the oracle's orc_fluxes on the same state.
 
-The GPU state after n steps is the post-collision f~*; lbm_solver_fluxes pulls
-it (streaming + wall fill) to the pre-collision f~ of step n, which is the
-oracle's state after n steps.
+The GPU starts from a post-collision f~* = rho g^eq and the oracle from the same
+values taken as pre-collision f~ (a fixed point of the collision), so the GPU
+state after n steps is the oracle's state after n steps, collided.
+lbm_solver_fluxes pulls it (streaming + wall fill) to the next pre-collision
+f~: the oracle's state after n + 1 steps.
 """
 import numpy as np
 import pytest
@@ -36,7 +38,7 @@ def test_fp64_fluxes_match_oracle(lbm, oracle, lattice, Nx, Ny, accom):
     p = oracle.Problem(**kw, accom=accom)
     rho = inputs.rho_field(Nx, Ny, 1e-2, seed=4)
     fo = oracle.init_fields(p, rho)
-    oracle.run(p, fo, 30)
+    oracle.run(p, fo, 31)
     ref = oracle.fluxes(p, fo)
     s = lbm.Solver(lbm.Config(**kw, precision="fp64", accom=accom))
     s.init_fields(rho)

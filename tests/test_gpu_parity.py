@@ -66,10 +66,13 @@ def test_fp64_couette_d2q25_1x64(lbm, oracle):
 # thermal lattice; the worst entries are the smallest populations (w = 2.5e-4)
 # near the walls, where ~1e-7 of round-off per step (Q terms of 6e-8 relative
 # each, on values of order w) accumulates to ~2.5e-9 absolute; bound 2e-5.
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
-def test_d2q37_thermal_grid_multi_block(lbm, oracle, precision, tol):
+# After 1000 steps the same per-step round-off, accumulated linearly in the
+# worst case, gives 5 x that bound.
+@pytest.mark.parametrize("precision,n,tol", [("fp64", 1000, 1e-12), ("fp32", 200, 2e-5),
+                                             ("fp32", 1000, 1e-4)])
+def test_d2q37_thermal_grid_multi_block(lbm, oracle, precision, n, tol):
     # 300 columns = 2 full 128-column blocks + a ragged 44, 40 rows, noise on rho
-    Nx, Ny, n = 300, 40, 200
+    Nx, Ny = 300, 40
     s, p, perm = make_pair(lbm, oracle, "D2Q37", Nx, Ny, precision=precision, Kn=0.05,
                            u_wall=(-0.3, 0.3), T_wall=(1.02, 0.98))
     rho = inputs.rho_field(Nx, Ny, 1e-3, seed=7)
@@ -79,7 +82,7 @@ def test_d2q37_thermal_grid_multi_block(lbm, oracle, precision, tol):
     oracle.run(p, f, n)
     err = rel_err(s.get_f(), oracle.collide(p, f)[perm])
     s.close()
-    report(f"parity_grid_d2q37_{precision}", {"max_rel_err_per_population": err, "steps": n})
+    report(f"parity_grid_d2q37_{precision}_{n}", {"max_rel_err_per_population": err, "steps": n})
     assert err < tol, err
 
 
