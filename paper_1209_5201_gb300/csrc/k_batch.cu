@@ -49,16 +49,16 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
 k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
               float *__restrict__ pool, int chunk, long long pool_elems, int *dbg) {
     __shared__ SlotDesc sd;
-    __shared__ double s_min[2];
+    __shared__ BatchWallShared sw;
     const int slot = blockIdx.x;
     load_desc(desc + slot, &sd);
     __syncthreads();
     if (sd.Q == 0 || status[slot].state != kSlotRunning) return;
     if (!desc_ok(sd, pool_elems, slot, 1, dbg)) return;
     switch (sd.Q) {
-    case 17: batch_slot<17>(sd, pool, status + slot, s_min); break;
-    case 25: batch_slot<25>(sd, pool, status + slot, s_min); break;
-    case 37: batch_slot<37>(sd, pool, status + slot, s_min); break;
+    case 17: batch_slot<17>(sd, pool, status + slot, sw); break;
+    case 25: batch_slot<25>(sd, pool, status + slot, sw); break;
+    case 37: batch_slot<37>(sd, pool, status + slot, sw); break;
     default: break;
     }
     if (threadIdx.x == 0) desc[slot].cur = (sd.cur + sd.chunk_steps) & 1;

@@ -17,9 +17,16 @@
 
 namespace lbm {
 
+// Shared per-step wall data of a slot: the re-emitted deviations of Eq. (12)
+// per wall and velocity, and the accommodation of each wall in FP32.
+struct BatchWallShared {
+    float fill[2][kMaxQ];
+    float acc[2];
+};
+
 template <int Q>
 __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict__ pool,
-                                           SlotStatus *__restrict__ st, double *s_min) {
+                                           SlotStatus *__restrict__ st, BatchWallShared &sw) {
     const int chunk = d.chunk_steps;
     using L = Lat<Q>;
     const KConsts<float> &k = d.k;
@@ -33,8 +40,14 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
     const float *src = d.cur ? buf1 : buf0;
     float *dst = d.cur ? buf0 : buf1;
 
+    if (tid < 2) sw.acc[tid] = (float)k.accom[tid];
     for (int step = 0; step < chunk; ++step) {
         if (warp < 2) {
+            // numerator of Eq. (12) in FP64, then the normalised re-emission
+            // M_in g^w_a / D_w of each outgoing velocity, formed in FP64 once
+            // per wall and step (lane a and a + 32) and kept as an FP32
+            // deviation: GB300's FP64 rate is a small fraction of its FP32 rate,
+            // so no FP64 work is left in the per-cell loop
             double v = 0.0;
             if (lane < NT) {
                 const int a = d.term_a[warp][lane];
@@ -44,23 +57,31 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
                 v = (double)src[(long long)a * Ny + row] + (double)k.w[a];
             }
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) s_min[warp] = v;
+            const double m = __shfl_sync(0xffffffffu, v, 0);
+            for (int a = lane; a < Q; a += 32)
+                sw.fill[warp][a] = k.wcoef[warp][a] != 0.0
+                                       ? (float)(m * k.wcoef[warp][a] - (double)k.w[a]) : 0.0f;
         }
         __syncthreads();
-        const double mb = s_min[0], mt = s_min[1];
         for (int j = tid; j < Ny; j += nth) {
+            // the slot's constants live in shared memory; this compiler barrier
+            // keeps them there (re-read per cell) instead of hoisted into
+            // registers for the whole step loop, which spilled
+            asm volatile("" ::: "memory");
             float f[Q];
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const int sj = j - L::ey(a);
                 if (sj < 0 || sj >= Ny) {
                     // Eq. (9): diffuse part of the wall, plus the specular part
-                    // (the mirrored velocity of the same row) when accom < 1
+                    // (the mirrored velocity of the same row) when accom < 1;
+                    // both are deviations from w_a, so the mix is linear in them
                     const int wall = sj < 0 ? 0 : 1;
-                    const float spec = k.accom[wall] != 1.0
-                                           ? src[(long long)k.mirror[a] * Ny + j] : 0.0f;
-                    f[a] = wall_mix<LBM_FP32>(wall == 0 ? mb : mt, k.wcoef[wall][a], k.w[a],
-                                              k.accom[wall], spec);
+                    const float acc = sw.acc[wall];
+                    float v = sw.fill[wall][a];
+                    if (acc != 1.0f)
+                        v = acc * v + (1.0f - acc) * src[(long long)k.mirror[a] * Ny + j];
+                    f[a] = v;
                 } else {
                     f[a] = src[(long long)a * Ny + sj];
                 }
