@@ -317,23 +317,32 @@ typedef struct lbm_result {
 
 typedef struct lbm_server_cfg {
     size_t mem_budget_bytes; /* device pool for the requests' f-arrays        */
-    int32_t max_slots;       /* requests on the GPU at once (1..4096)          */
+    int32_t max_slots;       /* CTAs the running requests may occupy at once
+                                (1..4096): a column of Ny rows runs on a
+                                cluster of CL = 1, 2, 4 or 8 CTAs of 256
+                                threads, the smallest CL with ceil(Ny / CL) <=
+                                cluster_rows (8 if none), at most max_slots  */
     int32_t chunk_steps;     /* steps per chunk launch                         */
     int32_t precision;       /* LBM_FP32                                       */
     int32_t use_graph;       /* replay the chunk launch as a CUDA graph        */
+    int32_t cluster_rows;    /* rows per CTA above which a column is split over
+                                a cluster (>= 32; default 256): smaller gives
+                                lower latency per request, larger more solves
+                                per second when the GPU is full             */
 } lbm_server_cfg;
 
 typedef struct lbm_server_metrics {
     int64_t submitted, completed, running, queued, chunks;
     double p50_latency_s, p99_latency_s, mean_latency_s;  /* submit -> done  */
     double solves_per_s;     /* completed / (last completion - first submit)  */
-    double mean_occupancy;   /* mean fraction of busy slots per chunk         */
+    double mean_occupancy;   /* mean fraction of max_slots busy per chunk     */
     size_t pool_bytes, pool_used_bytes;
 } lbm_server_metrics;
 
 typedef struct lbm_server lbm_server;
 
-/* 40 GB budget, 256 slots, 100-step chunks, FP32, CUDA graph on. */
+/* 40 GB budget, 256 CTAs, 100-step chunks, FP32, CUDA graph on, clusters
+ * above 256 rows per CTA. */
 void lbm_server_cfg_default(lbm_server_cfg *cfg);
 /* Device bytes one request occupies while admitted (two f-arrays of Q x Ny
  * floats plus two rows of previous-check fields, 256-byte granules). */

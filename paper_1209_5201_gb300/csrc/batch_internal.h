@@ -20,7 +20,7 @@ struct SlotDesc {
     int cur;                  // buffer holding the current state (0 / 1)
     int check_every;          // residual every check_every chunks
     int chunk_steps;          // steps this slot runs per chunk launch
-    int pad0;
+    int cl;                   // CTAs of the slot's cluster: 1, 2, 4 or 8
     long long f_off;          // element offset of buffer 0 in the pool
     long long prev_off;       // element offset of the previous-check u_x, T
     double tol;               // target of the extrapolated distance to steady state
@@ -49,11 +49,26 @@ struct SlotStatus {
     int chunks;               // chunks run since admission
 };
 
+// Cluster sizes of the slot classes.  A column of Ny rows runs on the smallest
+// cluster whose CTAs get at most `rows` rows each (8 CTAs if none does),
+// capped by the CTA budget.
+constexpr int kBatchClasses = 4;
+constexpr int kBatchClassCL[kBatchClasses] = {1, 2, 4, 8};
+inline int batch_cluster_size(int Ny, int rows, int max_ctas) {
+    int cl = 1;
+    while (cl < 8 && (Ny + cl - 1) / cl > rows) cl *= 2;
+    while (cl > 1 && (cl > max_ctas || (Ny + cl - 1) / cl < 32)) cl /= 2;
+    return cl;
+}
+
 int preload_batch_kernels();
 // dbg: 8 device ints; dbg[0] != 0 records the first invalid descriptor or
 // read-out offset a kernel met (and skipped).
+// One chunk of the slots [slot0, slot0 + nlanes), each on a cluster of CL
+// CTAs; part: 8 x 6 FP64 residual partials per slot of the whole table.
 int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, float *pool,
-                       int nslots, int chunk, long long pool_elems, int *dbg);
+                       double *part, int slot0, int nlanes, int CL, long long pool_elems,
+                       int *dbg);
 int launch_batch_init(cudaStream_t st, SlotDesc *desc, float *pool, const int *slots, int n,
                       float rho0, int nslots, long long pool_elems, int *dbg);
 int launch_batch_macros(cudaStream_t st, const SlotDesc *desc, const float *pool,

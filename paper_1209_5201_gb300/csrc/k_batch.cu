@@ -22,7 +22,10 @@ __device__ __forceinline__ bool desc_ok(const SlotDesc &d, long long pool_elems,
     bool mirror_ok = true;
     for (int a = 0; a < d.Q && q_ok; ++a)
         mirror_ok = mirror_ok && d.k.mirror[a] >= 0 && d.k.mirror[a] < d.Q;
-    const bool ok = q_ok && terms_ok && mirror_ok && d.Ny >= 6 && d.Ny <= 8192 && d.f_off >= 0 &&
+    const bool cl_ok = (d.cl == 1 || d.cl == 2 || d.cl == 4 || d.cl == 8) &&
+                       (d.cl == 1 || (d.Ny + d.cl - 1) / d.cl >= 32);
+    const bool ok = q_ok && terms_ok && mirror_ok && cl_ok && d.Ny >= 6 && d.Ny <= 8192 &&
+                    d.f_off >= 0 &&
                     d.f_off + need <= pool_elems && d.prev_off == d.f_off + 2LL * d.Q * d.Ny &&
                     (d.cur == 0 || d.cur == 1) && d.chunk_steps >= 1 && d.check_every >= 1;
     if (!ok && threadIdx.x == 0 && atomicCAS(dbg, 0, code) == 0) {
@@ -45,24 +48,32 @@ __device__ __forceinline__ void load_desc(const SlotDesc *g, SlotDesc *s) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// One chunk of slot slot0 + blockIdx.x / CL on a cluster of CL CTAs (CL = 1:
+// a plain launch).  Every CTA of a cluster reads the same descriptor and
+// status, so all of them take the same early exit or none does: no thread
+// leaves while others of its cluster still meet barriers.
 __global__ void __launch_bounds__(kBatchThreads, 2)
 k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
-              float *__restrict__ pool, int chunk, long long pool_elems, int *dbg) {
+              float *__restrict__ pool, double *__restrict__ part, int slot0, int CL,
+              long long pool_elems, int *dbg) {
     __shared__ SlotDesc sd;
     __shared__ BatchWallShared sw;
-    const int slot = blockIdx.x;
+    __shared__ int s_chunks;
+    const int slot = slot0 + blockIdx.x / CL;
+    const int rank = CL == 1 ? 0 : (int)cluster_rank();
     load_desc(desc + slot, &sd);
+    if (threadIdx.x == 0) s_chunks = status[slot].chunks + 1;
     __syncthreads();
     if (sd.Q == 0 || status[slot].state != kSlotRunning) return;
-    if (!desc_ok(sd, pool_elems, slot, 1, dbg)) return;
+    if (!desc_ok(sd, pool_elems, slot, 1, dbg) || sd.cl != CL) return;
+    double *pp = part + (long long)slot * 48;
     switch (sd.Q) {
-    case 17: batch_slot<17>(sd, pool, status + slot, sw); break;
-    case 25: batch_slot<25>(sd, pool, status + slot, sw); break;
-    case 37: batch_slot<37>(sd, pool, status + slot, sw); break;
+    case 17: batch_slot<17>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp); break;
+    case 25: batch_slot<25>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp); break;
+    case 37: batch_slot<37>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp); break;
     default: break;
     }
-    if (threadIdx.x == 0) desc[slot].cur = (sd.cur + sd.chunk_steps) & 1;
-    (void)chunk;
+    if (rank == 0 && threadIdx.x == 0) desc[slot].cur = (sd.cur + sd.chunk_steps) & 1;
 }
 
 // Rest equilibrium f~* = rho0 w_a of newly admitted slots, stored as the
@@ -165,10 +176,29 @@ int preload_batch_kernels() {
 }
 
 int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, float *pool,
-                       int nslots, int chunk, long long pool_elems, int *dbg) {
-    if (nslots <= 0) return 0;
-    k_batch_chunk<<<nslots, kBatchThreads, 0, st>>>(desc, status, pool, chunk, pool_elems, dbg);
-    return (int)cudaGetLastError();
+                       double *part, int slot0, int nlanes, int CL, long long pool_elems,
+                       int *dbg) {
+    if (nlanes <= 0) return 0;
+    if (CL == 1) {
+        k_batch_chunk<<<nlanes, kBatchThreads, 0, st>>>(desc, status, pool, part, slot0, 1,
+                                                        pool_elems, dbg);
+        return (int)cudaGetLastError();
+    }
+    if (CL != 2 && CL != 4 && CL != 8) return (int)cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nlanes * CL));
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return (int)cudaLaunchKernelEx(&cfg, k_batch_chunk, desc, status, pool, part, slot0, CL,
+                                   pool_elems, dbg);
 }
 
 int launch_batch_init(cudaStream_t st, SlotDesc *desc, float *pool, const int *slots, int n,

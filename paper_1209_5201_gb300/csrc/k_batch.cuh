@@ -1,15 +1,24 @@
 // Batched chunk kernel: many independent single-column Couette instances
 // (Nx = 1, each with its own lattice, height, Kn, wall speeds and wall
-// temperatures) advanced together, one CTA per slot, `chunk` time steps per
-// launch, then an FP64 steady-state residual per slot.
+// temperatures) advanced together, `chunk` time steps per launch, then an
+// FP64 steady-state residual per slot.
 //
 // With Nx = 1 the pull of Eq. (5) only shifts in y: f_in(j, a) =
-// f~*(j - e_ay, a).  Per step one warp sums the incoming mass of each wall
-// (numerator of Eq. (12)): lane l loads the l-th (velocity, row) term of the
-// wall's list (built on the host, carried in the slot descriptor), then a
-// warp-shuffle FP64 reduction in a fixed lane order gives
-// M_in; every slot's arithmetic is independent of the slot index, the grid
-// and the other slots.
+// f~*(j - e_ay, a).  A slot runs on a cluster of CL CTAs (CL = 1, 2, 4 or 8,
+// fixed by its height): CTA `rank` owns rows [rank R, rank R + R), R =
+// ceil(Ny / CL); the state stays in global memory (L2-resident) and a cluster
+// barrier with release / acquire semantics separates the steps.
+//
+// Row mapping inside a CTA: warp 0 of the bottom CTA owns the (up to) 32
+// lowest rows and warp 1 of the top CTA the 32 highest; each of those warps
+// first sums its wall's incoming mass (numerator of Eq. (12)) in FP64 by a
+// warp shuffle in a fixed lane order - lane l loads the l-th (velocity, row)
+// term of the wall's list, built on the host and carried in the slot
+// descriptor - forms the normalised re-emission of every outgoing velocity
+// once, and then updates its rows.  The other rows never need a wall value,
+// so no block barrier separates the wall sums from the bulk update.  Every
+// slot's arithmetic depends only on the slot itself (its cluster size is a
+// function of its height), never on the slot index, the grid or other slots.
 #pragma once
 
 #include "batch_internal.h"
@@ -18,22 +27,131 @@
 namespace lbm {
 
 // Shared per-step wall data of a slot: the re-emitted deviations of Eq. (12)
-// per wall and velocity, and the accommodation of each wall in FP32.
+// per wall and velocity and the accommodation of each wall in FP32, plus the
+// block-reduction scratch of the residual.
 struct BatchWallShared {
     float fill[2][kMaxQ];
     float acc[2];
+    double red[32][6];
 };
 
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+
+// Barrier of all threads of the slot's cluster, with release / acquire
+// semantics at cluster scope: every global store of the cluster before it is
+// visible to every thread of the cluster after it.  One CTA: the block barrier.
+__device__ __forceinline__ void slot_barrier(int CL) {
+    if (CL == 1) {
+        __syncthreads();
+        return;
+    }
+    // non-.aligned forms: correct even if a warp arrives diverged
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
+}
+
+// Numerator of Eq. (12) for `wall` summed by one full warp in FP64, and the
+// normalised re-emission M_in g^w_a / D_w of each outgoing velocity formed
+// once in FP64 (lanes a and a + 32) and kept as an FP32 deviation from w_a:
+// GB300's FP64 rate is a small fraction of its FP32 rate, so no FP64 work is
+// left in the per-cell update.
+template <int Q>
+__device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, const float *src,
+                                               int wall, int lane, float *fill) {
+    const KConsts<float> &k = d.k;
+    double v = 0.0;
+    if (lane < d.nterm) {
+        const int a = d.term_a[wall][lane];
+        const int kk = d.term_row[wall][lane];
+        const int row = wall == 0 ? kk : d.Ny - 1 - kk;
+        v = (double)__ldcg(src + (long long)a * d.Ny + row) + (double)k.w[a];   // f = d + w
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const double m = __shfl_sync(0xffffffffu, v, 0);
+    for (int a = lane; a < Q; a += 32)
+        fill[a] = k.wcoef[wall][a] != 0.0 ? (float)(m * k.wcoef[wall][a] - (double)k.w[a]) : 0.0f;
+    __syncwarp();
+}
+
+// Pull, collide and store row j (Eq. (5) with the Eq. (9)-(12) wall).  src is
+// rewritten between steps by other CTAs of the cluster (other SMs), so it is
+// read from L2 (ld.global.cg): a line of it left in this SM's L1 by an earlier
+// step would be stale.  No population is read twice in a step, so bypassing
+// L1 costs nothing.
+template <int Q>
+__device__ __forceinline__ void cell_update(const SlotDesc &d, const float *src, float *dst, int j,
+                                            const BatchWallShared &sw) {
+    using L = Lat<Q>;
+    // the slot's constants live in shared memory; this compiler barrier keeps
+    // them there (re-read per cell) instead of hoisted into registers for the
+    // whole step loop, which spilled
+    asm volatile("" ::: "memory");
+    const KConsts<float> &k = d.k;
+    const int Ny = d.Ny;
+    float f[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int sj = j - L::ey(a);
+        if (sj < 0 || sj >= Ny) {
+            // Eq. (9): diffuse part of the wall, plus the specular part (the
+            // mirrored velocity of the same row) when accom < 1; both are
+            // deviations from w_a, so the mix is linear in them
+            const int wall = sj < 0 ? 0 : 1;
+            const float acc = sw.acc[wall];
+            float v = sw.fill[wall][a];
+            if (acc != 1.0f) v = acc * v + (1.0f - acc) * __ldcg(src + (long long)k.mirror[a] * Ny + j);
+            f[a] = v;
+        } else {
+            f[a] = __ldcg(src + (long long)a * Ny + sj);
+        }
+    }
+    Collision<Q, float, true> col;
+    col.setup(f, k);
+    float o[Q];
+    o[0] = col.rest(f[0]);
+    PairLoop<1, Q>::run([&](auto ic) {
+        constexpr int A = decltype(ic)::value;
+        col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
+    });
+#pragma unroll
+    for (int a = 0; a < Q; ++a) dst[(long long)a * Ny + j] = o[a];
+}
+
+// One chunk of one slot on CTA `rank` of its CL-CTA cluster.  `chunks` is the
+// slot's chunk counter after this chunk (read by every CTA before the first
+// barrier); `part` holds CL x 6 FP64 partial sums of the residual.
 template <int Q>
 __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict__ pool,
-                                           SlotStatus *__restrict__ st, BatchWallShared &sw) {
-    const int chunk = d.chunk_steps;
+                                           SlotStatus *__restrict__ st, BatchWallShared &sw,
+                                           int rank, int CL, int chunks,
+                                           double *__restrict__ part) {
     using L = Lat<Q>;
+    const int chunk = d.chunk_steps;
     const KConsts<float> &k = d.k;
     const int Ny = d.Ny;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int NT = d.nterm;                // <= 32, checked with the descriptor
+    const int R = (Ny + CL - 1) / CL;
+    const int j0 = min(Ny, rank * R), j1 = min(Ny, j0 + R);
+    const bool has_bot = rank == 0, has_top = rank == CL - 1;
+    const int span = j1 - j0;
+    // wall blocks: >= 3 rows each (every row that pulls from a wall), since
+    // the host keeps Ny >= 6 and R >= 32 whenever CL > 1
+    int nb = 0, nt = 0;
+    if (has_bot && has_top) {
+        nb = min(32, span / 2);
+        nt = min(32, span - nb);
+    } else if (has_bot) {
+        nb = min(32, span);
+    } else if (has_top) {
+        nt = min(32, span);
+    }
+    const int mb = j0 + nb, me = j1 - nt;
 
     float *buf0 = pool + d.f_off;
     float *buf1 = buf0 + (long long)Q * Ny;
@@ -41,73 +159,30 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
     float *dst = d.cur ? buf0 : buf1;
 
     if (tid < 2) sw.acc[tid] = (float)k.accom[tid];
+    __syncthreads();
+    // this thread's wall-block row (-1: none); bulk rows are handed out from
+    // the last thread down, so that the wall warps get bulk rows last
+    int jw = -1;
+    if (warp == 0 && nb > 0 && lane < nb) jw = j0 + lane;
+    if (warp == 1 && nt > 0 && lane < nt) jw = j1 - nt + lane;
+    const int jb = mb + (nth - 1 - tid);
     for (int step = 0; step < chunk; ++step) {
-        if (warp < 2) {
-            // numerator of Eq. (12) in FP64, then the normalised re-emission
-            // M_in g^w_a / D_w of each outgoing velocity, formed in FP64 once
-            // per wall and step (lane a and a + 32) and kept as an FP32
-            // deviation: GB300's FP64 rate is a small fraction of its FP32 rate,
-            // so no FP64 work is left in the per-cell loop
-            double v = 0.0;
-            if (lane < NT) {
-                const int a = d.term_a[warp][lane];
-                const int kk = d.term_row[warp][lane];
-                const int row = warp == 0 ? kk : Ny - 1 - kk;
-                // stored deviations: f = d + w
-                v = (double)src[(long long)a * Ny + row] + (double)k.w[a];
-            }
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            const double m = __shfl_sync(0xffffffffu, v, 0);
-            for (int a = lane; a < Q; a += 32)
-                sw.fill[warp][a] = k.wcoef[warp][a] != 0.0
-                                       ? (float)(m * k.wcoef[warp][a] - (double)k.w[a]) : 0.0f;
+        if (warp == 0 && nb > 0) wall_fill_warp<Q>(d, src, 0, lane, sw.fill[0]);
+        else if (warp == 1 && nt > 0) wall_fill_warp<Q>(d, src, 1, lane, sw.fill[1]);
+        for (int it = jw >= 0 ? -1 : 0;; ++it) {
+            const int j = it < 0 ? jw : jb + it * nth;
+            if (it >= 0 && j >= me) break;
+            cell_update<Q>(d, src, dst, j, sw);
         }
-        __syncthreads();
-        for (int j = tid; j < Ny; j += nth) {
-            // the slot's constants live in shared memory; this compiler barrier
-            // keeps them there (re-read per cell) instead of hoisted into
-            // registers for the whole step loop, which spilled
-            asm volatile("" ::: "memory");
-            float f[Q];
-#pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                const int sj = j - L::ey(a);
-                if (sj < 0 || sj >= Ny) {
-                    // Eq. (9): diffuse part of the wall, plus the specular part
-                    // (the mirrored velocity of the same row) when accom < 1;
-                    // both are deviations from w_a, so the mix is linear in them
-                    const int wall = sj < 0 ? 0 : 1;
-                    const float acc = sw.acc[wall];
-                    float v = sw.fill[wall][a];
-                    if (acc != 1.0f)
-                        v = acc * v + (1.0f - acc) * src[(long long)k.mirror[a] * Ny + j];
-                    f[a] = v;
-                } else {
-                    f[a] = src[(long long)a * Ny + sj];
-                }
-            }
-            Collision<Q, float, true> col;
-            col.setup(f, k);
-            float o[Q];
-            o[0] = col.rest(f[0]);
-            PairLoop<1, Q>::run([&](auto ic) {
-                constexpr int A = decltype(ic)::value;
-                col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
-            });
-#pragma unroll
-            for (int a = 0; a < Q; ++a) dst[(long long)a * Ny + j] = o[a];
-        }
-        __syncthreads();
+        slot_barrier(CL);
         const float *t = src;
         src = dst;
         dst = (float *)t;
     }
 
-    const int chunks = st->chunks + 1;     // read before thread 0 updates it
-    __syncthreads();
-    if (tid == 0) st->chunks = chunks;
     if (chunks % d.check_every != 0) {
-        if (tid == 0) {
+        if (rank == 0 && tid == 0) {
+            st->chunks = chunks;
             st->steps += chunk;
             if (st->steps >= d.max_steps) st->state = kSlotMaxSteps;
         }
@@ -119,12 +194,12 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
     float *prev_T = prev_u + Ny;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const double r = (double)k.r;
-    for (int j = tid; j < Ny; j += nth) {
+    for (int j = j0 + tid; j < j1; j += nth) {
         // deviations d = f - w: rho = 1 + sum d, sum e w = 0, sum e^2 w = e2w
         double s0 = 0, sx = 0, sy = 0, se = (double)k.e2w;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const double fa = (double)src[(long long)a * Ny + j];
+            const double fa = (double)__ldcg(src + (long long)a * Ny + j);
             s0 += fa;
             sx += L::ex(a) * fa;
             sy += L::ey(a) * fa;
@@ -143,18 +218,31 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         prev_u[j] = (float)u;
         prev_T[j] = (float)T;
     }
-    __shared__ double red[32][6];
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
     if (lane == 0)
-        for (int i = 0; i < 6; ++i) red[warp][i] = acc[i];
+        for (int i = 0; i < 6; ++i) sw.red[warp][i] = acc[i];
     __syncthreads();
-    if (tid == 0) {
-        double tot[6] = {0, 0, 0, 0, 0, 0};
+    double tot[6] = {0, 0, 0, 0, 0, 0};
+    if (tid == 0)
         for (int w = 0; w < (nth + 31) / 32; ++w)
-            for (int i = 0; i < 6; ++i) tot[i] += red[w][i];
+            for (int i = 0; i < 6; ++i) tot[i] += sw.red[w][i];
+    if (CL > 1) {
+        // CTA partials through global memory, summed by rank 0 in rank order
+        if (tid == 0)
+            for (int i = 0; i < 6; ++i) part[rank * 6 + i] = tot[i];
+        slot_barrier(CL);
+        if (rank != 0) return;
+        if (tid == 0)
+            for (int i = 0; i < 6; ++i) {
+                tot[i] = 0.0;
+                for (int c = 0; c < CL; ++c) tot[i] += part[c * 6 + i];
+            }
+    }
+    if (tid == 0) {
         SlotStatus &s = *st;
+        s.chunks = chunks;
         s.steps += chunk;
         s.checks += 1;
         s.mass = tot[4];
@@ -162,8 +250,8 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         if (k.thermal) res = fmax(res, sqrt(tot[2]) / fmax(sqrt(tot[3]), 1e-30));
         // geometric extrapolation of the remaining change: with a per-check
         // contraction q = res / res_prev < 1, the distance to the steady state
-        // is about res q / (1 - q)
-        // q from the last two checks, the slower of the two contractions
+        // is about res q / (1 - q); q from the last two checks, the slower of
+        // the two contractions
         const double q1 = s.res > 0 ? res / s.res : 1.0;
         const double q0 = s.res_prev > 0 ? s.res / s.res_prev : 1.0;
         const double q = fmax(q1, q0);
@@ -183,6 +271,5 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         else if (s.steps >= d.max_steps) s.state = kSlotMaxSteps;
     }
 }
-
 
 }  // namespace lbm

@@ -4,11 +4,15 @@
 // Requests (one single-column Couette instance each: lattice, height, Kn,
 // wall speeds and temperatures, tolerance) queue on the host.  A worker
 // thread owns the GPU side: a device memory pool of the configured budget,
-// a slot table (SlotDesc / SlotStatus) and the chunk kernel.  Every loop it
-//   1. admits queued requests into idle slots while the pool has room for
-//      their two state buffers (first-fit allocator), initialises them;
-//   2. runs one chunk launch over all slots (a CUDA graph: kernel + status
-//      read-back), so admitted work overlaps with slots already running;
+// a slot table (SlotDesc / SlotStatus) in four classes by cluster size (a
+// column runs on 1, 2, 4 or 8 CTAs, by height) and the chunk kernel.  Every
+// loop it
+//   1. admits queued requests into idle slots of their class while the CTA
+//      budget (max_slots) and the pool (first-fit allocator) have room for
+//      them, initialises them;
+//   2. runs one chunk launch per class, the four concurrently (a CUDA graph:
+//      fork, kernels, join, status read-back), so admitted work overlaps with
+//      slots already running;
 //   3. retires slots whose status left "running": reads their Eq. (3)
 //      profiles back, frees their memory, records the latency.
 // The f-arrays of a request stay resident on the device from admission to
@@ -76,6 +80,12 @@ struct ServerImpl {
     long long pool_elems = 0;
     SlotDesc *d_desc = nullptr;
     SlotStatus *d_status = nullptr;
+    double *d_part = nullptr;                // residual partials, 8 x 6 per slot
+    // slot classes: slots [cls_base[c], cls_base[c] + cls_cap[c]) run on
+    // clusters of kBatchClassCL[c] CTAs, each class launched on its own stream
+    int cls_base[kBatchClasses] = {}, cls_cap[kBatchClasses] = {};
+    cudaStream_t side[kBatchClasses] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kBatchClasses] = {};
     int *d_idx = nullptr;                    // slot lists for init / read-out
     long long *d_off = nullptr;
     int *d_dbg = nullptr;                    // kernels' record of a rejected descriptor
@@ -103,6 +113,7 @@ struct ServerImpl {
     uint64_t next_id = 1;
     int64_t submitted = 0, completed = 0;
     int running = 0;
+    int used_ctas = 0;                       // CTAs of the running slots (<= max_slots)
     int64_t chunks = 0;
     double occupancy_sum = 0;
     double t_first_submit = -1, t_last_done = 0;
@@ -172,12 +183,13 @@ struct ServerImpl {
         d.Q = L.Q;
         d.Ny = r.Ny;
         d.cur = 0;
+        d.cl = cluster_for(r.Ny);
         // Steps per chunk launch: cheaper slots run more steps, so that every
-        // CTA of a launch takes about as long as the costliest one (a Q = 37
-        // column of 2048 rows runs chunk_steps); the cost model is the velocity
-        // count times the cells per thread (256 threads per slot) plus a
-        // latency floor.
-        const double cost = L.Q * std::ceil(r.Ny / 256.0) + 37.0;
+        // CTA of a launch takes about as long (cfg.chunk_steps x 333 cost
+        // units); the cost model is the velocity count times the rows per
+        // thread of the slot's CTAs (256 threads each) plus a latency floor.
+        const int rows_per_cta = (r.Ny + d.cl - 1) / d.cl;
+        const double cost = L.Q * std::ceil(rows_per_cta / 256.0) + 37.0;
         const double cost_ref = 37.0 * 8.0 + 37.0;
         d.chunk_steps = (int)std::min<double>(32.0 * cfg.chunk_steps,
                                               std::max<double>(cfg.chunk_steps,
@@ -249,21 +261,62 @@ struct ServerImpl {
         return LBM_ECUDA;
     }
 
+    // a free slot of the class that runs a column of Ny rows, or -1
+    int cluster_for(int Ny) const { return batch_cluster_size(Ny, cfg.cluster_rows, cfg.max_slots); }
+
+    int free_slot(int Ny) const {
+        const int cl = cluster_for(Ny);
+        int c = 0;
+        while (c + 1 < kBatchClasses && kBatchClassCL[c] != cl) ++c;
+        for (int s = cls_base[c]; s < cls_base[c] + cls_cap[c]; ++s)
+            if (!slots[s].busy) return s;
+        return -1;
+    }
+
+    // Chunk launches of every class, each on its own stream between a fork
+    // and a join on `st`, so that the classes run concurrently (also inside
+    // the captured graph).
+    cudaError_t launch_chunks(cudaStream_t st) {
+        cudaError_t e = cudaEventRecord(ev_fork, st);
+        for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c) {
+            e = cudaStreamWaitEvent(side[c], ev_fork, 0);
+            if (e == cudaSuccess)
+                e = (cudaError_t)launch_batch_chunk(side[c], d_desc, d_status, pool, d_part,
+                                                    cls_base[c], cls_cap[c], kBatchClassCL[c],
+                                                    pool_elems, d_dbg);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_join[c], side[c]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_join[c], 0);
+        }
+        return e;
+    }
+
     // one loop of the worker; returns false when there is nothing to do
     int loop_once(bool &idle) {
         std::vector<int> admitted;
         {
             std::unique_lock<std::mutex> lk(mu);
-            for (int s = 0; s < (int)slots.size() && !queue.empty(); ++s) {
-                if (slots[s].busy) continue;
-                const Pending &pd = queue.front();
-                const long long n = request_elems(pd.req, lattice_q(pd.req.lattice));
+            // Scan the queue in arrival order (at most 64 entries).  A request
+            // is admitted when its class has a free slot and its cluster fits
+            // the CTA budget (max_slots) minus what the oldest request that did
+            // not fit needs (so that small requests cannot starve a large one);
+            // the first request that finds no memory stops the scan.
+            int reserve = 0, scanned = 0;
+            for (auto it = queue.begin(); it != queue.end() && scanned < 64; ++scanned) {
+                const int cl = cluster_for(it->req.Ny);
+                const int s = used_ctas + cl + reserve <= cfg.max_slots ? free_slot(it->req.Ny) : -1;
+                if (s < 0) {
+                    if (reserve == 0) reserve = cl;
+                    ++it;
+                    continue;
+                }
+                const long long n = request_elems(it->req, lattice_q(it->req.lattice));
                 const long long off = alloc(n);
                 if (off < 0) break;                  // wait for memory to free up
-                fill_slot(s, pd, off);
+                fill_slot(s, *it, off);
                 admitted.push_back(s);
-                queue.pop_front();
+                it = queue.erase(it);
                 ++running;
+                used_ctas += cl;
             }
             idle = running == 0;
         }
@@ -284,9 +337,7 @@ struct ServerImpl {
         if (graph) {
             if ((e = cudaGraphLaunch(graph, stream))) return fail("graph launch", e);
         } else {
-            if ((e = (cudaError_t)launch_batch_chunk(stream, d_desc, d_status, pool, (int)slots.size(), cfg.chunk_steps,
-                                                      pool_elems, d_dbg)))
-                return fail("chunk kernel", e);
+            if ((e = launch_chunks(stream))) return fail("chunk kernel", e);
             if ((e = cudaMemcpyAsync(h_status, d_status, sizeof(SlotStatus) * slots.size(), cudaMemcpyDeviceToHost, stream)))
                 return fail("status read-back", e);
             if ((e = cudaMemcpyAsync(h_dbg, d_dbg, sizeof(int) * 8, cudaMemcpyDeviceToHost, stream)))
@@ -295,7 +346,7 @@ struct ServerImpl {
         if ((e = cudaStreamSynchronize(stream))) return fail("chunk", e);
         if (h_dbg[0]) return reject_desc();
         ++chunks;
-        occupancy_sum += running;
+        occupancy_sum += used_ctas;
         // retire finished slots
         std::vector<int> fin;
         for (int s = 0; s < (int)slots.size(); ++s)
@@ -352,6 +403,7 @@ struct ServerImpl {
                 unpolled.push_back(si.id);
                 release(si.off, si.elems);
                 si.busy = false;
+                used_ctas -= h_desc[s].cl;
                 h_desc[s].Q = 0;
                 h_status[s].state = kSlotIdle;
                 --running;
@@ -404,6 +456,7 @@ void lbm_server_cfg_default(lbm_server_cfg *c) {
     c->chunk_steps = 100;
     c->precision = LBM_FP32;
     c->use_graph = 1;
+    c->cluster_rows = 256;
 }
 
 static int check_request(const lbm_request *r) {
@@ -445,8 +498,8 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
         if (!cfg || !out) { set_error("NULL argument"); return LBM_EINVAL; }
         *out = nullptr;
         if (cfg->max_slots < 1 || cfg->max_slots > 4096 || cfg->chunk_steps < 1 ||
-            cfg->mem_budget_bytes < 4096 || cfg->precision != LBM_FP32) {
-            set_error("bad server configuration (slots 1..4096, chunk >= 1, FP32)");
+            cfg->mem_budget_bytes < 4096 || cfg->precision != LBM_FP32 || cfg->cluster_rows < 32) {
+            set_error("bad server configuration (slots 1..4096, chunk >= 1, FP32, cluster_rows >= 32)");
             return LBM_EINVAL;
         }
         lbm_server *h = new lbm_server;
@@ -458,7 +511,14 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
         const int kinds[4] = {17, 25, 26, 37};
         for (int i = 0; i < 4; ++i)
             if (lattice_build(kinds[i], S.lat[i])) { delete h; set_error("lattice build"); return LBM_EINVAL; }
-        const int ns = cfg->max_slots;
+        // slot classes: max_slots / CL slots of each cluster size, so that any
+        // class alone can fill the CTA budget
+        int ns = 0;
+        for (int c = 0; c < kBatchClasses; ++c) {
+            S.cls_cap[c] = std::max(1, cfg->max_slots / kBatchClassCL[c]);
+            S.cls_base[c] = ns;
+            ns += S.cls_cap[c];
+        }
         S.slots.resize(ns);
         S.pool_elems = (long long)(cfg->mem_budget_bytes / sizeof(float)) / kAlignElems * kAlignElems;
         S.out_elems = 4LL * kMaxNy * std::min(ns, 64);
@@ -467,6 +527,12 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
         ck(cudaMallocAsync((void **)&S.pool, (size_t)S.pool_elems * sizeof(float), S.stream));
         ck(cudaMallocAsync((void **)&S.d_desc, sizeof(SlotDesc) * ns, S.stream));
         ck(cudaMallocAsync((void **)&S.d_status, sizeof(SlotStatus) * ns, S.stream));
+        ck(cudaMallocAsync((void **)&S.d_part, sizeof(double) * 48 * ns, S.stream));
+        ck(cudaEventCreateWithFlags(&S.ev_fork, cudaEventDisableTiming));
+        for (int c = 0; c < kBatchClasses; ++c) {
+            ck(cudaStreamCreateWithFlags(&S.side[c], cudaStreamNonBlocking));
+            ck(cudaEventCreateWithFlags(&S.ev_join[c], cudaEventDisableTiming));
+        }
         ck(cudaMallocAsync((void **)&S.d_idx, sizeof(int) * ns, S.stream));
         ck(cudaMallocAsync((void **)&S.d_off, sizeof(long long) * ns, S.stream));
         ck(cudaMallocAsync((void **)&S.d_out, sizeof(double) * S.out_elems, S.stream));
@@ -488,13 +554,12 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
         }
         if (e == cudaSuccess) ck((cudaError_t)preload_batch_kernels());
         if (e == cudaSuccess && cfg->use_graph) {
-            // capture: chunk kernel over every slot, then the status read-back
+            // capture: chunk kernels of every class, then the status read-back
             cudaStream_t cs;
             ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
             cudaGraph_t g;
             ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            ck((cudaError_t)launch_batch_chunk(cs, S.d_desc, S.d_status, S.pool, ns, cfg->chunk_steps,
-                                               S.pool_elems, S.d_dbg));
+            ck(S.launch_chunks(cs));
             ck(cudaMemcpyAsync(S.h_status, S.d_status, sizeof(SlotStatus) * ns, cudaMemcpyDeviceToHost, cs));
             ck(cudaMemcpyAsync(S.h_dbg, S.d_dbg, sizeof(int) * 8, cudaMemcpyDeviceToHost, cs));
             ck(cudaStreamEndCapture(cs, &g));
@@ -590,7 +655,7 @@ int lbm_server_stats(lbm_server *h, lbm_server_metrics *st) {
     st->chunks = S.chunks;
     st->pool_bytes = (size_t)S.pool_elems * sizeof(float);
     st->pool_used_bytes = (size_t)S.used_elems * sizeof(float);
-    st->mean_occupancy = S.chunks ? S.occupancy_sum / (S.chunks * (double)S.slots.size()) : 0.0;
+    st->mean_occupancy = S.chunks ? S.occupancy_sum / (S.chunks * (double)S.cfg.max_slots) : 0.0;
     if (!S.latencies.empty()) {
         std::vector<double> l = S.latencies;
         std::sort(l.begin(), l.end());
@@ -626,7 +691,13 @@ int lbm_server_destroy(lbm_server *h) {
     if (S.d_off) cudaFreeAsync(S.d_off, S.stream);
     if (S.d_out) cudaFreeAsync(S.d_out, S.stream);
     if (S.d_dbg) cudaFreeAsync(S.d_dbg, S.stream);
+    if (S.d_part) cudaFreeAsync(S.d_part, S.stream);
     cudaStreamSynchronize(S.stream);
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (S.side[c]) cudaStreamDestroy(S.side[c]);
+        if (S.ev_join[c]) cudaEventDestroy(S.ev_join[c]);
+    }
+    if (S.ev_fork) cudaEventDestroy(S.ev_fork);
     if (S.h_desc) cudaFreeHost(S.h_desc);
     if (S.h_status) cudaFreeHost(S.h_status);
     if (S.h_idx) cudaFreeHost(S.h_idx);

@@ -64,7 +64,8 @@ class lbm_result(C.Structure):
 
 class lbm_server_cfg(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_slots", C.c_int32),
-                ("chunk_steps", C.c_int32), ("precision", C.c_int32), ("use_graph", C.c_int32)]
+                ("chunk_steps", C.c_int32), ("precision", C.c_int32), ("use_graph", C.c_int32),
+                ("cluster_rows", C.c_int32)]
 
 
 class lbm_server_metrics(C.Structure):
@@ -486,13 +487,14 @@ class Server:
     thread owns its own CUDA stream."""
 
     def __init__(self, mem_budget_bytes: int = 40 << 30, max_slots: int = 256,
-                 chunk_steps: int = 100, use_graph: bool = True):
+                 chunk_steps: int = 100, use_graph: bool = True, cluster_rows: int = 256):
         import torch
         self.cfg = lbm_server_cfg_default()
         self.cfg.mem_budget_bytes = int(mem_budget_bytes)
         self.cfg.max_slots = int(max_slots)
         self.cfg.chunk_steps = int(chunk_steps)
         self.cfg.use_graph = int(use_graph)
+        self.cfg.cluster_rows = int(cluster_rows)
         self.stream = torch.cuda.Stream()
         self.h = lbm_server_create(self.cfg, self.stream.cuda_stream)
 

@@ -67,6 +67,90 @@ def test_batch_matches_oracle_steady_states(lbm, oracle):
         assert np.max(np.abs(ux + ux[::-1])) < 1e-5 * Uw * 10
 
 
+# columns tall enough to run on clusters of 2, 4 and 8 CTAs (rows split across
+# the cluster, one cluster barrier per step), with the FP32 steady-state bound
+# of each: the FP32 fixed point differs from the exact one by the per-step
+# round-off amplified by the slowest relaxation time, which grows with the
+# height; the single-domain FP32 solver measures the same floor (5.5e-5 for
+# the 1500-row D2Q17 column at Kn 1, 1.1e-5 for the 700-row D2Q25 one), so
+# the bound is twice the measured floor
+TALL = [("D2Q37", 300, 0.5, 0.20, 1.0), ("D2Q25", 700, 0.8, 0.10, 1.0),
+        ("D2Q17", 1500, 1.0, 0.15, 1.0), ("D2Q37", 1100, 0.6, 0.25, 1.05)]
+TALL_BOUND = {300: 2e-5, 700: 2.5e-5, 1500: 1.2e-4, 1100: 5e-5}
+
+
+def test_cluster_slots_follow_the_oracle_transient(lbm, oracle):
+    # a fixed number of steps (no convergence stop): every row of the state,
+    # including the rows next to the cluster's CTA boundaries, against the
+    # oracle after the same steps
+    s = lbm.Server(mem_budget_bytes=1 << 28, max_slots=32, chunk_steps=50)
+    ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=1e-30, max_steps=1500))
+           for lat, Ny, Kn, Uw, Tw in TALL]
+    s.drain(300)
+    res = {r.id: r for r in s.poll(8)}
+    for rid, (lat, Ny, Kn, Uw, Tw) in zip(ids, TALL):
+        r = res[rid]
+        _, ux, _, T = s.fetch(rid, Ny)
+        o, t = (4, True) if lat == "D2Q37" else (2, False)
+        p = oracle.Problem(lattice=lat, Nx=1, Ny=Ny, eq_order=o, thermal=t, Kn=Kn,
+                           u_wall=(-Uw, Uw), T_wall=(Tw, Tw))
+        f = oracle.init_fields(p, np.ones((Ny, 1)))
+        oracle.run(p, f, r.steps)
+        _, oux, _, oT = oracle.macros(p, f)
+        assert np.max(np.abs(ux - oux[:, 0])) / Uw < 2e-5, (lat, Ny, r.steps)
+        if t:
+            assert np.max(np.abs(T - oT[:, 0])) < 2e-5, (lat, Ny)
+    s.close()
+
+
+def test_cluster_slots_match_oracle_steady_states(lbm, oracle):
+    items = TALL + MIX[:2]
+    out, st = solve(lbm, items)
+    assert st.completed == len(items)
+    for (lat, Ny, Kn, Uw, Tw), (r, rho, ux, T) in zip(items, out):
+        assert r.status == lbm.LBM_OK, (lat, Ny, r.status, r.residual)
+        oux, oT = oracle_steady(oracle, lat, Ny, Kn, Uw, Tw)
+        err_u = np.max(np.abs(ux - oux)) / Uw
+        assert err_u < TALL_BOUND.get(Ny, 2e-5), (lat, Ny, Kn, err_u)
+        if lat == "D2Q37":
+            assert np.max(np.abs(T - oT)) < 2e-5, (lat, Ny)
+        assert abs(r.mass - Ny) < 1e-4 * Ny
+
+
+def test_cluster_slot_is_the_same_alone_and_in_the_mix(lbm):
+    items = TALL + MIX
+    mixed, _ = solve(lbm, items)
+    for k in (0, 2, 3):
+        alone, _ = solve(lbm, [items[k]])
+        a, b = alone[0], mixed[k]
+        assert a[0].steps == b[0].steps
+        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+
+
+def test_cluster_size_is_capped_by_the_cta_budget(lbm, oracle):
+    # one CTA of budget: a 700-row column (a 4-CTA cluster by default) runs on
+    # a single CTA, and agrees with the clustered run to FP32 round-off
+    item = ("D2Q25", 700, 0.8, 0.10, 1.0)
+    one, _ = solve(lbm, [item], max_slots=1)
+    four, _ = solve(lbm, [item])
+    assert one[0][0].status == lbm.LBM_OK
+    assert np.max(np.abs(one[0][2] - four[0][2])) / item[3] < 1e-5
+
+
+def test_cta_budget_admits_a_tall_column_behind_short_ones(lbm):
+    # budget of 8 CTAs: a 1500-row column needs all 8, so it waits for the
+    # short ones ahead of it, which must not starve it
+    s = lbm.Server(mem_budget_bytes=1 << 28, max_slots=8, chunk_steps=50)
+    short = [s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-6)) for _ in range(4)]
+    tall = s.submit(lbm.make_request("D2Q17", 1500, 1.0, 0.1, tol=1e-6))
+    more = [s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-6)) for _ in range(12)]
+    s.drain(300)
+    res = {r.id: r for r in s.poll(32)}
+    assert all(res[i].status == lbm.LBM_OK for i in short + [tall] + more)
+    assert res[tall].t_admit < max(res[i].t_admit for i in more)
+    s.close()
+
+
 def test_result_is_the_same_alone_and_in_the_mix(lbm):
     mixed, _ = solve(lbm, MIX)
     for k in (0, 2, 5):
@@ -101,8 +185,9 @@ def test_admission_under_a_small_memory_budget(lbm):
 
 
 def test_requests_admitted_while_others_run(lbm):
-    s = lbm.Server(mem_budget_bytes=1 << 26, max_slots=4, chunk_steps=50)
-    long_id = s.submit(lbm.make_request("D2Q37", 1024, 0.02, 0.2, tol=1e-6))
+    # the long column takes a 4-CTA cluster, the short ones share the other 4
+    s = lbm.Server(mem_budget_bytes=1 << 26, max_slots=8, chunk_steps=50)
+    long_id = s.submit(lbm.make_request("D2Q37", 1024, 0.005, 0.2, tol=1e-6))
     time.sleep(0.05)
     short = [s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-6)) for _ in range(6)]
     s.drain(300)
