@@ -143,6 +143,9 @@ def _request(lbm, inst, tol):
                             max_steps=20_000_000)
 
 
+Q_OF = {"D2Q17": 17, "D2Q25": 25, "D2Q25b": 25, "D2Q37": 37}
+
+
 def resident_ctas() -> int:
     """CTA budget of the server: every batch CTA resident at once (two 256-thread
     CTAs per SM)."""
@@ -207,7 +210,11 @@ def run_batched(lbm, n=256, seed=7, tol=1e-5, baseline_every=16, baseline_budget
             "p50_latency_s": st.p50_latency_s,
             "p99_latency_s": st.p99_latency_s, "mean_occupancy": st.mean_occupancy,
             "total_steps": int(sum(res[i].steps for i in ids)),
-            "cell_steps": int(sum(res[i].steps * it.Ny for i, it in zip(ids, insts)))}
+            "cell_steps": int(sum(res[i].steps * it.Ny for i, it in zip(ids, insts))),
+            # one read and one write of every population per lattice update,
+            # over the makespan (the pool is L2-resident: an L2 rate)
+            "achieved_GBps": sum(res[i].steps * it.Ny * 8 * Q_OF[it.lattice]
+                                 for i, it in zip(ids, insts)) / makespan / 1e9}
 
 
 def run_serving(lbm, n=10000, seed=11, rate=200.0, tol=1e-5):
@@ -238,6 +245,27 @@ def run_serving(lbm, n=10000, seed=11, rate=200.0, tol=1e-5):
             "cell_steps": int(cell_steps), "GLUPS": cell_steps / wall / 1e9,
             "max_residual": max((res[i].residual for i in ids if res[i].status == 0),
                                 default=None)}
+
+
+def run_slots(lbm, n, lattice, Ny, Kn, steps, cluster_rows=256):
+    """Rate of the batched path at a fixed step count: n identical
+    single-column requests (walls -+0.1) that never meet their tolerance,
+    each run for `steps` steps (rounded up to whole chunks); wall time from
+    the first submit to the drain."""
+    srv = lbm.Server(mem_budget_bytes=8 << 30, max_slots=resident_ctas(), chunk_steps=100,
+                     cluster_rows=cluster_rows)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        srv.submit(lbm.make_request(lattice, Ny, Kn, 0.1, tol=1e-30, max_steps=steps))
+    srv.drain(600)
+    wall = time.perf_counter() - t0
+    res = srv.poll(n)
+    srv.close()
+    mean_steps = sum(r.steps for r in res) / len(res)
+    return {"slots": n, "lattice": lattice, "Ny": Ny, "Kn": Kn, "cluster_rows": cluster_rows,
+            "mean_steps": mean_steps, "wall_s": wall,
+            "us_per_step_per_slot": wall / mean_steps * 1e6,
+            "GLUPS": n * mean_steps * Ny / wall / 1e9}
 
 
 def run_column_fp64(lbm, steps=20000):
@@ -348,9 +376,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the per-variant timing diagnostic")
-    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "serving"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "serving", "slots"],
                     help="grid: the D2Q37 4096x2048 line (default, also runs the batched "
-                         "workload and a shortened serving run); batched / serving: only that")
+                         "workload and a shortened serving run); batched / serving: only that; "
+                         "slots: batched-path rate of --slots identical columns")
+    ap.add_argument("--slots", type=int, default=1)
+    ap.add_argument("--lattice", default="D2Q37", choices=["D2Q17", "D2Q25", "D2Q37"])
+    ap.add_argument("--Kn", type=float, default=0.005)
+    ap.add_argument("--slot-steps", type=int, default=20000)
+    ap.add_argument("--cluster-rows", type=int, default=256)
     ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true",
                     help="grid line only (skip the batched and serving runs)")
@@ -376,10 +410,15 @@ def main():
         dist.init_process_group("nccl")
 
     lbm.load()
-    if args.workload in ("batched", "serving"):
+    if args.workload in ("batched", "serving", "slots"):
         if rank == 0:
-            r = run_batched(lbm) if args.workload == "batched" else \
-                run_serving(lbm, n=args.serving_requests)
+            if args.workload == "batched":
+                r = run_batched(lbm)
+            elif args.workload == "serving":
+                r = run_serving(lbm, n=args.serving_requests)
+            else:
+                r = run_slots(lbm, args.slots, args.lattice, args.Ny, args.Kn, args.slot_steps,
+                              args.cluster_rows)
             print(json.dumps({"workload": args.workload, **r}))
         return 0
     cfg = lbm.Config(lattice="D2Q37", Nx=args.Nx, Ny=args.Ny, eq_order=4, thermal=True,

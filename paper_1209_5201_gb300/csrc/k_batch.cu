@@ -59,6 +59,7 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
     __shared__ SlotDesc sd;
     __shared__ BatchWallShared sw;
     __shared__ int s_chunks;
+    extern __shared__ __align__(16) float batch_sm[];
     const int slot = slot0 + blockIdx.x / CL;
     const int rank = CL == 1 ? 0 : (int)cluster_rank();
     load_desc(desc + slot, &sd);
@@ -68,12 +69,15 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
     if (!desc_ok(sd, pool_elems, slot, 1, dbg) || sd.cl != CL) return;
     double *pp = part + (long long)slot * 48;
     switch (sd.Q) {
-    case 17: batch_slot<17>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp); break;
-    case 25: batch_slot<25>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp); break;
-    case 37: batch_slot<37>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp); break;
+    case 17: batch_slot<17>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp, batch_sm); break;
+    case 25: batch_slot<25>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp, batch_sm); break;
+    case 37: batch_slot<37>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp, batch_sm); break;
     default: break;
     }
-    if (rank == 0 && threadIdx.x == 0) desc[slot].cur = (sd.cur + sd.chunk_steps) & 1;
+    // the global-memory path leaves the state in the other buffer after an odd
+    // chunk; the shared-memory path writes it back where it came from
+    const bool smem = (sd.Ny + CL - 1) / CL <= kSmemRows;
+    if (!smem && rank == 0 && threadIdx.x == 0) desc[slot].cur = (sd.cur + sd.chunk_steps) & 1;
 }
 
 // Rest equilibrium f~* = rho0 w_a of newly admitted slots, stored as the
@@ -169,7 +173,9 @@ __global__ void k_batch_macros(const SlotDesc *__restrict__ desc, const float *_
 // Load the batch kernels' module now (not lazily during a stream capture).
 int preload_batch_kernels() {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, k_batch_chunk);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_batch_chunk);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_batch_init);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_batch_macros);
     return (int)e;
@@ -180,15 +186,15 @@ int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, floa
                        int *dbg) {
     if (nlanes <= 0) return 0;
     if (CL == 1) {
-        k_batch_chunk<<<nlanes, kBatchThreads, 0, st>>>(desc, status, pool, part, slot0, 1,
-                                                        pool_elems, dbg);
+        k_batch_chunk<<<nlanes, kBatchThreads, kSmemBytes, st>>>(desc, status, pool, part, slot0,
+                                                                 1, pool_elems, dbg);
         return (int)cudaGetLastError();
     }
     if (CL != 2 && CL != 4 && CL != 8) return (int)cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nlanes * CL));
     cfg.blockDim = dim3(kBatchThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kSmemBytes;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;

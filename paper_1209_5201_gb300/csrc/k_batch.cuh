@@ -6,8 +6,12 @@
 // With Nx = 1 the pull of Eq. (5) only shifts in y: f_in(j, a) =
 // f~*(j - e_ay, a).  A slot runs on a cluster of CL CTAs (CL = 1, 2, 4 or 8,
 // fixed by its height): CTA `rank` owns rows [rank R, rank R + R), R =
-// ceil(Ny / CL); the state stays in global memory (L2-resident) and a cluster
-// barrier with release / acquire semantics separates the steps.
+// ceil(Ny / CL), and a cluster barrier with release / acquire semantics
+// separates the steps.  When R <= kSmemRows the CTA keeps its rows' two state
+// buffers in shared memory for the whole chunk (loaded from the pool at the
+// start, written back at the end) and pulls the <= 3 rows it needs from each
+// neighbour through distributed shared memory; taller slots keep the state in
+// global memory (L2-resident) and read it with ld.global.cg.
 //
 // Row mapping inside a CTA: warp 0 of the bottom CTA owns the (up to) 32
 // lowest rows and warp 1 of the top CTA the 32 highest; each of those warps
@@ -55,21 +59,83 @@ __device__ __forceinline__ void slot_barrier(int CL) {
     asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
 }
 
+// Rows of a CTA's shared-memory state: two buffers of Q x kSmemRows floats.
+constexpr int kSmemRows = 256;
+constexpr int kSmemBytes = 2 * kMaxQ * kSmemRows * (int)sizeof(float);
+
+// Generic address of the same shared-memory location in CTA `rank` of the
+// cluster (distributed shared memory).
+__device__ __forceinline__ float *map_rank(float *p, unsigned rank) {
+    unsigned long long out;
+    asm volatile("mapa.u64 %0, %1, %2;\n" : "=l"(out) : "l"((unsigned long long)p), "r"(rank));
+    return (float *)out;
+}
+
+// Slot state in global memory (pool), two buffers of [Q][Ny]; a step reads
+// `src` and writes `dst`, rows of any CTA of the cluster.
+struct GlobalState {
+    const float *src;
+    float *dst;
+    int Ny;
+    // population a of slot row `row` of the current state (coherent L2 read:
+    // another SM may have written it)
+    __device__ __forceinline__ float ld(int a, int row) const {
+        return __ldcg(src + (long long)a * Ny + row);
+    }
+    __device__ __forceinline__ float ld_own(int a, int row) const { return ld(a, row); }
+    __device__ __forceinline__ void st(int a, int row, float v) const {
+        dst[(long long)a * Ny + row] = v;
+    }
+    __device__ __forceinline__ void flip() {
+        const float *t = src;
+        src = dst;
+        dst = (float *)t;
+    }
+};
+
+// Slot state in the cluster's shared memory: this CTA holds rows [j0, j0 + R)
+// as buf[b][a][row - j0] (b = current buffer); lo / hi are the same buffers of
+// the neighbouring CTAs (rows j0 - R .., j0 + R ..), null at the slot's ends.
+struct SmemState {
+    float *buf;                // local buffers, 2 x Q x R floats
+    const float *lo, *hi;      // neighbours' buffers (distributed shared memory)
+    int R, j0, QR, b;
+    __device__ __forceinline__ float ld(int a, int row) const {
+        int lr = row - j0;
+        const float *p = buf;
+        if (lr < 0) {
+            p = lo;
+            lr += R;
+        } else if (lr >= R) {
+            p = hi;
+            lr -= R;
+        }
+        return p[b * QR + a * R + lr];
+    }
+    __device__ __forceinline__ float ld_own(int a, int row) const {
+        return buf[b * QR + a * R + row - j0];
+    }
+    __device__ __forceinline__ void st(int a, int row, float v) const {
+        buf[(b ^ 1) * QR + a * R + row - j0] = v;
+    }
+    __device__ __forceinline__ void flip() { b ^= 1; }
+};
+
 // Numerator of Eq. (12) for `wall` summed by one full warp in FP64, and the
 // normalised re-emission M_in g^w_a / D_w of each outgoing velocity formed
 // once in FP64 (lanes a and a + 32) and kept as an FP32 deviation from w_a:
 // GB300's FP64 rate is a small fraction of its FP32 rate, so no FP64 work is
-// left in the per-cell update.
-template <int Q>
-__device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, const float *src,
-                                               int wall, int lane, float *fill) {
+// left in the per-cell update.  The wall rows belong to this CTA.
+template <int Q, class State>
+__device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, const State &S, int wall,
+                                               int lane, float *fill) {
     const KConsts<float> &k = d.k;
     double v = 0.0;
     if (lane < d.nterm) {
         const int a = d.term_a[wall][lane];
         const int kk = d.term_row[wall][lane];
         const int row = wall == 0 ? kk : d.Ny - 1 - kk;
-        v = (double)__ldcg(src + (long long)a * d.Ny + row) + (double)k.w[a];   // f = d + w
+        v = (double)S.ld_own(a, row) + (double)k.w[a];   // f = d + w
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const double m = __shfl_sync(0xffffffffu, v, 0);
@@ -78,13 +144,12 @@ __device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, const float *s
     __syncwarp();
 }
 
-// Pull, collide and store row j (Eq. (5) with the Eq. (9)-(12) wall).  src is
-// rewritten between steps by other CTAs of the cluster (other SMs), so it is
-// read from L2 (ld.global.cg): a line of it left in this SM's L1 by an earlier
-// step would be stale.  No population is read twice in a step, so bypassing
-// L1 costs nothing.
-template <int Q>
-__device__ __forceinline__ void cell_update(const SlotDesc &d, const float *src, float *dst, int j,
+// Pull, collide and store row j (Eq. (5) with the Eq. (9)-(12) wall).  EDGE:
+// the row is within 3 rows of its CTA's first or last row, so a source may lie
+// beyond the slot's walls or in a neighbouring CTA; otherwise every source is
+// one of this CTA's rows.
+template <int Q, bool EDGE, class State>
+__device__ __forceinline__ void cell_update(const SlotDesc &d, const State &S, int j,
                                             const BatchWallShared &sw) {
     using L = Lat<Q>;
     // the slot's constants live in shared memory; this compiler barrier keeps
@@ -97,17 +162,19 @@ __device__ __forceinline__ void cell_update(const SlotDesc &d, const float *src,
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int sj = j - L::ey(a);
-        if (sj < 0 || sj >= Ny) {
+        if (!EDGE) {
+            f[a] = S.ld_own(a, sj);
+        } else if (sj < 0 || sj >= Ny) {
             // Eq. (9): diffuse part of the wall, plus the specular part (the
             // mirrored velocity of the same row) when accom < 1; both are
             // deviations from w_a, so the mix is linear in them
             const int wall = sj < 0 ? 0 : 1;
             const float acc = sw.acc[wall];
             float v = sw.fill[wall][a];
-            if (acc != 1.0f) v = acc * v + (1.0f - acc) * __ldcg(src + (long long)k.mirror[a] * Ny + j);
+            if (acc != 1.0f) v = acc * v + (1.0f - acc) * S.ld_own(k.mirror[a], j);
             f[a] = v;
         } else {
-            f[a] = __ldcg(src + (long long)a * Ny + sj);
+            f[a] = S.ld(a, sj);
         }
     }
     Collision<Q, float, true> col;
@@ -119,17 +186,46 @@ __device__ __forceinline__ void cell_update(const SlotDesc &d, const float *src,
         col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
     });
 #pragma unroll
-    for (int a = 0; a < Q; ++a) dst[(long long)a * Ny + j] = o[a];
+    for (int a = 0; a < Q; ++a) S.st(a, j, o[a]);
+}
+
+// The chunk's time steps.  Warp 0 of the bottom CTA and warp 1 of the top CTA
+// own the wall blocks [j0, j0 + nb) and [j1 - nt, j1) and first form their
+// wall's re-emission; every thread then updates its wall-block row (if any)
+// and its share of the bulk rows [mb, me), handed out from the last thread
+// down so that the wall warps get bulk rows last.
+template <int Q, class State>
+__device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWallShared &sw,
+                                          int chunk, int CL, int warp, int lane, int tid,
+                                          int nth, int j0, int j1, int nb, int nt, int mb,
+                                          int me) {
+    int jw = -1;
+    if (warp == 0 && nb > 0 && lane < nb) jw = j0 + lane;
+    if (warp == 1 && nt > 0 && lane < nt) jw = j1 - nt + lane;
+    const int jb = mb + (nth - 1 - tid);
+    for (int step = 0; step < chunk; ++step) {
+        if (warp == 0 && nb > 0) wall_fill_warp<Q>(d, S, 0, lane, sw.fill[0]);
+        else if (warp == 1 && nt > 0) wall_fill_warp<Q>(d, S, 1, lane, sw.fill[1]);
+        for (int it = jw >= 0 ? -1 : 0;; ++it) {
+            const int j = it < 0 ? jw : jb + it * nth;
+            if (it >= 0 && j >= me) break;
+            if (j < j0 + 3 || j >= j1 - 3) cell_update<Q, true>(d, S, j, sw);
+            else cell_update<Q, false>(d, S, j, sw);
+        }
+        slot_barrier(CL);
+        S.flip();
+    }
 }
 
 // One chunk of one slot on CTA `rank` of its CL-CTA cluster.  `chunks` is the
 // slot's chunk counter after this chunk (read by every CTA before the first
-// barrier); `part` holds CL x 6 FP64 partial sums of the residual.
+// barrier); `part` holds CL x 6 FP64 partial sums of the residual; `sm` the
+// CTA's kSmemBytes of dynamic shared memory (used when R <= kSmemRows).
 template <int Q>
 __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict__ pool,
                                            SlotStatus *__restrict__ st, BatchWallShared &sw,
                                            int rank, int CL, int chunks,
-                                           double *__restrict__ part) {
+                                           double *__restrict__ part, float *sm) {
     using L = Lat<Q>;
     const int chunk = d.chunk_steps;
     const KConsts<float> &k = d.k;
@@ -153,31 +249,33 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
     }
     const int mb = j0 + nb, me = j1 - nt;
 
-    float *buf0 = pool + d.f_off;
-    float *buf1 = buf0 + (long long)Q * Ny;
-    const float *src = d.cur ? buf1 : buf0;
-    float *dst = d.cur ? buf0 : buf1;
-
+    float *g_cur = pool + d.f_off + (d.cur ? (long long)Q * Ny : 0);
+    float *g_oth = pool + d.f_off + (d.cur ? 0 : (long long)Q * Ny);
+    const bool smem = R <= kSmemRows;
+    const float *fin;                          // the state after the chunk
     if (tid < 2) sw.acc[tid] = (float)k.accom[tid];
-    __syncthreads();
-    // this thread's wall-block row (-1: none); bulk rows are handed out from
-    // the last thread down, so that the wall warps get bulk rows last
-    int jw = -1;
-    if (warp == 0 && nb > 0 && lane < nb) jw = j0 + lane;
-    if (warp == 1 && nt > 0 && lane < nt) jw = j1 - nt + lane;
-    const int jb = mb + (nth - 1 - tid);
-    for (int step = 0; step < chunk; ++step) {
-        if (warp == 0 && nb > 0) wall_fill_warp<Q>(d, src, 0, lane, sw.fill[0]);
-        else if (warp == 1 && nt > 0) wall_fill_warp<Q>(d, src, 1, lane, sw.fill[1]);
-        for (int it = jw >= 0 ? -1 : 0;; ++it) {
-            const int j = it < 0 ? jw : jb + it * nth;
-            if (it >= 0 && j >= me) break;
-            cell_update<Q>(d, src, dst, j, sw);
+    if (smem) {
+        // own rows into buffer 0
+        for (int i = tid; i < Q * span; i += nth) {
+            const int a = i / span, r = i - a * span;
+            sm[a * R + r] = __ldcg(g_cur + (long long)a * Ny + j0 + r);
         }
-        slot_barrier(CL);
-        const float *t = src;
-        src = dst;
-        dst = (float *)t;
+        SmemState S{sm, nullptr, nullptr, R, j0, Q * R, 0};
+        if (rank > 0) S.lo = map_rank(sm, rank - 1);
+        if (rank < CL - 1) S.hi = map_rank(sm, rank + 1);
+        slot_barrier(CL);                      // every CTA loaded before any neighbour reads
+        run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me);
+        fin = sm + S.b * Q * R;
+        // write the final state back to the pool buffer it came from
+        for (int i = tid; i < Q * span; i += nth) {
+            const int a = i / span, r = i - a * span;
+            g_cur[(long long)a * Ny + j0 + r] = fin[a * R + r];
+        }
+    } else {
+        __syncthreads();
+        GlobalState S{g_cur, g_oth, Ny};
+        run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me);
+        fin = S.src;
     }
 
     if (chunks % d.check_every != 0) {
@@ -199,7 +297,8 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         double s0 = 0, sx = 0, sy = 0, se = (double)k.e2w;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const double fa = (double)__ldcg(src + (long long)a * Ny + j);
+            const double fa = smem ? (double)fin[a * R + j - j0]
+                                   : (double)__ldcg(fin + (long long)a * Ny + j);
             s0 += fa;
             sx += L::ex(a) * fa;
             sy += L::ey(a) * fa;

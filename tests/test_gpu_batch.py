@@ -79,16 +79,22 @@ TALL = [("D2Q37", 300, 0.5, 0.20, 1.0), ("D2Q25", 700, 0.8, 0.10, 1.0),
 TALL_BOUND = {300: 2e-5, 700: 2.5e-5, 1500: 1.2e-4, 1100: 5e-5}
 
 
+# a column whose CTAs get more rows than fit their shared memory (the state
+# stays in global memory)
+XTALL = [("D2Q17", 2500, 1.0, 0.15, 1.0)]
+
+
 def test_cluster_slots_follow_the_oracle_transient(lbm, oracle):
     # a fixed number of steps (no convergence stop): every row of the state,
     # including the rows next to the cluster's CTA boundaries, against the
     # oracle after the same steps
     s = lbm.Server(mem_budget_bytes=1 << 28, max_slots=32, chunk_steps=50)
+    items = TALL + XTALL
     ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=1e-30, max_steps=1500))
-           for lat, Ny, Kn, Uw, Tw in TALL]
+           for lat, Ny, Kn, Uw, Tw in items]
     s.drain(300)
     res = {r.id: r for r in s.poll(8)}
-    for rid, (lat, Ny, Kn, Uw, Tw) in zip(ids, TALL):
+    for rid, (lat, Ny, Kn, Uw, Tw) in zip(ids, items):
         r = res[rid]
         _, ux, _, T = s.fetch(rid, Ny)
         o, t = (4, True) if lat == "D2Q37" else (2, False)
