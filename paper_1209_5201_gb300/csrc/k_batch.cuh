@@ -9,9 +9,10 @@
 // ceil(Ny / CL), and a cluster barrier with release / acquire semantics
 // separates the steps.  When R <= kSmemRows the CTA keeps its rows' two state
 // buffers in shared memory for the whole chunk (loaded from the pool at the
-// start, written back at the end) and pulls the <= 3 rows it needs from each
-// neighbour through distributed shared memory; taller slots keep the state in
-// global memory (L2-resident) and read it with ld.global.cg.
+// start, written back at the end; rows of Q populations) and pulls the <= 3
+// rows it needs from each neighbour through distributed shared memory
+// (ld.shared::cluster); taller slots keep the state in global memory
+// (L2-resident) and read it with ld.global.cg.
 //
 // Row mapping inside a CTA: warp 0 of the bottom CTA owns the (up to) 32
 // lowest rows and warp 1 of the top CTA the 32 highest; each of those warps
@@ -63,12 +64,29 @@ __device__ __forceinline__ void slot_barrier(int CL) {
 constexpr int kSmemRows = 256;
 constexpr int kSmemBytes = 2 * kMaxQ * kSmemRows * (int)sizeof(float);
 
-// Generic address of the same shared-memory location in CTA `rank` of the
-// cluster (distributed shared memory).
-__device__ __forceinline__ float *map_rank(float *p, unsigned rank) {
-    unsigned long long out;
-    asm volatile("mapa.u64 %0, %1, %2;\n" : "=l"(out) : "l"((unsigned long long)p), "r"(rank));
-    return (float *)out;
+// compile-time loop a = A, A + 1, ..., N - 1
+template <int A, int N>
+struct StaticFor {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&fn) {
+        if constexpr (A < N) {
+            fn(std::integral_constant<int, A>{});
+            StaticFor<A + 1, N>::run(fn);
+        }
+    }
+};
+
+// Population a of the wall re-emission (Eq. (9) with R = accom R_D + (1 -
+// accom) R_S): the diffuse part formed by the wall warp, plus the specular
+// part (the mirrored velocity of the same row, `spec`, read only when accom <
+// 1); both are deviations from w_a, so the mix is linear in them.
+template <class SpecFn>
+__device__ __forceinline__ float wall_value(const BatchWallShared &sw, int wall, int a,
+                                            SpecFn &&spec) {
+    const float acc = sw.acc[wall];
+    float v = sw.fill[wall][a];
+    if (acc != 1.0f) v = acc * v + (1.0f - acc) * spec();
+    return v;
 }
 
 // Slot state in global memory (pool), two buffers of [Q][Ny]; a step reads
@@ -83,8 +101,24 @@ struct GlobalState {
         return __ldcg(src + (long long)a * Ny + row);
     }
     __device__ __forceinline__ float ld_own(int a, int row) const { return ld(a, row); }
-    __device__ __forceinline__ void st(int a, int row, float v) const {
-        dst[(long long)a * Ny + row] = v;
+    // f_in of row j (Eq. (5) pull with the Eq. (12) wall)
+    template <int Q, bool EDGE>
+    __device__ __forceinline__ void pull(const SlotDesc &d, const BatchWallShared &sw, int j,
+                                         float (&f)[Q]) const {
+        using L = Lat<Q>;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int sj = j - L::ey(a);
+            if (EDGE && (sj < 0 || sj >= Ny))
+                f[a] = wall_value(sw, sj < 0 ? 0 : 1, a, [&] { return ld(d.k.mirror[a], j); });
+            else
+                f[a] = ld(a, sj);
+        }
+    }
+    template <int Q>
+    __device__ __forceinline__ void store(int j, const float (&o)[Q]) const {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) dst[(long long)a * Ny + j] = o[a];
     }
     __device__ __forceinline__ void flip() {
         const float *t = src;
@@ -93,30 +127,87 @@ struct GlobalState {
     }
 };
 
-// Slot state in the cluster's shared memory: this CTA holds rows [j0, j0 + R)
-// as buf[b][a][row - j0] (b = current buffer); lo / hi are the same buffers of
-// the neighbouring CTAs (rows j0 - R .., j0 + R ..), null at the slot's ends.
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];\n" : "=f"(v) : "r"(addr), "n"(OFF) : "memory");
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts_f32(uint32_t addr, float v) {
+    asm volatile("st.shared.f32 [%0+%1], %2;\n" ::"r"(addr), "n"(OFF), "f"(v) : "memory");
+}
+__device__ __forceinline__ float ldsc_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+// shared::cluster address of the same location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, unsigned rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(out) : "r"(addr), "r"(rank));
+    return out;
+}
+
+// Slot state in the cluster's shared memory.  This CTA holds rows [j0, j0 + R)
+// in two buffers of R rows x Q floats (row-major: a thread's Q populations are
+// contiguous and Q is odd, so the 32 lanes of a warp, on 32 consecutive rows,
+// hit 32 different banks); `b` is the buffer holding the current state.  lo /
+// hi are the same buffers of the neighbouring CTAs (rows j0 - R .., j0 + R ..)
+// as shared::cluster addresses, 0 at the slot's ends.  Bulk rows read with
+// compile-time offsets from their own row address.
+template <int Q>
 struct SmemState {
-    float *buf;                // local buffers, 2 x Q x R floats
-    const float *lo, *hi;      // neighbours' buffers (distributed shared memory)
-    int R, j0, QR, b;
+    uint32_t base;             // shared::cta address of buffer 0
+    uint32_t lo, hi;           // shared::cluster addresses of the neighbours' buffer 0
+    int R, j0, b;
+    __device__ __forceinline__ uint32_t row_addr(int buf, int lr) const {
+        return base + (uint32_t)((buf * R + lr) * Q) * 4u;
+    }
     __device__ __forceinline__ float ld(int a, int row) const {
-        int lr = row - j0;
-        const float *p = buf;
-        if (lr < 0) {
-            p = lo;
-            lr += R;
-        } else if (lr >= R) {
-            p = hi;
-            lr -= R;
-        }
-        return p[b * QR + a * R + lr];
+        const int lr = row - j0;
+        if (lr < 0) return ldsc_f32(lo + (uint32_t)(((b * R + lr + R) * Q + a) * 4));
+        if (lr >= R) return ldsc_f32(hi + (uint32_t)(((b * R + lr - R) * Q + a) * 4));
+        return lds_f32(row_addr(b, lr) + (uint32_t)a * 4u);
     }
     __device__ __forceinline__ float ld_own(int a, int row) const {
-        return buf[b * QR + a * R + row - j0];
+        return lds_f32(row_addr(b, row - j0) + (uint32_t)a * 4u);
     }
-    __device__ __forceinline__ void st(int a, int row, float v) const {
-        buf[(b ^ 1) * QR + a * R + row - j0] = v;
+    template <int Q_, bool EDGE>
+    __device__ __forceinline__ void pull(const SlotDesc &d, const BatchWallShared &sw, int j,
+                                         float (&f)[Q_]) const {
+        using L = Lat<Q_>;
+        if constexpr (!EDGE) {
+            // every source row lies in [lr - 3, lr + 3] of this CTA: offsets
+            // from row lr - 3 are compile-time constants
+            const uint32_t r0 = row_addr(b, j - j0 - 3);
+            StaticFor<0, Q_>::run([&](auto ic) {
+                constexpr int a = decltype(ic)::value;
+                f[a] = lds_f32<((3 - L::ey(a)) * Q_ + a) * 4>(r0);
+            });
+        } else {
+#pragma unroll
+            for (int a = 0; a < Q_; ++a) {
+                const int sj = j - L::ey(a);
+                if (sj < 0 || sj >= d.Ny)
+                    f[a] = wall_value(sw, sj < 0 ? 0 : 1, a, [&] { return ld_own(d.k.mirror[a], j); });
+                else
+                    f[a] = ld(a, sj);
+            }
+        }
+    }
+    template <int Q_>
+    __device__ __forceinline__ void store(int j, const float (&o)[Q_]) const {
+        const uint32_t r = row_addr(b ^ 1, j - j0);
+        StaticFor<0, Q_>::run([&](auto ic) {
+            constexpr int a = decltype(ic)::value;
+            sts_f32<a * 4>(r, o[a]);
+        });
     }
     __device__ __forceinline__ void flip() { b ^= 1; }
 };
@@ -151,32 +242,13 @@ __device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, const State &S
 template <int Q, bool EDGE, class State>
 __device__ __forceinline__ void cell_update(const SlotDesc &d, const State &S, int j,
                                             const BatchWallShared &sw) {
-    using L = Lat<Q>;
     // the slot's constants live in shared memory; this compiler barrier keeps
     // them there (re-read per cell) instead of hoisted into registers for the
     // whole step loop, which spilled
     asm volatile("" ::: "memory");
     const KConsts<float> &k = d.k;
-    const int Ny = d.Ny;
     float f[Q];
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        const int sj = j - L::ey(a);
-        if (!EDGE) {
-            f[a] = S.ld_own(a, sj);
-        } else if (sj < 0 || sj >= Ny) {
-            // Eq. (9): diffuse part of the wall, plus the specular part (the
-            // mirrored velocity of the same row) when accom < 1; both are
-            // deviations from w_a, so the mix is linear in them
-            const int wall = sj < 0 ? 0 : 1;
-            const float acc = sw.acc[wall];
-            float v = sw.fill[wall][a];
-            if (acc != 1.0f) v = acc * v + (1.0f - acc) * S.ld_own(k.mirror[a], j);
-            f[a] = v;
-        } else {
-            f[a] = S.ld(a, sj);
-        }
-    }
+    S.template pull<Q, EDGE>(d, sw, j, f);
     Collision<Q, float, true> col;
     col.setup(f, k);
     float o[Q];
@@ -185,8 +257,7 @@ __device__ __forceinline__ void cell_update(const SlotDesc &d, const State &S, i
         constexpr int A = decltype(ic)::value;
         col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
     });
-#pragma unroll
-    for (int a = 0; a < Q; ++a) S.st(a, j, o[a]);
+    S.template store<Q>(j, o);
 }
 
 // The chunk's time steps.  Warp 0 of the bottom CTA and warp 1 of the top CTA
@@ -209,7 +280,11 @@ __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWall
         for (int it = jw >= 0 ? -1 : 0;; ++it) {
             const int j = it < 0 ? jw : jb + it * nth;
             if (it >= 0 && j >= me) break;
-            if (j < j0 + 3 || j >= j1 - 3) cell_update<Q, true>(d, S, j, sw);
+            // one path per warp: a warp with any row within 3 rows of its
+            // CTA's ends takes the general (EDGE) path for all its rows, so
+            // the collision is never executed twice by a diverged warp
+            const bool edge = __any_sync(__activemask(), j < j0 + 3 || j >= j1 - 3);
+            if (edge) cell_update<Q, true>(d, S, j, sw);
             else cell_update<Q, false>(d, S, j, sw);
         }
         slot_barrier(CL);
@@ -255,21 +330,22 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
     const float *fin;                          // the state after the chunk
     if (tid < 2) sw.acc[tid] = (float)k.accom[tid];
     if (smem) {
-        // own rows into buffer 0
+        // own rows into buffer 0, transposed to rows of Q populations
         for (int i = tid; i < Q * span; i += nth) {
             const int a = i / span, r = i - a * span;
-            sm[a * R + r] = __ldcg(g_cur + (long long)a * Ny + j0 + r);
+            sm[r * Q + a] = __ldcg(g_cur + (long long)a * Ny + j0 + r);
         }
-        SmemState S{sm, nullptr, nullptr, R, j0, Q * R, 0};
-        if (rank > 0) S.lo = map_rank(sm, rank - 1);
-        if (rank < CL - 1) S.hi = map_rank(sm, rank + 1);
+        const uint32_t base = (uint32_t)__cvta_generic_to_shared(sm);
+        SmemState<Q> S{base, 0u, 0u, R, j0, 0};
+        if (rank > 0) S.lo = map_rank(base, rank - 1);
+        if (rank < CL - 1) S.hi = map_rank(base, rank + 1);
         slot_barrier(CL);                      // every CTA loaded before any neighbour reads
         run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me);
         fin = sm + S.b * Q * R;
         // write the final state back to the pool buffer it came from
         for (int i = tid; i < Q * span; i += nth) {
             const int a = i / span, r = i - a * span;
-            g_cur[(long long)a * Ny + j0 + r] = fin[a * R + r];
+            g_cur[(long long)a * Ny + j0 + r] = fin[r * Q + a];
         }
     } else {
         __syncthreads();
@@ -297,7 +373,7 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         double s0 = 0, sx = 0, sy = 0, se = (double)k.e2w;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const double fa = smem ? (double)fin[a * R + j - j0]
+            const double fa = smem ? (double)fin[(j - j0) * Q + a]
                                    : (double)__ldcg(fin + (long long)a * Ny + j);
             s0 += fa;
             sx += L::ex(a) * fa;
