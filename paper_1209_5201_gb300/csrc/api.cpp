@@ -185,6 +185,7 @@ void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int p
     double e2w = 0;
     for (int a = 0; a < L.Q; ++a) e2w += (double)(C)L.w[a] * (L.ex[a] * L.ex[a] + L.ey[a] * L.ey[a]);
     k.e2w = (C)e2w;
+    k.th0 = (C)((double)k.r2 * e2w - 2.0);
     for (int a = 0; a < L.Q; ++a) {
         k.mirror[a] = a;
         for (int b = 0; b < L.Q; ++b)

@@ -49,15 +49,34 @@ struct SlotStatus {
     int chunks;               // chunks run since admission
 };
 
-// Cluster sizes of the slot classes.  A column of Ny rows runs on the smallest
-// cluster whose CTAs get at most `rows` rows each (8 CTAs if none does),
-// capped by the CTA budget.
+// Cluster sizes of the slot classes.
 constexpr int kBatchClasses = 4;
 constexpr int kBatchClassCL[kBatchClasses] = {1, 2, 4, 8};
+// Rows of the residual's partial sums (one warp each) and their most per slot.
+constexpr int kResidualChunk = 32;
+constexpr int kMaxResidualChunks = 8192 / kResidualChunk;
+
+// Rows per CTA of a column of Ny rows on a cluster of CL CTAs: all of them on
+// one CTA, else ceil(Ny / CL) rounded up to whole residual chunks, so that no
+// chunk straddles two CTAs.
+__host__ __device__ inline int batch_rows_per_cta(int Ny, int CL) {
+    if (CL <= 1) return Ny;
+    const int r = (Ny + CL - 1) / CL;
+    return (r + kResidualChunk - 1) / kResidualChunk * kResidualChunk;
+}
+// A split is usable when every CTA, the last included, gets >= 32 rows.
+__host__ __device__ inline bool batch_split_ok(int Ny, int CL) {
+    if (CL == 1) return Ny >= 6;
+    const int R = batch_rows_per_cta(Ny, CL);
+    return (CL == 2 || CL == 4 || CL == 8) && (CL - 1) * R + 32 <= Ny;
+}
+// The largest cluster a column of Ny rows may use: the smallest CL whose CTAs
+// get at most `rows` rows each (8 if none does), reduced until the split is
+// usable and fits the CTA budget.
 inline int batch_cluster_size(int Ny, int rows, int max_ctas) {
     int cl = 1;
-    while (cl < 8 && (Ny + cl - 1) / cl > rows) cl *= 2;
-    while (cl > 1 && (cl > max_ctas || (Ny + cl - 1) / cl < 32)) cl /= 2;
+    while (cl < 8 && batch_rows_per_cta(Ny, cl) > rows) cl *= 2;
+    while (cl > 1 && (cl > max_ctas || !batch_split_ok(Ny, cl))) cl /= 2;
     return cl;
 }
 
@@ -65,7 +84,8 @@ int preload_batch_kernels();
 // dbg: 8 device ints; dbg[0] != 0 records the first invalid descriptor or
 // read-out offset a kernel met (and skipped).
 // One chunk of the slots [slot0, slot0 + nlanes), each on a cluster of CL
-// CTAs; part: 8 x 6 FP64 residual partials per slot of the whole table.
+// CTAs; part: kMaxResidualChunks x 6 FP64 residual partials per slot of the
+// whole table.
 int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, float *pool,
                        double *part, int slot0, int nlanes, int CL, long long pool_elems,
                        int *dbg);

@@ -22,8 +22,7 @@ __device__ __forceinline__ bool desc_ok(const SlotDesc &d, long long pool_elems,
     bool mirror_ok = true;
     for (int a = 0; a < d.Q && q_ok; ++a)
         mirror_ok = mirror_ok && d.k.mirror[a] >= 0 && d.k.mirror[a] < d.Q;
-    const bool cl_ok = (d.cl == 1 || d.cl == 2 || d.cl == 4 || d.cl == 8) &&
-                       (d.cl == 1 || (d.Ny + d.cl - 1) / d.cl >= 32);
+    const bool cl_ok = batch_split_ok(d.Ny, d.cl);
     const bool ok = q_ok && terms_ok && mirror_ok && cl_ok && d.Ny >= 6 && d.Ny <= 8192 &&
                     d.f_off >= 0 &&
                     d.f_off + need <= pool_elems && d.prev_off == d.f_off + 2LL * d.Q * d.Ny &&
@@ -67,7 +66,7 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
     __syncthreads();
     if (sd.Q == 0 || status[slot].state != kSlotRunning) return;
     if (!desc_ok(sd, pool_elems, slot, 1, dbg) || sd.cl != CL) return;
-    double *pp = part + (long long)slot * 48;
+    double *pp = part + (long long)slot * (6 * kMaxResidualChunks);
     switch (sd.Q) {
     case 17: batch_slot<17>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp, batch_sm); break;
     case 25: batch_slot<25>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp, batch_sm); break;
@@ -76,7 +75,7 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
     }
     // the global-memory path leaves the state in the other buffer after an odd
     // chunk; the shared-memory path writes it back where it came from
-    const bool smem = (sd.Ny + CL - 1) / CL <= kSmemRows;
+    const bool smem = batch_uses_smem(sd.Ny, CL);
     if (!smem && rank == 0 && threadIdx.x == 0) desc[slot].cur = (sd.cur + sd.chunk_steps) & 1;
 }
 

@@ -32,12 +32,10 @@
 namespace lbm {
 
 // Shared per-step wall data of a slot: the re-emitted deviations of Eq. (12)
-// per wall and velocity and the accommodation of each wall in FP32, plus the
-// block-reduction scratch of the residual.
+// per wall and velocity and the accommodation of each wall in FP32.
 struct BatchWallShared {
     float fill[2][kMaxQ];
     float acc[2];
-    double red[32][6];
 };
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -63,6 +61,12 @@ __device__ __forceinline__ void slot_barrier(int CL) {
 // Rows of a CTA's shared-memory state: two buffers of Q x kSmemRows floats.
 constexpr int kSmemRows = 256;
 constexpr int kSmemBytes = 2 * kMaxQ * kSmemRows * (int)sizeof(float);
+
+// The shared-memory path serves split columns whose CTAs' rows fit; a column on
+// one CTA keeps its state in global memory (L2), which measured faster there.
+__host__ __device__ inline bool batch_uses_smem(int Ny, int CL) {
+    return CL > 1 && batch_rows_per_cta(Ny, CL) <= kSmemRows;
+}
 
 // compile-time loop a = A, A + 1, ..., N - 1
 template <int A, int N>
@@ -294,7 +298,7 @@ __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWall
 
 // One chunk of one slot on CTA `rank` of its CL-CTA cluster.  `chunks` is the
 // slot's chunk counter after this chunk (read by every CTA before the first
-// barrier); `part` holds CL x 6 FP64 partial sums of the residual; `sm` the
+// barrier); `part` the slot's per-chunk FP64 partial sums of the residual; `sm` the
 // CTA's kSmemBytes of dynamic shared memory (used when R <= kSmemRows).
 template <int Q>
 __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict__ pool,
@@ -307,12 +311,12 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
     const int Ny = d.Ny;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int R = (Ny + CL - 1) / CL;
+    const int R = batch_rows_per_cta(Ny, CL);
     const int j0 = min(Ny, rank * R), j1 = min(Ny, j0 + R);
     const bool has_bot = rank == 0, has_top = rank == CL - 1;
     const int span = j1 - j0;
     // wall blocks: >= 3 rows each (every row that pulls from a wall), since
-    // the host keeps Ny >= 6 and R >= 32 whenever CL > 1
+    // the host keeps Ny >= 6 and every CTA of a split >= 32 rows
     int nb = 0, nt = 0;
     if (has_bot && has_top) {
         nb = min(32, span / 2);
@@ -326,7 +330,7 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
 
     float *g_cur = pool + d.f_off + (d.cur ? (long long)Q * Ny : 0);
     float *g_oth = pool + d.f_off + (d.cur ? 0 : (long long)Q * Ny);
-    const bool smem = R <= kSmemRows;
+    const bool smem = batch_uses_smem(Ny, CL);
     const float *fin;                          // the state after the chunk
     if (tid < 2) sw.acc[tid] = (float)k.accom[tid];
     if (smem) {
@@ -363,57 +367,60 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         return;
     }
 
-    // residual over the slot's cells (Eq. (3) moments of the current state)
+    // Residual over the slot's cells (Eq. (3) moments of the current state).
+    // Partial sums per 32-row chunk (one warp each, fixed lane order) in
+    // global memory, then one warp of CTA 0 adds the chunks in a fixed order:
+    // the result does not depend on how the rows were split across CTAs.
     float *prev_u = (float *)(pool + d.prev_off);
     float *prev_T = prev_u + Ny;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
     const double r = (double)k.r;
-    for (int j = j0 + tid; j < j1; j += nth) {
-        // deviations d = f - w: rho = 1 + sum d, sum e w = 0, sum e^2 w = e2w
-        double s0 = 0, sx = 0, sy = 0, se = (double)k.e2w;
+    const int nwarps = nth >> 5;
+    for (int c = j0 / kResidualChunk + warp; c * kResidualChunk < j1; c += nwarps) {
+        const int j = c * kResidualChunk + lane;
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        if (j < j1) {
+            // deviations d = f - w: rho = 1 + sum d, sum e w = 0, sum e^2 w = e2w
+            double s0 = 0, sx = 0, sy = 0, se = (double)k.e2w;
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const double fa = smem ? (double)fin[(j - j0) * Q + a]
-                                   : (double)__ldcg(fin + (long long)a * Ny + j);
-            s0 += fa;
-            sx += L::ex(a) * fa;
-            sy += L::ey(a) * fa;
-            se += L::e2(a) * fa;
-        }
-        const double rh = 1.0 + s0;
-        const double u = r * sx / rh, v = r * sy / rh;
-        const double T = ((double)k.r2 * se - rh * (u * u + v * v)) / (2.0 * rh);
-        const double du = u - prev_u[j], dT = T - prev_T[j];
-        acc[0] += du * du;
-        acc[1] += u * u;
-        acc[2] += dT * dT;
-        acc[3] += T * T;
-        acc[4] += rh;
-        if (!isfinite(u) || !isfinite(T)) acc[5] += 1.0;
-        prev_u[j] = (float)u;
-        prev_T[j] = (float)T;
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-        for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
-    if (lane == 0)
-        for (int i = 0; i < 6; ++i) sw.red[warp][i] = acc[i];
-    __syncthreads();
-    double tot[6] = {0, 0, 0, 0, 0, 0};
-    if (tid == 0)
-        for (int w = 0; w < (nth + 31) / 32; ++w)
-            for (int i = 0; i < 6; ++i) tot[i] += sw.red[w][i];
-    if (CL > 1) {
-        // CTA partials through global memory, summed by rank 0 in rank order
-        if (tid == 0)
-            for (int i = 0; i < 6; ++i) part[rank * 6 + i] = tot[i];
-        slot_barrier(CL);
-        if (rank != 0) return;
-        if (tid == 0)
-            for (int i = 0; i < 6; ++i) {
-                tot[i] = 0.0;
-                for (int c = 0; c < CL; ++c) tot[i] += part[c * 6 + i];
+            for (int a = 0; a < Q; ++a) {
+                const double fa = smem ? (double)fin[(j - j0) * Q + a]
+                                       : (double)__ldcg(fin + (long long)a * Ny + j);
+                s0 += fa;
+                sx += L::ex(a) * fa;
+                sy += L::ey(a) * fa;
+                se += L::e2(a) * fa;
             }
+            const double rh = 1.0 + s0;
+            const double u = r * sx / rh, v = r * sy / rh;
+            const double T = ((double)k.r2 * se - rh * (u * u + v * v)) / (2.0 * rh);
+            const double du = u - prev_u[j], dT = T - prev_T[j];
+            acc[0] = du * du;
+            acc[1] = u * u;
+            acc[2] = dT * dT;
+            acc[3] = T * T;
+            acc[4] = rh;
+            acc[5] = (!isfinite(u) || !isfinite(T)) ? 1.0 : 0.0;
+            prev_u[j] = (float)u;
+            prev_T[j] = (float)T;
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+        if (lane == 0)
+            for (int i = 0; i < 6; ++i) part[c * 6 + i] = acc[i];
+    }
+    slot_barrier(CL);                          // every chunk's partials written
+    if (rank != 0) return;
+    double tot[6] = {0, 0, 0, 0, 0, 0};
+    if (warp == 0) {
+        const int nch = (Ny + kResidualChunk - 1) / kResidualChunk;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double v = 0.0;
+            for (int c = lane; c < nch; c += 32) v += part[c * 6 + i];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            tot[i] = v;
+        }
     }
     if (tid == 0) {
         SlotStatus &s = *st;

@@ -115,11 +115,18 @@ struct Collision {
         const C u2 = ux * ux + uy * uy;
         C th = 0, T = 1;
         if (k.thermal) {
-            C e2 = SHIFT ? k.e2w : C(0);
+            C e2 = C(0);
 #pragma unroll
             for (int a = 1; a < Q; a += 2) e2 += C(L::e2(a)) * (f[a] + f[a + 1]);
-            T = (k.r2 * e2 * inv - u2) * C(0.5);
-            th = T - C(1);
+            if (SHIFT) {
+                // deviations: 2 rho theta = (r^2 e2w - 2) + r^2 sum e^2 d - rho u^2
+                // - 2 drho, every term small (no cancellation against 2)
+                th = (k.th0 + k.r2 * e2 - rho * u2 - C(2) * drho) * (C(0.5) * inv);
+                T = C(1) + th;
+            } else {
+                T = (k.r2 * e2 * inv - u2) * C(0.5);
+                th = T - C(1);
+            }
         }
         C taul;
         if (k.const_tau) taul = k.tau_lat;

@@ -48,6 +48,8 @@ struct KConsts {
     C c2sh[kMaxShells];       // |c|^2 = r^2 |e|^2 of each shell
     C w[kMaxQ];               // per-velocity weights
     C e2w;                    // sum_a |e_a|^2 w_a (= D / r^2 up to rounding)
+    C th0;                    // r^2 e2w - D, formed in FP64: theta = T - 1 of the
+                              // shifted storage without cancellation against D
     int off_src[kMaxQ];       // a * plane - e_ay * pitch - e_ax: pull source offset
     int off_dst[kMaxQ];       // a * plane: store offset
     int mirror[kMaxQ];        // velocity with (e_x, -e_y): specular partner

@@ -38,6 +38,9 @@ namespace lbm {
 namespace {
 
 constexpr int kMaxNy = 8192;
+// work above which a request counts as long for the cluster choice: row-steps
+// per thread on one CTA (~1 s at ~4 us per step and 256 rows)
+constexpr double kLongRowSteps = 2.5e5;
 constexpr long long kAlignElems = 64;        // 256-byte granularity (floats)
 
 struct Pending {
@@ -80,7 +83,7 @@ struct ServerImpl {
     long long pool_elems = 0;
     SlotDesc *d_desc = nullptr;
     SlotStatus *d_status = nullptr;
-    double *d_part = nullptr;                // residual partials, 8 x 6 per slot
+    double *d_part = nullptr;                // residual partials per 32-row chunk
     // slot classes: slots [cls_base[c], cls_base[c] + cls_cap[c]) run on
     // clusters of kBatchClassCL[c] CTAs, each class launched on its own stream
     int cls_base[kBatchClasses] = {}, cls_cap[kBatchClasses] = {};
@@ -159,7 +162,7 @@ struct ServerImpl {
         }
     }
 
-    void fill_slot(int s, const Pending &pd, long long off) {
+    void fill_slot(int s, const Pending &pd, long long off, int cl) {
         const lbm_request &r = pd.req;
         const LatticeHost &L = lattice(r.lattice);
         lbm_params p;
@@ -183,13 +186,14 @@ struct ServerImpl {
         d.Q = L.Q;
         d.Ny = r.Ny;
         d.cur = 0;
-        d.cl = cluster_for(r.Ny);
+        d.cl = cl;
         // Steps per chunk launch: cheaper slots run more steps, so that every
         // CTA of a launch takes about as long (cfg.chunk_steps x 333 cost
         // units); the cost model is the velocity count times the rows per
-        // thread of the slot's CTAs (256 threads each) plus a latency floor.
-        const int rows_per_cta = (r.Ny + d.cl - 1) / d.cl;
-        const double cost = L.Q * std::ceil(rows_per_cta / 256.0) + 37.0;
+        // thread of one 256-thread CTA plus a latency floor.  It ignores the
+        // cluster on purpose: chunk lengths and residual checks then fall on
+        // the same steps however the column is split.
+        const double cost = L.Q * std::ceil(r.Ny / 256.0) + 37.0;
         const double cost_ref = 37.0 * 8.0 + 37.0;
         d.chunk_steps = (int)std::min<double>(32.0 * cfg.chunk_steps,
                                               std::max<double>(cfg.chunk_steps,
@@ -262,10 +266,25 @@ struct ServerImpl {
     }
 
     // a free slot of the class that runs a column of Ny rows, or -1
-    int cluster_for(int Ny) const { return batch_cluster_size(Ny, cfg.cluster_rows, cfg.max_slots); }
+    // Whether a request may be split over a cluster, with its cluster size and
+    // estimated work.  A split column moves fewer lattice updates per SM than
+    // one CTA (a barrier per step across the cluster), so it is only worth its
+    // latency gain for long requests: estimated row-steps per thread on one
+    // CTA (14 e-folding times of the slowest shear mode, Ny / 256 rows per
+    // thread) above kLongRowSteps.  Results do not depend on the split: every
+    // cell update is the same arithmetic on the same values, chunk lengths and
+    // checks ignore the cluster, and the residual is summed over 32-row chunks
+    // in a fixed order.
+    bool long_split(const lbm_request &r, int &cl, double &work) const {
+        cl = batch_cluster_size(r.Ny, cfg.cluster_rows, cfg.max_slots);
+        if (cl == 1) return false;
+        const LatticeHost &L = lattice(r.lattice);
+        const double efold = r.tau > 0 ? r.Ny / (9.8696 * r.tau * L.r) : 0.127 * r.Ny * L.r / r.Kn;
+        work = 14.0 * efold * std::ceil(r.Ny / 256.0);
+        return work >= kLongRowSteps;
+    }
 
-    int free_slot(int Ny) const {
-        const int cl = cluster_for(Ny);
+    int free_slot(int cl) const {
         int c = 0;
         while (c + 1 < kBatchClasses && kBatchClassCL[c] != cl) ++c;
         for (int s = cls_base[c]; s < cls_base[c] + cls_cap[c]; ++s)
@@ -295,15 +314,38 @@ struct ServerImpl {
         std::vector<int> admitted;
         {
             std::unique_lock<std::mutex> lk(mu);
+            // CTAs beyond one for every queued request go to the longest queued
+            // requests (among the first 512), longest first, as clusters: the
+            // GPU's idle CTAs shorten the requests that set the latency tail,
+            // and none is taken from a request still waiting.
+            std::map<uint64_t, int> split;
+            long long extra = (long long)cfg.max_slots - used_ctas - (long long)queue.size();
+            if (extra > 0) {
+                std::vector<std::pair<double, std::pair<uint64_t, int>>> cand;
+                int n = 0;
+                for (auto q = queue.begin(); q != queue.end() && n < 512; ++q, ++n) {
+                    int cl;
+                    double work;
+                    if (long_split(q->req, cl, work)) cand.push_back({work, {q->id, cl}});
+                }
+                std::sort(cand.begin(), cand.end(),
+                          [](const auto &x, const auto &y) { return x.first > y.first; });
+                for (const auto &c : cand)
+                    if (extra >= c.second.second - 1) {
+                        split[c.second.first] = c.second.second;
+                        extra -= c.second.second - 1;
+                    }
+            }
             // Scan the queue in arrival order (at most 64 entries).  A request
             // is admitted when its class has a free slot and its cluster fits
             // the CTA budget (max_slots) minus what the oldest request that did
-            // not fit needs (so that small requests cannot starve a large one);
-            // the first request that finds no memory stops the scan.
+            // not fit needs (so that later requests cannot starve it); the
+            // first request that finds no memory stops the scan.
             int reserve = 0, scanned = 0;
             for (auto it = queue.begin(); it != queue.end() && scanned < 64; ++scanned) {
-                const int cl = cluster_for(it->req.Ny);
-                const int s = used_ctas + cl + reserve <= cfg.max_slots ? free_slot(it->req.Ny) : -1;
+                const auto sp = split.find(it->id);
+                const int cl = sp == split.end() ? 1 : sp->second;
+                const int s = used_ctas + cl + reserve <= cfg.max_slots ? free_slot(cl) : -1;
                 if (s < 0) {
                     if (reserve == 0) reserve = cl;
                     ++it;
@@ -312,7 +354,7 @@ struct ServerImpl {
                 const long long n = request_elems(it->req, lattice_q(it->req.lattice));
                 const long long off = alloc(n);
                 if (off < 0) break;                  // wait for memory to free up
-                fill_slot(s, *it, off);
+                fill_slot(s, *it, off, cl);
                 admitted.push_back(s);
                 it = queue.erase(it);
                 ++running;
@@ -527,7 +569,7 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
         ck(cudaMallocAsync((void **)&S.pool, (size_t)S.pool_elems * sizeof(float), S.stream));
         ck(cudaMallocAsync((void **)&S.d_desc, sizeof(SlotDesc) * ns, S.stream));
         ck(cudaMallocAsync((void **)&S.d_status, sizeof(SlotStatus) * ns, S.stream));
-        ck(cudaMallocAsync((void **)&S.d_part, sizeof(double) * 48 * ns, S.stream));
+        ck(cudaMallocAsync((void **)&S.d_part, sizeof(double) * 6 * kMaxResidualChunks * ns, S.stream));
         ck(cudaEventCreateWithFlags(&S.ev_fork, cudaEventDisableTiming));
         for (int c = 0; c < kBatchClasses; ++c) {
             ck(cudaStreamCreateWithFlags(&S.side[c], cudaStreamNonBlocking));

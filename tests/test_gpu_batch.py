@@ -67,36 +67,39 @@ def test_batch_matches_oracle_steady_states(lbm, oracle):
         assert np.max(np.abs(ux + ux[::-1])) < 1e-5 * Uw * 10
 
 
-# columns tall enough to run on clusters of 2, 4 and 8 CTAs (rows split across
-# the cluster, one cluster barrier per step), with the FP32 steady-state bound
-# of each: the FP32 fixed point differs from the exact one by the per-step
-# round-off amplified by the slowest relaxation time, which grows with the
-# height; the single-domain FP32 solver measures the same floor (5.5e-5 for
-# the 1500-row D2Q17 column at Kn 1, 1.1e-5 for the 700-row D2Q25 one), so
-# the bound is twice the measured floor
+# Tall columns, with the FP32 steady-state bound of each: the FP32 fixed point
+# differs from the exact one by the per-step round-off amplified by the
+# slowest relaxation time, which grows with the height; the single-domain FP32
+# solver measures the same floor (5.5e-5 for the 1500-row D2Q17 column at Kn 1,
+# 1.1e-5 for the 700-row D2Q25 one), so the bound is twice the measured floor.
 TALL = [("D2Q37", 300, 0.5, 0.20, 1.0), ("D2Q25", 700, 0.8, 0.10, 1.0),
         ("D2Q17", 1500, 1.0, 0.15, 1.0), ("D2Q37", 1100, 0.6, 0.25, 1.05)]
 TALL_BOUND = {300: 2e-5, 700: 2.5e-5, 1500: 1.2e-4, 1100: 5e-5}
+# Long requests (small Kn): the server splits them over clusters of 2, 4 and
+# 8 CTAs while CTAs are spare; the 2500-row one has more rows per CTA than fit
+# shared memory (its state stays in global memory).
+LONG = [("D2Q37", 300, 0.004, 0.20, 1.0), ("D2Q25", 700, 0.004, 0.10, 1.0),
+        ("D2Q17", 1500, 0.004, 0.15, 1.0), ("D2Q37", 1100, 0.004, 0.25, 1.05),
+        ("D2Q17", 2500, 0.004, 0.15, 1.0)]
 
 
-# a column whose CTAs get more rows than fit their shared memory (the state
-# stays in global memory)
-XTALL = [("D2Q17", 2500, 1.0, 0.15, 1.0)]
+def fixed_steps(lbm, items, steps, **srv):
+    """Run every item for `steps` steps (rounded up to whole chunks)."""
+    s = lbm.Server(**{**dict(mem_budget_bytes=1 << 28, max_slots=32, chunk_steps=50), **srv})
+    ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=1e-30, max_steps=steps))
+           for lat, Ny, Kn, Uw, Tw in items]
+    s.drain(300)
+    res = {r.id: r for r in s.poll(64)}
+    out = [(res[i], *s.fetch(i, it[1])) for i, it in zip(ids, items)]
+    s.close()
+    return out
 
 
 def test_cluster_slots_follow_the_oracle_transient(lbm, oracle):
     # a fixed number of steps (no convergence stop): every row of the state,
     # including the rows next to the cluster's CTA boundaries, against the
     # oracle after the same steps
-    s = lbm.Server(mem_budget_bytes=1 << 28, max_slots=32, chunk_steps=50)
-    items = TALL + XTALL
-    ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=1e-30, max_steps=1500))
-           for lat, Ny, Kn, Uw, Tw in items]
-    s.drain(300)
-    res = {r.id: r for r in s.poll(8)}
-    for rid, (lat, Ny, Kn, Uw, Tw) in zip(ids, items):
-        r = res[rid]
-        _, ux, _, T = s.fetch(rid, Ny)
+    for (lat, Ny, Kn, Uw, Tw), (r, rho, ux, uy, T) in zip(LONG, fixed_steps(lbm, LONG, 1500)):
         o, t = (4, True) if lat == "D2Q37" else (2, False)
         p = oracle.Problem(lattice=lat, Nx=1, Ny=Ny, eq_order=o, thermal=t, Kn=Kn,
                            u_wall=(-Uw, Uw), T_wall=(Tw, Tw))
@@ -106,10 +109,24 @@ def test_cluster_slots_follow_the_oracle_transient(lbm, oracle):
         assert np.max(np.abs(ux - oux[:, 0])) / Uw < 2e-5, (lat, Ny, r.steps)
         if t:
             assert np.max(np.abs(T - oT[:, 0])) < 2e-5, (lat, Ny)
-    s.close()
 
 
-def test_cluster_slots_match_oracle_steady_states(lbm, oracle):
+@pytest.mark.parametrize("how", ["no clusters", "one CTA of budget"])
+def test_result_does_not_depend_on_the_split(lbm, how):
+    # the same long requests split over clusters (default) and on one CTA each:
+    # the same steps, residual and fields, bit for bit
+    kw = dict(cluster_rows=8192) if how == "no clusters" else dict(max_slots=1)
+    items = LONG[1:4] + LONG[4:]
+    split = fixed_steps(lbm, items, 2000)
+    whole = [fixed_steps(lbm, [it], 2000, **kw)[0] for it in items] if how != "no clusters" \
+        else fixed_steps(lbm, items, 2000, **kw)
+    for it, a, b in zip(items, split, whole):
+        assert a[0].steps == b[0].steps and a[0].residual == b[0].residual, it
+        for x, y in zip(a[1:], b[1:]):
+            assert np.array_equal(x, y), it
+
+
+def test_tall_columns_match_oracle_steady_states(lbm, oracle):
     items = TALL + MIX[:2]
     out, st = solve(lbm, items)
     assert st.completed == len(items)
@@ -124,28 +141,17 @@ def test_cluster_slots_match_oracle_steady_states(lbm, oracle):
 
 
 def test_cluster_slot_is_the_same_alone_and_in_the_mix(lbm):
-    items = TALL + MIX
-    mixed, _ = solve(lbm, items)
+    items = LONG[:4] + MIX
+    mixed = fixed_steps(lbm, items, 1500)
     for k in (0, 2, 3):
-        alone, _ = solve(lbm, [items[k]])
-        a, b = alone[0], mixed[k]
-        assert a[0].steps == b[0].steps
-        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
-
-
-def test_cluster_size_is_capped_by_the_cta_budget(lbm, oracle):
-    # one CTA of budget: a 700-row column (a 4-CTA cluster by default) runs on
-    # a single CTA, and agrees with the clustered run to FP32 round-off
-    item = ("D2Q25", 700, 0.8, 0.10, 1.0)
-    one, _ = solve(lbm, [item], max_slots=1)
-    four, _ = solve(lbm, [item])
-    assert one[0][0].status == lbm.LBM_OK
-    assert np.max(np.abs(one[0][2] - four[0][2])) / item[3] < 1e-5
+        alone = fixed_steps(lbm, [items[k]], 1500)[0]
+        assert alone[0].steps == mixed[k][0].steps
+        assert np.array_equal(alone[2], mixed[k][2]) and np.array_equal(alone[4], mixed[k][4])
 
 
 def test_cta_budget_admits_a_tall_column_behind_short_ones(lbm):
-    # budget of 8 CTAs: a 1500-row column needs all 8, so it waits for the
-    # short ones ahead of it, which must not starve it
+    # budget of 8 CTAs, short requests ahead of and behind a long tall one:
+    # with others waiting the tall one runs on one CTA and is admitted in order
     s = lbm.Server(mem_budget_bytes=1 << 28, max_slots=8, chunk_steps=50)
     short = [s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-6)) for _ in range(4)]
     tall = s.submit(lbm.make_request("D2Q17", 1500, 1.0, 0.1, tol=1e-6))
