@@ -73,6 +73,16 @@ typedef struct lbm_lattice lbm_lattice;
  * the caller and released with lbm_lattice_destroy.
  * Errors: LBM_EINVAL (unknown kind), LBM_ENOMEM. */
 int lbm_lattice_create(int kind, lbm_lattice **out);
+/* A lattice xi = {c_a = r e_a, w_a} from caller tables (Sec. II: the velocity
+ * set "may be determined through several ways"): e is Q x 2 int8 (x then y, any
+ * order), w the Q weights in the same order, r the scale.  The velocities must
+ * be one of the built-in sets (Q = 17, 25 or 37; the kernels are compiled for
+ * them), the weights positive and equal within each shell of symmetric
+ * velocities; the isotropy degree is measured (lbm_lattice_info).  The tables
+ * are copied; *out is owned by the caller.  Errors: LBM_EINVAL (message says
+ * which condition failed), LBM_ENOMEM. */
+int lbm_lattice_create_custom(int Q, const int8_t *e, const double *w, double r,
+                              lbm_lattice **out);
 int lbm_lattice_destroy(lbm_lattice *lat);
 /* Q, scale r, ghost depth N = max |e_y| (Sec. III) and isotropy degree. */
 int lbm_lattice_info(const lbm_lattice *lat, int *Q, double *r, int *ghost_depth,

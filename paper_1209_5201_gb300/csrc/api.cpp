@@ -291,6 +291,23 @@ int lbm_lattice_create(int kind, lbm_lattice **out) {
     API_END
 }
 
+int lbm_lattice_create_custom(int Q, const int8_t *e, const double *w, double r,
+                              lbm_lattice **out) {
+    API_BEGIN
+    if (!out) { set_error("out is NULL"); return LBM_EINVAL; }
+    *out = nullptr;
+    lbm_lattice *l = new lbm_lattice;
+    const char *why = "";
+    if (lattice_build_custom(Q, e, w, r, l->L, &why) != 0) {
+        delete l;
+        set_error(why);
+        return LBM_EINVAL;
+    }
+    *out = l;
+    return LBM_OK;
+    API_END
+}
+
 int lbm_lattice_destroy(lbm_lattice *lat) {
     delete lat;
     return LBM_OK;

@@ -237,6 +237,48 @@ int lattice_build(int kind, LatticeHost &L) {
     return 0;
 }
 
+int lattice_build_custom(int Q, const int8_t *e, const double *w, double r, LatticeHost &L,
+                         const char **why) {
+    const int kind = Q == 17 ? 17 : Q == 25 ? 25 : Q == 37 ? 37 : 0;
+    if (!kind) { *why = "Q must be 17, 25 or 37 (the velocity sets the kernels are built for)"; return -1; }
+    if (!e || !w) { *why = "NULL table"; return -1; }
+    if (!(r > 0) || !std::isfinite(r)) { *why = "r must be positive and finite"; return -1; }
+    // the library's tables of this velocity set, then the caller's weights in
+    // the library's order
+    if (lattice_build(kind, L) != 0) { *why = "velocity set tables"; return -1; }
+    int from[kMaxQ];
+    for (int a = 0; a < Q; ++a) {
+        from[a] = -1;
+        for (int b = 0; b < Q; ++b)
+            if (e[2 * b] == L.ex[a] && e[2 * b + 1] == L.ey[a]) {
+                if (from[a] >= 0) { *why = "a velocity appears twice"; return -1; }
+                from[a] = b;
+            }
+        if (from[a] < 0) { *why = "the velocities are not the built-in set of this Q"; return -1; }
+    }
+    double wsh[kMaxShells];
+    bool seen[kMaxShells] = {};
+    for (int a = 0; a < Q; ++a) {
+        const double v = w[from[a]];
+        if (!(v > 0) || !std::isfinite(v)) { *why = "weights must be positive and finite"; return -1; }
+        const int sh = L.shell[a];
+        if (!seen[sh]) { seen[sh] = true; wsh[sh] = v; }
+        // the kernels keep one weight per shell of symmetric velocities
+        else if (std::fabs(v - wsh[sh]) > 1e-12 * wsh[sh]) {
+            *why = "weights must be equal within each shell of symmetric velocities";
+            return -1;
+        }
+        L.w[a] = v;
+    }
+    L.r = r;
+    // isotropy degree: the largest odd degree whose moments match the Gaussian
+    L.degree = 0;
+    for (int d = 1; d <= 15; d += 2)
+        if (lattice_isotropy_error(L, d) < 1e-10) L.degree = d;
+    L.kind = kind;
+    return 0;
+}
+
 double lattice_isotropy_error(const LatticeHost &L, int degree) {
     // brute-force moments of every monomial c_x^p c_y^q, p + q <= degree
     double worst = 0.0;

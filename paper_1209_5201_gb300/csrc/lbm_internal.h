@@ -28,6 +28,10 @@ struct LatticeHost {
 };
 
 int lattice_build(int kind, LatticeHost &L);
+// A built-in velocity set (Q = 17, 25 or 37) with the caller's weights and
+// scale; 0 or -1 with *why set.
+int lattice_build_custom(int Q, const int8_t *e, const double *w, double r, LatticeHost &L,
+                         const char **why);
 double lattice_isotropy_error(const LatticeHost &L, int degree);
 
 // Per-solve constants handed to every kernel by value.  C is the compute type

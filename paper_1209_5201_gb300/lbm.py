@@ -85,6 +85,8 @@ _SIGS = {
     "lbm_last_error": ([C.c_char_p, C.c_size_t], C.c_int),
     "lbm_version": ([C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "lbm_lattice_create": ([C.c_int, C.POINTER(_VP)], C.c_int),
+    "lbm_lattice_create_custom": ([C.c_int, C.POINTER(C.c_int8), _DP, C.c_double, C.POINTER(_VP)],
+                                  C.c_int),
     "lbm_lattice_destroy": ([_VP], C.c_int),
     "lbm_lattice_info": ([_VP, C.POINTER(C.c_int), _DP, C.POINTER(C.c_int), C.POINTER(C.c_int)],
                          C.c_int),
@@ -185,6 +187,19 @@ def lbm_version():
 def lbm_lattice_create(kind: int):
     h = _VP()
     _check(load().lbm_lattice_create(kind, C.byref(h)), "lbm_lattice_create")
+    return h
+
+
+def lbm_lattice_create_custom(e, w, r: float):
+    """e: (Q, 2) integer velocities, w: (Q,) weights in the same order, r: scale."""
+    e = np.ascontiguousarray(e, dtype=np.int8)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    if e.ndim != 2 or e.shape[1] != 2 or w.shape != (e.shape[0],):
+        raise ValueError("e must be (Q, 2) and w (Q,)")
+    h = _VP()
+    _check(load().lbm_lattice_create_custom(e.shape[0], e.ctypes.data_as(C.POINTER(C.c_int8)),
+                                            _dp(w), float(r), C.byref(h)),
+           "lbm_lattice_create_custom")
     return h
 
 
@@ -436,9 +451,12 @@ def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
 # ---- convenience wrappers (still marshalling only) -----------------------------
 
 class Lattice:
-    def __init__(self, name: str):
+    def __init__(self, name: str, custom=None):
+        """A built-in lattice by name, or custom=(e, w, r): one of the built-in
+        velocity sets with the caller's weights and scale."""
         self.name = name
-        self.h = lbm_lattice_create(LATTICE_KIND[name])
+        self.h = lbm_lattice_create(LATTICE_KIND[name]) if custom is None else \
+            lbm_lattice_create_custom(*custom)
         self.Q, self.r, self.ghost_depth, self.degree = lbm_lattice_info(self.h)
         self.e, self.w = lbm_lattice_tables(self.h)
 
@@ -529,10 +547,10 @@ class Solver:
     """A solver whose device memory is a torch allocation on the current device
     and whose work runs on torch's current CUDA stream."""
 
-    def __init__(self, cfg: Config, stream=None):
+    def __init__(self, cfg: Config, stream=None, lattice: "Lattice | None" = None):
         import torch
         self.cfg = cfg
-        self.lat = Lattice(cfg.lattice)
+        self.lat = lattice if lattice is not None else Lattice(cfg.lattice)
         self.p = cfg.params()
         nbytes = lbm_solver_required_bytes(self.lat.h, self.p)
         self.mem = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")

@@ -145,3 +145,23 @@ def test_accommodation_parameter_checks(lbm):
     r = lbm.make_request("D2Q25", 32, 0.1, 0.1, accom=(0.5, 2.0))
     with pytest.raises(lbm.LBMError):
         lbm.lbm_request_bytes(r)
+
+
+def test_custom_lattice_from_tables(lbm):
+    ref = lbm.Lattice("D2Q25b")
+    perm = np.random.default_rng(3).permutation(ref.Q)
+    cus = lbm.Lattice("custom", custom=(ref.e[perm], ref.w[perm], ref.r))
+    assert cus.Q == 25 and cus.r == ref.r and cus.ghost_depth == 3 and cus.degree == 7
+    assert np.array_equal(cus.e, ref.e) and np.array_equal(cus.w, ref.w)  # library order
+    assert cus.verify(7) < 1e-12
+    bad = ref.w.copy()
+    bad[1] *= 1.001                                  # breaks a shell's symmetry
+    with pytest.raises(lbm.LBMError):
+        lbm.Lattice("custom", custom=(ref.e, bad, ref.r))
+    with pytest.raises(lbm.LBMError):
+        lbm.Lattice("custom", custom=(ref.e[:, ::-1] * 2, ref.w, ref.r))   # not the built-in set
+    with pytest.raises(lbm.LBMError):
+        lbm.Lattice("custom", custom=(ref.e, -ref.w, ref.r))
+    # a weight set that is not a quadrature is accepted but its degree says so
+    w = np.full(25, 1.0 / 25)
+    assert lbm.Lattice("custom", custom=(ref.e, w, ref.r)).degree < 3
