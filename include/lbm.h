@@ -104,6 +104,8 @@ int lbm_lattice_verify(const lbm_lattice *lat, int degree, double *max_err);
 #define LBM_KERNEL_AUTO     0   /* library picks                             */
 #define LBM_KERNEL_DIRECT   1   /* one-pass pull kernel, global loads         */
 #define LBM_KERNEL_STAGED   2   /* TMA-staged tile kernel (shared memory)     */
+#define LBM_KERNEL_CELLWARP 3   /* one warp per cell (grids of a few thousand
+                                   cells; AUTO picks it up to 4096 cells)    */
 
 typedef struct lbm_params {
     int32_t Nx;          /* periodic columns, >= 1                            */

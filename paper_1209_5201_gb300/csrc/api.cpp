@@ -70,7 +70,7 @@ int check_params(const LatticeHost &L, const lbm_params &p) {
     }
     if (p.thermal && (p.T_wall[0] <= 0 || p.T_wall[1] <= 0)) { set_error("T_wall must be > 0"); return LBM_EINVAL; }
     if (!(p.rho0 > 0)) { set_error("rho0 must be > 0"); return LBM_EINVAL; }
-    if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_STAGED) { set_error("bad kernel"); return LBM_EINVAL; }
+    if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_CELLWARP) { set_error("bad kernel"); return LBM_EINVAL; }
     if (!(p.accom[0] >= 0 && p.accom[0] <= 1 && p.accom[1] >= 0 && p.accom[1] <= 1)) {
         set_error("accom must lie in [0, 1]");
         return LBM_EINVAL;
@@ -116,9 +116,11 @@ int dispatch_prec(int prec, F &&fn) {
 }
 
 int effective_kernel(const SolverImpl &s) {
-    // the direct kernel is the faster one on every measured workload; the
-    // autotuner can still choose a staged variant
-    return s.p.kernel != LBM_KERNEL_AUTO ? s.p.kernel : LBM_KERNEL_DIRECT;
+    // the direct kernel is the faster one on every measured grid but the
+    // smallest, where one warp per cell shortens the per-step latency chain;
+    // the autotuner can still choose any kernel
+    if (s.p.kernel != LBM_KERNEL_AUTO) return s.p.kernel;
+    return (long long)s.p.Nx * s.p.Ny <= kCellwarpAutoCells ? LBM_KERNEL_CELLWARP : LBM_KERNEL_DIRECT;
 }
 
 // Error flags the staged kernel raises when a bounded wait runs out.
@@ -225,8 +227,9 @@ int dispatch_init_rest(SolverImpl &s) {
 int launch_step_variant(SolverImpl &s, int src, int dst, int kernel, int variant) {
     return dispatch_prec(s.p.precision, [&](auto P) {
         constexpr int PP = decltype(P)::value;
-        return kernel == LBM_KERNEL_STAGED ? Launch<PP>::step_staged(s, src, dst, variant)
-                                           : Launch<PP>::step(s, src, dst, variant);
+        return kernel == LBM_KERNEL_STAGED     ? Launch<PP>::step_staged(s, src, dst, variant)
+               : kernel == LBM_KERNEL_CELLWARP ? Launch<PP>::step_cellwarp(s, src, dst)
+                                               : Launch<PP>::step(s, src, dst, variant);
     });
 }
 
@@ -770,9 +773,10 @@ int lbm_solver_wall_mass(lbm_solver *h, double *m_in) {
 int lbm_solver_set_kernel(lbm_solver *h, int32_t kernel, int32_t variant) {
     if (!h) { set_error("NULL solver"); return LBM_EINVAL; }
     SolverImpl &s = h->s;
-    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_STAGED) { set_error("bad kernel"); return LBM_EINVAL; }
-    const int nv = kernel == LBM_KERNEL_STAGED ? staged_variant_count(s.p.precision)
-                                               : direct_variant_count(s.p.precision);
+    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_CELLWARP) { set_error("bad kernel"); return LBM_EINVAL; }
+    const int nv = kernel == LBM_KERNEL_STAGED     ? staged_variant_count(s.p.precision)
+                   : kernel == LBM_KERNEL_CELLWARP ? 1
+                                                   : direct_variant_count(s.p.precision);
     if (variant < 0 || variant >= nv) { set_error("bad variant"); return LBM_EINVAL; }
     s.p.kernel = kernel;
     s.variant = variant;
@@ -788,12 +792,14 @@ int lbm_solver_kernel_info(lbm_solver *h, int32_t *kernel, int32_t *variant, int
 }
 
 int lbm_solver_variant_count(lbm_solver *h, int32_t kernel, int32_t *n) {
-    if (!h || !n || (kernel != LBM_KERNEL_DIRECT && kernel != LBM_KERNEL_STAGED)) {
+    if (!h || !n || (kernel != LBM_KERNEL_DIRECT && kernel != LBM_KERNEL_STAGED &&
+                     kernel != LBM_KERNEL_CELLWARP)) {
         set_error("bad argument");
         return LBM_EINVAL;
     }
-    *n = kernel == LBM_KERNEL_STAGED ? staged_variant_count(h->s.p.precision)
-                                     : direct_variant_count(h->s.p.precision);
+    *n = kernel == LBM_KERNEL_STAGED     ? staged_variant_count(h->s.p.precision)
+         : kernel == LBM_KERNEL_CELLWARP ? 1
+                                         : direct_variant_count(h->s.p.precision);
     return LBM_OK;
 }
 

@@ -1,7 +1,7 @@
 // Tile / block-shape autotuner of the step kernel.
 //
 // Candidates: every variant of the one-pass direct kernel and of the TMA-staged one compiled
-// for the solver's precision.  Each runs `trial` steps after two warm-up
+// for the solver's precision, and the one-warp-per-cell kernel on small grids.  Each runs `trial` steps after two warm-up
 // steps, timed with CUDA events on the solver's stream; the fastest wins.
 // Results are cached per (lattice, precision, order, Nx class, Ny class) for
 // the life of the process and, when LBM_AUTOTUNE_CACHE names a file, across
@@ -118,6 +118,11 @@ int autotune_solver(SolverImpl &s, int trial) {
     for (int v = 0; v < nv; ++v) {
         if ((rc = time_candidate(s, LBM_KERNEL_STAGED, v, trial, &ms))) return rc;
         if (ms < best.ms) best = Choice{LBM_KERNEL_STAGED, v, ms};
+    }
+    // one warp per cell: only a candidate for small grids (32 threads a cell)
+    if ((long long)s.p.Nx * s.p.Ny <= 16 * kCellwarpAutoCells) {
+        if ((rc = time_candidate(s, LBM_KERNEL_CELLWARP, 0, trial, &ms))) return rc;
+        if (ms < best.ms) best = Choice{LBM_KERNEL_CELLWARP, 0, ms};
     }
     s.p.kernel = best.kernel;
     s.variant = best.variant;

@@ -68,18 +68,6 @@ __host__ __device__ inline bool batch_uses_smem(int Ny, int CL) {
     return CL > 1 && batch_rows_per_cta(Ny, CL) <= kSmemRows;
 }
 
-// compile-time loop a = A, A + 1, ..., N - 1
-template <int A, int N>
-struct StaticFor {
-    template <class F>
-    __device__ __forceinline__ static void run(F &&fn) {
-        if constexpr (A < N) {
-            fn(std::integral_constant<int, A>{});
-            StaticFor<A + 1, N>::run(fn);
-        }
-    }
-};
-
 // Population a of the wall re-emission (Eq. (9) with R = accom R_D + (1 -
 // accom) R_S): the diffuse part formed by the wall warp, plus the specular
 // part (the mirrored velocity of the same row, `spec`, read only when accom <

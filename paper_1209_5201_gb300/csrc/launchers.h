@@ -11,6 +11,7 @@ struct Launch {
     static int step(SolverImpl &s, int src, int dst, int variant);   // direct kernel
     static int direct_variants();
     static int step_staged(SolverImpl &s, int src, int dst, int variant);
+    static int step_cellwarp(SolverImpl &s, int src, int dst);
     static int staged_variants();
     static int init_rest(SolverImpl &s);
     static int init_fields(SolverImpl &s, const double *rho, const double *ux,

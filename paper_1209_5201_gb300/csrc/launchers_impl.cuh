@@ -3,6 +3,7 @@
 
 #include "k_aux.cuh"
 #include "k_fluxes.cuh"
+#include "k_step_cellwarp.cuh"
 #include "k_step_direct.cuh"
 #include "k_step_staged.cuh"
 #include "launchers.h"
@@ -73,6 +74,17 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
 
 template <int PREC>
 int Launch<PREC>::direct_variants() { return DirectVariants::n; }
+
+template <int PREC>
+int Launch<PREC>::step_cellwarp(SolverImpl &s, int src, int dst) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    const long long cells = (long long)s.p.Nx * s.p.Ny;
+    if (cells > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+    LBM_DISPATCH_Q(s.L.Q, (k_step_cellwarp<QQ, PREC><<<(unsigned)cells, 32, 0, s.stream>>>(
+                               (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k)));
+    return (int)cudaGetLastError();
+}
 
 // ---- TMA-staged kernel variants (tile TX x TY, ring of STAGES, CPT cells per
 // consumer thread); the autotuner picks one per solver ------------------------

@@ -222,6 +222,18 @@ specular_source(const typename Store<PREC>::S *__restrict__ fin, const float *__
     return v;
 }
 
+// compile-time loop a = A, A + 1, ..., N - 1
+template <int A, int N>
+struct StaticFor {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&fn) {
+        if constexpr (A < N) {
+            fn(std::integral_constant<int, A>{});
+            StaticFor<A + 1, N>::run(fn);
+        }
+    }
+};
+
 // compile-time loop over the velocity pairs (a = 1, 3, 5, ...)
 template <int A, int Q>
 struct PairLoop {

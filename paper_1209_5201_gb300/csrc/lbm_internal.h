@@ -16,6 +16,7 @@ namespace lbm {
 constexpr int kMaxQ = 37;
 constexpr int kMaxShells = 8;
 constexpr int kPadL = 4;          // periodic image columns kept left of x = 0
+constexpr long long kCellwarpAutoCells = 4096;   // LBM_KERNEL_AUTO: one warp per cell up to here
 
 struct LatticeHost {
     int kind;

@@ -2,7 +2,9 @@
 -+0.1, Kn = 0.1): FP64, FP32 (deviations from the rest weights) and BF16
 deviation storage, each run to its steady-state tolerance (1e-8 FP64, 1e-6
 otherwise), against the FP64 oracle's steady state (residual 1e-10).
-L-inf errors in rho, u_x / U_w and the kinetic temperature."""
+L-inf errors in rho, u_x / U_w and the kinetic temperature, with the
+one-thread-per-cell kernel and with the one-warp-per-cell kernel (the
+automatic choice on a grid this small)."""
 import numpy as np
 import pytest
 
@@ -12,17 +14,20 @@ pytestmark = pytest.mark.gpu
 
 # BF16 keeps 8 significant bits of d = f - w rho (|d| up to ~0.3 w here); the
 # steady state carries that round-off amplified by the relaxation time, a
-# floor measured at 4.4e-2 U_w in u_x and 2e-4 in rho; its residual stalls
-# near 5e-5, so the 1e-6 target is not reached (ENOTCONVERGED is expected).
+# floor measured at 4.4e-2 U_w in u_x with both kernels and 2e-4 (one thread
+# per cell) or 1.1e-3 (one warp per cell: its moment sums round differently)
+# in rho; the residual stalls at 5e-5 .. 6e-4, so the 1e-6 target is not
+# reached (ENOTCONVERGED is expected).
 BOUNDS = {          # rho, u_x / U_w, T
     "fp64": (1e-9, 1e-7, 1e-9),
     "fp32": (2e-6, 5e-6, 2e-6),
-    "bf16dev": (1e-3, 6e-2, 5e-3),
+    "bf16dev": (2.5e-3, 6e-2, 5e-3),
 }
+KERNELS = {"thread": 1, "warp": 3}
 TOL = {"fp64": 1e-8, "fp32": 1e-6, "bf16dev": 1e-6}
 
 
-def sweep(lbm, oracle):
+def sweep(lbm, oracle, kernel):
     Uw = 0.1
     p = oracle.Problem(lattice="D2Q25", Nx=1, Ny=64, Kn=0.1, u_wall=(-Uw, Uw))
     f = oracle.init_fields(p, np.ones((64, 1)))
@@ -34,7 +39,7 @@ def sweep(lbm, oracle):
     out = {}
     for prec in ("fp64", "fp32", "bf16dev"):
         s = lbm.Solver(lbm.Config(lattice="D2Q25", Nx=1, Ny=64, Kn=0.1, u_wall=(-Uw, Uw),
-                                  precision=prec))
+                                  precision=prec, kernel=kernel))
         s.init()
         st, steps, res = s.run_to_residual(TOL[prec], 2_000_000, 100)
         rho, ux, uy, T = s.macros()
@@ -51,9 +56,10 @@ def lbm_mod():
     return need_gpu()
 
 
-def test_precision_sweep_against_oracle_steady_state(lbm_mod, oracle):
-    res = sweep(lbm_mod, oracle)
-    report("precision_sweep", res)
+@pytest.mark.parametrize("kname", sorted(KERNELS))
+def test_precision_sweep_against_oracle_steady_state(lbm_mod, oracle, kname):
+    res = sweep(lbm_mod, oracle, KERNELS[kname])
+    report("precision_sweep" + ("" if kname == "thread" else "_cellwarp"), res)
     for prec, r in res.items():
         b = BOUNDS[prec]
         assert r["err_rho"] < b[0] and r["err_u"] < b[1] and r["err_T"] < b[2], (prec, r)
