@@ -159,6 +159,8 @@ def run_batched(lbm, n=256, seed=7, tol=1e-5, baseline_every=16, baseline_budget
     same instances run alone with the single-domain solver (one step launch
     per step) for the same step counts, timed on every baseline_every-th
     instance and extrapolated."""
+    import numpy as np
+
     import inputs
     insts = inputs.batched_instances(n, seed=seed)
     ctas = resident_ctas()
@@ -197,7 +199,32 @@ def run_batched(lbm, n=256, seed=7, tol=1e-5, baseline_every=16, baseline_budget
         base_n += 1
         sv.close()
     base_rate = base_n / base_t if base_t > 0 else None
+    # the oracle (as it stands) on the cheapest of every 16th instance, the
+    # same step counts, until ~10 s of host time
+    from oracle import oracle as orc
+    sample = sorted(range(0, n, baseline_every),
+                    key=lambda k: res[ids[k]].steps * insts[k].Ny * Q_OF[insts[k].lattice])
+    o_t, o_cells, o_done = 0.0, 0, []
+    for k in sample:
+        if o_t > 10.0:
+            break
+        it = insts[k]
+        p = orc.Problem(lattice=it.lattice, Nx=1, Ny=it.Ny, eq_order=it.eq_order,
+                        thermal=it.thermal, Kn=it.Kn, u_wall=(-it.U_w, it.U_w),
+                        T_wall=(it.T_w, it.T_w))
+        f = orc.init_fields(p, np.ones((it.Ny, 1)))
+        t1 = time.perf_counter()
+        orc.run(p, f, res[ids[k]].steps)
+        o_t += time.perf_counter() - t1
+        o_cells += res[ids[k]].steps * it.Ny
+        o_done.append(k)
+    cpu = {"value": len(o_done) / o_t if o_t > 0 else None, "unit": "solves/s",
+           "MLUPS": o_cells / o_t / 1e6 if o_t > 0 else None, "cores": orc.num_threads(),
+           "kind": "oracle",
+           "sample": f"{len(o_done)} cheapest of every {baseline_every}th instance "
+                     f"({o_cells:.3g} lattice updates, the GPU's step counts)"}
     return {"instances": n, "seed": seed, "tol": tol, "converged": ok,
+            "cpu_baseline": cpu,
             "makespan_s": makespan, "solves_per_s": n / makespan,
             "one_launch_per_solve_solves_per_s": base_rate,
             "speedup_vs_one_launch_per_solve": (n / makespan) / base_rate if base_rate else None,
@@ -279,6 +306,7 @@ def run_column_fp64(lbm, steps=20000):
     s.init()
     s.step(100)
     s.sync()
+    s_kernel = {1: "direct", 2: "staged", 3: "cellwarp"}.get(s.kernel_info()[0], "?")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s.stream)
     s.step(steps)
@@ -286,18 +314,26 @@ def run_column_fp64(lbm, steps=20000):
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     s.close()
-    # CPU baseline: the oracle (as it stands) on the same 20000 steps
+    # CPU baseline: the oracle (as it stands) on the same 20000 steps, on all
+    # host cores and on one
     p = orc.Problem(lattice="D2Q25", Nx=1, Ny=64, Kn=0.1, u_wall=(-0.1, 0.1))
-    f = orc.init_fields(p, np.ones((64, 1)))
-    t0 = time.perf_counter()
-    orc.run(p, f, steps)
-    ot = time.perf_counter() - t0
+    cores = orc.num_threads()
+    ot = {}
+    for n in (cores, 1):
+        orc.set_num_threads(n)
+        f = orc.init_fields(p, np.ones((64, 1)))
+        t0 = time.perf_counter()
+        orc.run(p, f, steps)
+        ot[n] = time.perf_counter() - t0
+    orc.set_num_threads(cores)
     return {"workload": "D2Q25 2nd-order isothermal Couette 1x64 FP64, 20000 steps",
             "us_per_step": ms * 1e3 / steps, "MLUPS": 64 * steps / (ms * 1e-3) / 1e6,
-            "gpu_launches": steps,
-            "cpu_baseline": {"value": 64 * steps / ot / 1e6, "unit": "MLUPS",
-                             "us_per_step": ot * 1e6 / steps, "cores": orc.num_threads(),
-                             "kind": "oracle", "sample": "the same 20000 steps"}}
+            "kernel": s_kernel, "gpu_launches": steps,
+            "cpu_baseline": {"value": 64 * steps / ot[cores] / 1e6, "unit": "MLUPS",
+                             "us_per_step": ot[cores] * 1e6 / steps, "cores": cores,
+                             "kind": "oracle", "sample": "the same 20000 steps",
+                             "one_core": {"value": 64 * steps / ot[1] / 1e6,
+                                          "us_per_step": ot[1] * 1e6 / steps}}}
 
 
 def run_reference(args):

@@ -445,3 +445,13 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops from now on (timing on one core or all). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

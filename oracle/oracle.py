@@ -67,6 +67,8 @@ def _load():
         lib.orc_macros.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp, dp, dp]
         lib.orc_macros_kinetic.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp,
                                            dp, dp]
+        lib.orc_set_num_threads.argtypes = [C.c_int]
+        lib.orc_set_num_threads.restype = None
         lib.orc_fluxes.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp, dp, dp, dp, dp,
                                    dp]
         lib.orc_run_to_residual.argtypes = [C.POINTER(_Lattice), C.POINTER(_Params), dp,
@@ -118,6 +120,10 @@ class Problem:
 
     def new_state(self) -> np.ndarray:
         return np.zeros((self.Q, self.Ny, self.Nx), dtype=np.float64)
+
+
+def set_num_threads(n: int) -> None:
+    _load().orc_set_num_threads(int(n))
 
 
 def num_threads() -> int:

@@ -1,6 +1,7 @@
 """Accuracy of the batched / serving path against the FP64 oracle, on the
 instances of the batched (seed 7) and serving (seed 11) workloads whose oracle
-steady state is cheap enough for the CPU (est. <= 4e6 cell-steps each).
+steady state is cheap enough for the CPU (est. <= 4e6 cell-steps each): the
+first 20 of the batched set and the first 50 of the serving set.
 
 Each request is solved to an extrapolated distance to the steady state of
 1e-5; the L-inf error of u_x / U_w (and of T for the thermal lattice) against
@@ -42,13 +43,13 @@ def test_steady_profiles_within_1e5(oracle, workload):
     lbm = need_gpu()
     insts = inputs.batched_instances(256, seed=7) if workload == "batched" else \
         inputs.serving_requests(2000, seed=11)
-    sample = cheap(insts)
-    assert len(sample) >= 5
-    srv = lbm.Server(mem_budget_bytes=1 << 28, max_slots=32, chunk_steps=100)
+    sample = cheap(insts, limit=20 if workload == "batched" else 50)
+    assert len(sample) >= 10
+    srv = lbm.Server(mem_budget_bytes=1 << 28, max_slots=64, chunk_steps=100)
     ids = [srv.submit(lbm.make_request(it.lattice, it.Ny, it.Kn, it.U_w, it.T_w, tol=1e-5))
            for _, it in sample]
     srv.drain(600)
-    res = {r.id: r for r in srv.poll(64)}
+    res = {r.id: r for r in srv.poll(128)}
     rows = []
     for rid, (k, it) in zip(ids, sample):
         r = res[rid]
