@@ -99,7 +99,10 @@ int lbm_lattice_verify(const lbm_lattice *lat, int degree, double *max_err);
 #define LBM_FP64     0   /* FP64 storage and arithmetic                        */
 #define LBM_FP32     1   /* FP32 storage and arithmetic                        */
 #define LBM_BF16DEV  2   /* BF16 storage of d_a = f~*_a - w_a rho, FP32 rho
-                            plane, FP32 arithmetic                            */
+                            plane, FP32 arithmetic; the step kernels round
+                            the stored d stochastically (unbiased, from a
+                            counter-based hash of step, cell and velocity), so
+                            results are reproducible run to run             */
 
 #define LBM_KERNEL_AUTO     0   /* library picks                             */
 #define LBM_KERNEL_DIRECT   1   /* one-pass pull kernel, global loads         */

@@ -146,8 +146,19 @@ int sum_rho(SolverImpl &s, double *out) {
     return LBM_OK;
 }
 
+// The rounding counter of the current buffer holds the step count.
+int set_round_counter(SolverImpl &s) {
+    s.pinned[63] = 0.0;
+    unsigned v = (unsigned)s.steps;
+    std::memcpy(&s.pinned[63], &v, sizeof v);
+    CU(cudaMemcpyAsync(s.sr + s.cur, &s.pinned[63], sizeof(unsigned), cudaMemcpyHostToDevice, s.stream));
+    CU(cudaStreamSynchronize(s.stream));
+    return LBM_OK;
+}
+
 int after_init(SolverImpl &s) {
     s.steps = 0;
+    if (int rc = set_round_counter(s)) return rc;
     s.last_res = -1;
     int rc = sum_rho(s, &s.mass0);
     if (rc) return rc;
@@ -417,6 +428,7 @@ int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
     s.red = (double *)q;
     s.red_elems = lo.red_bytes / 8;
     s.derr = (int *)(s.red + 8 * 1024 + 48);
+    s.sr = (unsigned *)(s.red + 8 * 1024 + 56);
     s.cur = 0;
     s.tm_key = -1;
     s.variant = 0;
@@ -436,6 +448,8 @@ int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
     }
     fill_consts(s.kd, s.L, s.p, s.pitch);
     fill_consts(s.kf, s.L, s.p, s.pitch);
+    s.kd.f0 = s.kf.f0 = s.f[0];
+    s.kd.sr = s.kf.sr = s.sr;
     s.last_res = -1;
     *out = h;
     return LBM_OK;
@@ -683,6 +697,7 @@ int lbm_solver_set_state(lbm_solver *h, const void *buf, size_t bytes) {
     CU(cudaStreamSynchronize(s.stream));
     s.steps = hd.steps;
     s.mass0 = hd.mass0;
+    if (int rc = set_round_counter(s)) return rc;
     const long long n = (long long)s.p.Nx * s.p.Ny;
     CU(dispatch_prec(s.p.precision, [&](auto P) {
         return Launch<decltype(P)::value>::macros(s, nullptr, s.prev, nullptr, s.prev + n);

@@ -54,6 +54,9 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
     }
     __syncwarp();
     const int j = blockIdx.x / k.Nx, x = blockIdx.x - j * k.Nx;
+    // BF16: step count of the stochastic rounding (block 0 advances it)
+    uint32_t seed = 0;
+    if constexpr (Store<PREC>::dev) seed = step_count(fin, k, blockIdx.x == 0 && lane == 0);
     const bool bot = j < L::N, top = j >= k.Ny - L::N;
 
     // value of population a at padded column xp of row `row`, in the
@@ -146,7 +149,7 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
         C v = col.omc * f + col.cw[s] * (E + O);
         if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
         store_with_images<S>(fout + (long long)a * k.plane + (long long)j * k.pitch, x, k.Nx,
-                             from_c<S>(v));
+                             store_rounded<S>(v, sr_bits(seed, (uint32_t)blockIdx.x, a)));
     };
     if (a0 < Q) relax_store(a0, f0);
     if (a1 < Q) relax_store(a1, f1);

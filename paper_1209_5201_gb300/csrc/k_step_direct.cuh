@@ -106,7 +106,12 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
         wall_prologue<Q, PREC, BX>(fin, rin, k, bot ? 0 : 1, x0, s_min);
         __syncthreads();
     }
+    // BF16: step count of the stochastic rounding (block 0 advances it)
+    uint32_t seed = 0;
+    if constexpr (Store<PREC>::dev)
+        seed = step_count(fin, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
     if (x >= k.Nx) return;
+    const uint32_t cell_id = (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x;
 
     C f[Q];
     if (bot || top) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, f);
@@ -128,8 +133,9 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
         for (int a = 0; a < Q; ++a) {
             C v = o[a];
             if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
-            if (CS) store_cs<S>(dst + k.off_dst[a], from_c<S>(v));
-            else dst[k.off_dst[a]] = from_c<S>(v);
+            const S sv = store_rounded<S>(v, sr_bits(seed, cell_id, a));
+            if (CS) store_cs<S>(dst + k.off_dst[a], sv);
+            else dst[k.off_dst[a]] = sv;
         }
         if constexpr (Store<PREC>::dev) rout[j * k.pitch + x + kPadL] = (float)col.rho;
     } else {
@@ -138,7 +144,8 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
         for (int a = 0; a < Q; ++a) {
             C v = o[a];
             if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
-            store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx, from_c<S>(v));
+            store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx,
+                                 store_rounded<S>(v, sr_bits(seed, cell_id, a)));
         }
         if constexpr (Store<PREC>::dev) store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);
     }

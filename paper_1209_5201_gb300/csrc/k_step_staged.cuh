@@ -134,6 +134,9 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
     const int ntiles = ntx * nty;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp == Cfg::kConsumerWarps;
+    // BF16: step count of the stochastic rounding (block 0 advances it)
+    uint32_t seed = 0;
+    if constexpr (Cfg::kDev) seed = step_count(fin, k, blockIdx.x == 0 && threadIdx.x == 0);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -283,7 +286,8 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
             for (int a = 0; a < Q; ++a) {
                 C v = o[a];
                 if constexpr (Cfg::kDev) v -= k.w[a] * col.rho;
-                store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx, from_c<S>(v));
+                store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx,
+                                     store_rounded<S>(v, sr_bits(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x, a)));
             }
             if constexpr (Cfg::kDev)
                 store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);

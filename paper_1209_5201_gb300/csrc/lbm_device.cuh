@@ -65,6 +65,47 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16>(float
 template <class S> __device__ __forceinline__ S from_c(double v);
 template <> __device__ __forceinline__ double from_c<double>(double v) { return v; }
 
+// ---- stochastic rounding of the BF16 store -----------------------------------
+// 32 pseudo-random bits per (step, cell, velocity): a counter-based integer
+// hash ("lowbias32", C. Wellons, hash-prospector, 2018) of the population's
+// index mixed with the step count.
+__device__ __forceinline__ uint32_t sr_bits(uint32_t step, uint32_t cell, int a) {
+    uint32_t x = cell * 37u + (uint32_t)a;
+    x ^= step * 0x9E3779B9u;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+// The value to store: BF16 keeps the top 16 bits of the FP32 pattern; adding
+// 16 random bits below them first rounds up with probability equal to the
+// dropped fraction (unbiased), so the fixed point of the rounded iteration
+// carries no systematic round-off.  FP32 / FP64 values are stored as they are.
+template <class S> __device__ __forceinline__ S store_rounded(float v, uint32_t bits);
+template <> __device__ __forceinline__ float store_rounded<float>(float v, uint32_t) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 store_rounded<__nv_bfloat16>(float v,
+                                                                               uint32_t bits) {
+    uint32_t u = __float_as_uint(v);
+    if ((u & 0x7f800000u) != 0x7f800000u) u += bits & 0xffffu;
+    return __ushort_as_bfloat16((unsigned short)(u >> 16));
+}
+template <class S> __device__ __forceinline__ S store_rounded(double v, uint32_t);
+template <> __device__ __forceinline__ double store_rounded<double>(double v, uint32_t) { return v; }
+
+// Step count of this launch's source buffer; block 0 writes the count of the
+// destination buffer (read by the next step only).
+template <class C>
+__device__ __forceinline__ uint32_t step_count(const void *fin, const KConsts<C> &k,
+                                               bool first_thread) {
+    if (k.sr == nullptr) return 0u;
+    const int src = fin == k.f0 ? 0 : 1;
+    const uint32_t n = k.sr[src];
+    if (first_thread) k.sr[src ^ 1] = n + 1u;
+    return n;
+}
+
 __device__ __forceinline__ int wrap(int v, int n) {
     int m = v % n;
     return m < 0 ? m + n : m;

@@ -60,6 +60,10 @@ struct KConsts {
     int mirror[kMaxQ];        // velocity with (e_x, -e_y): specular partner
     double accom[2];          // wall accommodation (1: diffuse)
     double wcoef[2][kMaxQ];   // g^w_a / D_w (0 unless a leaves the wall)
+    // step counter of the stochastic BF16 rounding: sr[b] is the number of
+    // steps done when state buffer b (base f0 for b = 0) is the source
+    const void *f0;
+    unsigned *sr;
 };
 
 // Kernel constants of one solve (Eq. (4)-(5) factors, Eq. (11)-(12) wall
@@ -92,6 +96,7 @@ struct SolverImpl {
     KConsts<double> kd;
     int sm_count;
     int *derr;                // device error flags of the staged kernel
+    unsigned *sr;             // step counters of the stochastic BF16 rounding (2)
     int variant;              // staged-kernel variant in use (see launchers)
     long long tm_key;         // (TX, TY) the tensor maps were encoded for; -1 none
     CUtensorMap tm_f[2];      // 3-D maps (x, y, a) of the two state buffers
