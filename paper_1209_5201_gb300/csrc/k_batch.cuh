@@ -47,15 +47,21 @@ __device__ __forceinline__ unsigned cluster_rank() {
 // Barrier of all threads of the slot's cluster, with release / acquire
 // semantics at cluster scope: every global store of the cluster before it is
 // visible to every thread of the cluster after it.  One CTA: the block barrier.
+__device__ __forceinline__ void cluster_arrive() {
+    // non-.aligned forms: correct even if a warp arrives diverged
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
+}
 __device__ __forceinline__ void slot_barrier(int CL) {
     if (CL == 1) {
         __syncthreads();
         return;
     }
-    // non-.aligned forms: correct even if a warp arrives diverged
-    __syncwarp();
-    asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
-    asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
+    cluster_arrive();
+    cluster_wait();
 }
 
 // Rows of a CTA's shared-memory state: two buffers of Q x kSmemRows floats.
@@ -266,9 +272,11 @@ __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWall
     if (warp == 0 && nb > 0 && lane < nb) jw = j0 + lane;
     if (warp == 1 && nt > 0 && lane < nt) jw = j1 - nt + lane;
     const int jb = mb + (nth - 1 - tid);
+    // a wall warp's incoming terms are rows of its own wall block
+    const bool wall_warp = (warp == 0 && nb > 0) || (warp == 1 && nt > 0);
+    const int wall = warp == 0 ? 0 : 1;
+    if (wall_warp) wall_fill_warp<Q>(d, S, wall, lane, sw.fill[wall]);
     for (int step = 0; step < chunk; ++step) {
-        if (warp == 0 && nb > 0) wall_fill_warp<Q>(d, S, 0, lane, sw.fill[0]);
-        else if (warp == 1 && nt > 0) wall_fill_warp<Q>(d, S, 1, lane, sw.fill[1]);
         for (int it = jw >= 0 ? -1 : 0;; ++it) {
             const int j = it < 0 ? jw : jb + it * nth;
             if (it >= 0 && j >= me) break;
@@ -279,8 +287,20 @@ __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWall
             if (edge) cell_update<Q, true>(d, S, j, sw);
             else cell_update<Q, false>(d, S, j, sw);
         }
-        slot_barrier(CL);
-        S.flip();
+        const bool more = step + 1 < chunk;
+        if (CL == 1) {
+            __syncthreads();
+            S.flip();
+            if (wall_warp && more) wall_fill_warp<Q>(d, S, wall, lane, sw.fill[wall]);
+        } else {
+            // the next step's wall sums read only rows this warp has just
+            // written (visible to it after __syncwarp), so they run between
+            // arriving at the cluster barrier and waiting on it
+            cluster_arrive();
+            S.flip();
+            if (wall_warp && more) wall_fill_warp<Q>(d, S, wall, lane, sw.fill[wall]);
+            cluster_wait();
+        }
     }
 }
 

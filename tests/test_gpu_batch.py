@@ -232,3 +232,14 @@ def test_batch_solve_entry_point(lbm):
     out = lbm.lbm_batch_solve(cfg, reqs)
     assert [r.tag for r in out] == [0, 1, 2, 3]
     assert all(r.status == lbm.LBM_OK and r.steps > 0 for r in out)
+
+
+def test_graph_and_plain_launches_agree(lbm):
+    # the chunk launches replayed as a CUDA graph and issued one by one give
+    # the same results, bit for bit (clusters included)
+    items = LONG[:2] + MIX[:4]
+    a = fixed_steps(lbm, items, 1200)
+    b = fixed_steps(lbm, items, 1200, use_graph=False)
+    for it, x, y in zip(items, a, b):
+        assert x[0].steps == y[0].steps and x[0].residual == y[0].residual, it
+        assert all(np.array_equal(u, v) for u, v in zip(x[1:], y[1:])), it
