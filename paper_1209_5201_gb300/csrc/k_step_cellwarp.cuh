@@ -57,6 +57,7 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
     // BF16: step count of the stochastic rounding (block 0 advances it)
     uint32_t seed = 0;
     if constexpr (Store<PREC>::dev) seed = step_count(fin, k, blockIdx.x == 0 && lane == 0);
+    const uint32_t hcell = Store<PREC>::dev ? sr_cell(seed, (uint32_t)blockIdx.x) : 0u;
     const bool bot = j < L::N, top = j >= k.Ny - L::N;
 
     // value of population a at padded column xp of row `row`, in the
@@ -149,7 +150,7 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
         C v = col.omc * f + col.cw[s] * (E + O);
         if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
         store_with_images<S>(fout + (long long)a * k.plane + (long long)j * k.pitch, x, k.Nx,
-                             store_rounded<S>(v, sr_bits(seed, (uint32_t)blockIdx.x, a)));
+                             store_rounded<S>(v, sr_bits(hcell, a)));
     };
     if (a0 < Q) relax_store(a0, f0);
     if (a1 < Q) relax_store(a1, f1);

@@ -111,7 +111,7 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
     if constexpr (Store<PREC>::dev)
         seed = step_count(fin, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
     if (x >= k.Nx) return;
-    const uint32_t cell_id = (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x;
+    const uint32_t hcell = Store<PREC>::dev ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
 
     C f[Q];
     if (bot || top) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, f);
@@ -133,7 +133,7 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
         for (int a = 0; a < Q; ++a) {
             C v = o[a];
             if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
-            const S sv = store_rounded<S>(v, sr_bits(seed, cell_id, a));
+            const S sv = store_rounded<S>(v, sr_bits(hcell, a));
             if (CS) store_cs<S>(dst + k.off_dst[a], sv);
             else dst[k.off_dst[a]] = sv;
         }
@@ -145,7 +145,7 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
             C v = o[a];
             if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
             store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx,
-                                 store_rounded<S>(v, sr_bits(seed, cell_id, a)));
+                                 store_rounded<S>(v, sr_bits(hcell, a)));
         }
         if constexpr (Store<PREC>::dev) store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);
     }

@@ -282,12 +282,13 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                 col.template pair<A>(fv[q][A], fv[q][A + 1], o[A], o[A + 1]);
             });
             const long long roff = (long long)j * k.pitch;
+            const uint32_t hcell = Cfg::kDev ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 C v = o[a];
                 if constexpr (Cfg::kDev) v -= k.w[a] * col.rho;
                 store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx,
-                                     store_rounded<S>(v, sr_bits(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x, a)));
+                                     store_rounded<S>(v, sr_bits(hcell, a)));
             }
             if constexpr (Cfg::kDev)
                 store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);

@@ -66,18 +66,22 @@ template <class S> __device__ __forceinline__ S from_c(double v);
 template <> __device__ __forceinline__ double from_c<double>(double v) { return v; }
 
 // ---- stochastic rounding of the BF16 store -----------------------------------
-// 32 pseudo-random bits per (step, cell, velocity): a counter-based integer
-// hash ("lowbias32", C. Wellons, hash-prospector, 2018) of the population's
-// index mixed with the step count.
-__device__ __forceinline__ uint32_t sr_bits(uint32_t step, uint32_t cell, int a) {
-    uint32_t x = cell * 37u + (uint32_t)a;
-    x ^= step * 0x9E3779B9u;
+// 16 pseudo-random bits per (step, cell, velocity): one counter-based integer
+// hash per cell ("lowbias32", C. Wellons, hash-prospector, 2018) of the cell's
+// index mixed with the step count, then per velocity the top 16 bits of its
+// product with an odd multiplier that depends on the velocity (one multiply
+// per population instead of a hash).
+__device__ __forceinline__ uint32_t sr_cell(uint32_t step, uint32_t cell) {
+    uint32_t x = cell ^ (step * 0x9E3779B9u);
     x ^= x >> 16;
     x *= 0x7feb352du;
     x ^= x >> 15;
     x *= 0x846ca68bu;
     x ^= x >> 16;
     return x;
+}
+__device__ __forceinline__ uint32_t sr_bits(uint32_t hcell, int a) {
+    return (hcell * (0x9E3779B9u * (2u * (uint32_t)a + 1u))) >> 16;
 }
 // The value to store: BF16 keeps the top 16 bits of the FP32 pattern; adding
 // 16 random bits below them first rounds up with probability equal to the
@@ -88,7 +92,7 @@ template <> __device__ __forceinline__ float store_rounded<float>(float v, uint3
 template <> __device__ __forceinline__ __nv_bfloat16 store_rounded<__nv_bfloat16>(float v,
                                                                                uint32_t bits) {
     uint32_t u = __float_as_uint(v);
-    if ((u & 0x7f800000u) != 0x7f800000u) u += bits & 0xffffu;
+    if ((u & 0x7f800000u) != 0x7f800000u) u += bits;   // bits < 2^16
     return __ushort_as_bfloat16((unsigned short)(u >> 16));
 }
 template <class S> __device__ __forceinline__ S store_rounded(double v, uint32_t);

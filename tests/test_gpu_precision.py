@@ -16,14 +16,14 @@ pytestmark = pytest.mark.gpu
 # With round-to-nearest the steady state carried that round-off as a bias
 # amplified by the relaxation time (4.4e-2 U_w in u_x); the step kernels now
 # round stochastically, so the steady state carries zero-mean noise instead:
-# measured 3.7e-3 (one thread per cell) and 4.7e-3 (one warp per cell) U_w in
-# u_x, 2.5e-4 / 3.0e-4 in rho, 1.7e-4 / 2.3e-4 in T; bounds about 3x those.
-# The noise keeps the residual near 4e-3, so the 1e-6 target is not reached
-# (ENOTCONVERGED is expected).
+# over two random streams and both kernels, measured 3.7e-3 .. 5.3e-3 U_w in
+# u_x, 2.5e-4 .. 6.6e-4 in rho, 1.3e-4 .. 2.3e-4 in T; bounds about 3x the
+# largest.  The noise keeps the residual near 4e-3, so the 1e-6 target is not
+# reached (ENOTCONVERGED is expected).
 BOUNDS = {          # rho, u_x / U_w, T
     "fp64": (1e-9, 1e-7, 1e-9),
     "fp32": (2e-6, 5e-6, 2e-6),
-    "bf16dev": (1e-3, 1.5e-2, 1e-3),
+    "bf16dev": (2e-3, 1.5e-2, 1e-3),
 }
 KERNELS = {"thread": 1, "warp": 3}
 TOL = {"fp64": 1e-8, "fp32": 1e-6, "bf16dev": 1e-6}
