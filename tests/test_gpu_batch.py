@@ -243,3 +243,17 @@ def test_graph_and_plain_launches_agree(lbm):
     for it, x, y in zip(items, a, b):
         assert x[0].steps == y[0].steps and x[0].residual == y[0].residual, it
         assert all(np.array_equal(u, v) for u, v in zip(x[1:], y[1:])), it
+
+
+@pytest.mark.parametrize("Ny", [257, 300, 511, 513, 1023, 1025, 1100, 2047, 2049, 4096, 8192])
+def test_split_at_class_boundaries(lbm, Ny):
+    # heights around every cluster-size boundary, up to the largest: the rows
+    # split over 2, 4 or 8 CTAs (shared memory or global memory) step exactly
+    # like one CTA holding them all
+    item = [("D2Q17", Ny, 0.002, 0.1, 1.0)]
+    split = fixed_steps(lbm, item, 300, max_slots=16)[0]
+    whole = fixed_steps(lbm, item, 300, max_slots=16, cluster_rows=8192)[0]
+    assert split[0].steps == whole[0].steps and split[0].residual == whole[0].residual
+    for x, y in zip(split[1:], whole[1:]):
+        assert np.array_equal(x, y)
+    assert abs(np.sum(split[1]) - Ny) < 1e-3 * Ny          # rho: the walls conserve mass
