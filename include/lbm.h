@@ -50,6 +50,7 @@ extern "C" {
 #define LBM_ETIMEOUT       6   /* a bounded device or host wait ran out      */
 #define LBM_ECUDA          7   /* a CUDA runtime call failed                 */
 #define LBM_EBUSY          8   /* queue or slot table full; retry later      */
+#define LBM_ECANCELLED     9   /* the request was cancelled by the caller    */
 
 /* Text of a status code (static storage). */
 const char *lbm_status_string(int status);
@@ -376,6 +377,12 @@ int lbm_server_poll(lbm_server *srv, lbm_result *out, int32_t max, int32_t *n);
  * NULL) and release them.  Errors: LBM_EINVAL for an unknown / fetched id. */
 int lbm_server_fetch(lbm_server *srv, uint64_t id, double *rho, double *ux,
                      double *uy, double *T);
+/* Cancel request `id`: a queued request is dropped, a running one stops at
+ * the end of its current chunk.  Either completes with status LBM_ECANCELLED
+ * (poll returns it, drain counts it); fetch then gives the fields where a
+ * running request stopped, and zeros for one that never ran.  Thread-safe.
+ * Errors: LBM_EINVAL (no queued or running request with this id). */
+int lbm_server_cancel(lbm_server *s, uint64_t id);
 /* Block until every submitted request has finished, or timeout_s seconds.
  * Errors: LBM_ETIMEOUT, or the worker's LBM_ECUDA. */
 int lbm_server_drain(lbm_server *srv, double timeout_s);

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launchers.h"
 #include "lbm_internal.h"
 
@@ -267,6 +269,7 @@ const char *lbm_status_string(int st) {
     case LBM_ETIMEOUT: return "timeout";
     case LBM_ECUDA: return "CUDA error";
     case LBM_EBUSY: return "busy";
+    case LBM_ECANCELLED: return "cancelled";
     default: return "unknown status";
     }
 }
@@ -532,8 +535,15 @@ int ensure_step_graph(SolverImpl &s, int kern) {
 }  // namespace
 }  // namespace lbm
 
+// NVTX range for the duration of a scope (visible in profilers' timelines)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 int lbm_solver_step(lbm_solver *h, int64_t n) {
     API_BEGIN
+    NvtxRange nvtx("lbm_solver_step");
     if (!h || n < 0) { set_error("NULL solver or negative step count"); return LBM_EINVAL; }
     SolverImpl &s = h->s;
     const int kern = effective_kernel(s);
@@ -710,6 +720,7 @@ int lbm_solver_set_state(lbm_solver *h, const void *buf, size_t bytes) {
 int lbm_solver_run_to_residual(lbm_solver *h, double tol, int64_t max_steps, int32_t check_every,
                                int64_t *steps, double *res) {
     API_BEGIN
+    NvtxRange nvtx("lbm_solver_run_to_residual");
     if (!h || check_every < 1 || max_steps < 0 || !(tol >= 0)) { set_error("bad argument"); return LBM_EINVAL; }
     SolverImpl &s = h->s;
     const long long n = (long long)s.p.Nx * s.p.Ny;

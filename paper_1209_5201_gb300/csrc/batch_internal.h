@@ -13,6 +13,7 @@ constexpr int kSlotConverged = 2;
 constexpr int kSlotNonFinite = 3;
 constexpr int kSlotMaxSteps = 4;
 constexpr int kSlotStagnated = 5;
+constexpr int kSlotCancelled = 6;         // set by the host; the kernel skips the slot
 
 struct SlotDesc {
     int Q;                    // 17, 25 or 37 (0: idle slot)

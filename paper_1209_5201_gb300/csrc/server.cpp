@@ -31,6 +31,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "batch_internal.h"
 #include "lbm_internal.h"
 
@@ -112,6 +114,7 @@ struct ServerImpl {
     std::deque<Pending> queue;
     std::map<uint64_t, Done> done;
     std::deque<uint64_t> unpolled;
+    std::vector<uint64_t> cancels;           // running requests to stop (worker applies)
     std::vector<double> latencies;
     uint64_t next_id = 1;
     int64_t submitted = 0, completed = 0;
@@ -311,9 +314,18 @@ struct ServerImpl {
 
     // one loop of the worker; returns false when there is nothing to do
     int loop_once(bool &idle) {
-        std::vector<int> admitted;
+        std::vector<int> admitted, stopped;
         {
             std::unique_lock<std::mutex> lk(mu);
+            // running requests cancelled since the last chunk: marked stopped
+            // on the host and, below, on the device, then retired as finished
+            for (uint64_t id : cancels)
+                for (int s = 0; s < (int)slots.size(); ++s)
+                    if (slots[s].busy && slots[s].id == id && h_status[s].state == kSlotRunning) {
+                        h_status[s].state = kSlotCancelled;
+                        stopped.push_back(s);
+                    }
+            cancels.clear();
             // CTAs beyond one for every queued request go to the longest queued
             // requests (among the first 512), longest first, as clusters: the
             // GPU's idle CTAs shorten the requests that set the latency tail,
@@ -362,8 +374,12 @@ struct ServerImpl {
             }
             idle = running == 0;
         }
-        if (idle) return LBM_OK;
         cudaError_t e;
+        for (int s : stopped)
+            if ((e = cudaMemcpyAsync(d_status + s, h_status + s, sizeof(SlotStatus),
+                                     cudaMemcpyHostToDevice, stream)))
+                return fail("upload cancelled status", e);
+        if (idle) return LBM_OK;
         if (!admitted.empty()) {
             // only the admitted entries: running slots' buffer index lives on the device
             for (int s : admitted)
@@ -376,6 +392,7 @@ struct ServerImpl {
                 return fail("init kernel", e);
         }
         // chunk launch + status read-back
+        nvtxRangePushA("lbm_server_chunk");
         if (graph) {
             if ((e = cudaGraphLaunch(graph, stream))) return fail("graph launch", e);
         } else {
@@ -385,7 +402,9 @@ struct ServerImpl {
             if ((e = cudaMemcpyAsync(h_dbg, d_dbg, sizeof(int) * 8, cudaMemcpyDeviceToHost, stream)))
                 return fail("check read-back", e);
         }
-        if ((e = cudaStreamSynchronize(stream))) return fail("chunk", e);
+        e = cudaStreamSynchronize(stream);
+        nvtxRangePop();
+        if (e) return fail("chunk", e);
         if (h_dbg[0]) return reject_desc();
         ++chunks;
         occupancy_sum += used_ctas;
@@ -427,8 +446,9 @@ struct ServerImpl {
                 std::memset(&d.meta, 0, sizeof(d.meta));
                 d.meta.id = si.id;
                 d.meta.tag = si.req.tag;
-                d.meta.status = st.state == kSlotConverged ? LBM_OK
+                d.meta.status = st.state == kSlotConverged   ? LBM_OK
                                 : st.state == kSlotNonFinite ? LBM_ENONFINITE
+                                : st.state == kSlotCancelled ? LBM_ECANCELLED
                                                              : LBM_ENOTCONVERGED;
                 d.meta.Ny = si.req.Ny;
                 d.meta.steps = st.steps;
@@ -439,7 +459,7 @@ struct ServerImpl {
                 d.meta.t_admit = si.t_admit;
                 d.meta.t_done = t;
                 d.fields.assign(h_out + h_off[i], h_out + h_off[i] + 4LL * si.req.Ny);
-                latencies.push_back(t - si.t_submit);
+                if (d.meta.status != LBM_ECANCELLED) latencies.push_back(t - si.t_submit);
                 t_last_done = t;
                 done.emplace(si.id, std::move(d));
                 unpolled.push_back(si.id);
@@ -656,6 +676,39 @@ int lbm_server_poll(lbm_server *h, lbm_result *out, int32_t max, int32_t *n) {
     }
     *n = k;
     if (S.worker_error) { set_error(S.worker_msg); return S.worker_error; }
+    return LBM_OK;
+}
+
+int lbm_server_cancel(lbm_server *h, uint64_t id) {
+    if (!h) { set_error("NULL server"); return LBM_EINVAL; }
+    ServerImpl &S = h->s;
+    {
+        std::unique_lock<std::mutex> lk(S.mu);
+        for (auto it = S.queue.begin(); it != S.queue.end(); ++it)
+            if (it->id == id) {
+                // never admitted: completes at once, with zero fields
+                Done d;
+                std::memset(&d.meta, 0, sizeof(d.meta));
+                d.meta.id = id;
+                d.meta.tag = it->req.tag;
+                d.meta.status = LBM_ECANCELLED;
+                d.meta.Ny = it->req.Ny;
+                d.meta.t_submit = it->t_submit;
+                d.meta.t_admit = d.meta.t_done = S.now();
+                d.fields.assign(4 * (size_t)it->req.Ny, 0.0);
+                S.done.emplace(id, std::move(d));
+                S.unpolled.push_back(id);
+                S.queue.erase(it);
+                ++S.completed;
+                S.cv_done.notify_all();
+                return LBM_OK;
+            }
+        bool running = false;
+        for (const SlotInfo &si : S.slots) running = running || (si.busy && si.id == id);
+        if (!running) { set_error("no queued or running request with this id"); return LBM_EINVAL; }
+        S.cancels.push_back(id);
+    }
+    S.cv_work.notify_one();
     return LBM_OK;
 }
 

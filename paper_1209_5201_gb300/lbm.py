@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblbm_gb300.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_EBUDGET, LBM_ENOTCONVERGED = 0, 1, 2, 3, 4
-LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ECUDA, LBM_EBUSY = 5, 6, 7, 8
+LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ECUDA, LBM_EBUSY, LBM_ECANCELLED = 5, 6, 7, 8, 9
 LBM_LATTICE_D2Q17, LBM_LATTICE_D2Q25, LBM_LATTICE_D2Q25B, LBM_LATTICE_D2Q37 = 17, 25, 26, 37
 LBM_FP64, LBM_FP32, LBM_BF16DEV = 0, 1, 2
 LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_STAGED, LBM_KERNEL_CELLWARP = 0, 1, 2, 3
@@ -124,6 +124,7 @@ _SIGS = {
     "lbm_server_submit": ([_VP, C.POINTER(lbm_request), C.POINTER(C.c_uint64)], C.c_int),
     "lbm_server_poll": ([_VP, C.POINTER(lbm_result), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "lbm_server_fetch": ([_VP, C.c_uint64, _DP, _DP, _DP, _DP], C.c_int),
+    "lbm_server_cancel": ([_VP, C.c_uint64], C.c_int),
     "lbm_server_drain": ([_VP, C.c_double], C.c_int),
     "lbm_server_stats": ([_VP, C.POINTER(lbm_server_metrics)], C.c_int),
     "lbm_server_destroy": ([_VP], C.c_int),
@@ -387,6 +388,10 @@ def lbm_server_poll(h, max_results: int = 1024):
     return [buf[i] for i in range(n.value)]
 
 
+def lbm_server_cancel(h, rid: int) -> None:
+    _check(load().lbm_server_cancel(h, int(rid)), "lbm_server_cancel")
+
+
 def lbm_server_fetch(h, rid: int, Ny: int):
     out = [np.empty(Ny) for _ in range(4)]
     _check(load().lbm_server_fetch(h, C.c_uint64(rid), *[_dp(a) for a in out]),
@@ -521,6 +526,9 @@ class Server:
 
     def poll(self, max_results: int = 1024):
         return lbm_server_poll(self.h, max_results)
+
+    def cancel(self, rid: int):
+        lbm_server_cancel(self.h, rid)
 
     def fetch(self, rid: int, Ny: int):
         return lbm_server_fetch(self.h, rid, Ny)

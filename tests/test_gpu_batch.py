@@ -257,3 +257,30 @@ def test_split_at_class_boundaries(lbm, Ny):
     for x, y in zip(split[1:], whole[1:]):
         assert np.array_equal(x, y)
     assert abs(np.sum(split[1]) - Ny) < 1e-3 * Ny          # rho: the walls conserve mass
+
+
+def test_cancel_running_and_queued_requests(lbm):
+    # one CTA of budget: a long request runs, a second waits in the queue;
+    # cancelling the queued one drops it, cancelling the running one stops it
+    # at the end of its chunk with the fields where it stopped
+    s = lbm.Server(mem_budget_bytes=1 << 26, max_slots=1, chunk_steps=50)
+    run = s.submit(lbm.make_request("D2Q37", 64, 0.002, 0.1, tol=1e-9))
+    wait = s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-6))
+    time.sleep(0.2)
+    s.cancel(wait)
+    s.cancel(run)
+    with pytest.raises(lbm.LBMError):
+        s.cancel(12345)                               # no such request
+    s.drain(60)
+    res = {r.id: r for r in s.poll(8)}
+    assert res[wait].status == lbm.LBM_ECANCELLED and res[wait].steps == 0
+    assert res[run].status == lbm.LBM_ECANCELLED and res[run].steps > 0
+    rho, ux, _, _ = s.fetch(run, 64)
+    assert abs(np.sum(rho) - 64) < 1e-3 and np.max(np.abs(ux)) > 0
+    rho_w, _, _, _ = s.fetch(wait, 24)
+    assert not np.any(rho_w)
+    # the server keeps serving
+    ok = s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-6))
+    s.drain(60)
+    assert s.poll(4)[0].status == lbm.LBM_OK
+    s.close()
