@@ -214,6 +214,12 @@ int lbm_solver_set_state(lbm_solver *s, const void *buf, size_t bytes);
  * the steps run by this call and the last residual. */
 int lbm_solver_run_to_residual(lbm_solver *s, double tol, int64_t max_steps,
                                int32_t check_every, int64_t *steps, double *res);
+/* Residual history of the last lbm_solver_run_to_residual call: one entry per
+ * check, the solver's step count and the residual at that check (the
+ * definition above).  Copies min(max, count) entries; *n receives the count.
+ * Errors: LBM_EINVAL (NULL argument, or max > 0 with NULL arrays). */
+int lbm_solver_residual_history(lbm_solver *s, int64_t *steps, double *res, int32_t max,
+                                int32_t *n);
 
 typedef struct lbm_stats {
     int64_t steps;        /* steps since the last init                        */

@@ -395,9 +395,8 @@ int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
         set_error("device_mem too small or not 256-byte aligned");
         return LBM_EINVAL;
     }
-    lbm_solver *h = new lbm_solver;
+    lbm_solver *h = new lbm_solver();   // value-initialised: plain fields zero
     SolverImpl &s = h->s;
-    std::memset(&s, 0, sizeof(s));
     s.L = lat->L;
     s.p = *p;
     s.stream = (cudaStream_t)stream;
@@ -731,6 +730,7 @@ int lbm_solver_run_to_residual(lbm_solver *h, double tol, int64_t max_steps, int
     int since_best = 0;
     int status = LBM_ENOTCONVERGED;
     int rc = LBM_OK;
+    s.res_history.clear();
     while (done < max_steps) {
         int64_t k = check_every;
         if (done + k > max_steps) k = max_steps - done;
@@ -749,6 +749,7 @@ int lbm_solver_run_to_residual(lbm_solver *h, double tol, int64_t max_steps, int
         if (v[4] > 0) { status = LBM_ENONFINITE; r = NAN; break; }
         r = std::sqrt(v[0]) / std::fmax(std::sqrt(v[1]), 1e-30);
         if (s.p.thermal) r = std::fmax(r, std::sqrt(v[2]) / std::fmax(std::sqrt(v[3]), 1e-30));
+        s.res_history.emplace_back(s.steps, r);
         if (!std::isfinite(r)) { status = LBM_ENONFINITE; break; }
         if (r <= tol) { status = LBM_OK; break; }
         if (r < best) { best = r; since_best = 0; }
@@ -761,6 +762,19 @@ int lbm_solver_run_to_residual(lbm_solver *h, double tol, int64_t max_steps, int
     if (status == LBM_ENONFINITE) set_error("non-finite residual");
     return status;
     API_END
+}
+
+int lbm_solver_residual_history(lbm_solver *h, int64_t *steps, double *res, int32_t max,
+                                int32_t *n) {
+    if (!h || !n || max < 0 || (max > 0 && (!steps || !res))) { set_error("bad argument"); return LBM_EINVAL; }
+    const auto &hist = h->s.res_history;
+    const int k = (int)std::min<size_t>(hist.size(), (size_t)max);
+    for (int i = 0; i < k; ++i) {
+        steps[i] = hist[i].first;
+        res[i] = hist[i].second;
+    }
+    *n = (int32_t)hist.size();
+    return LBM_OK;
 }
 
 int lbm_solver_stats(lbm_solver *h, lbm_stats *st) {

@@ -9,6 +9,9 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <utility>
+#include <vector>
+
 #include "../../include/lbm.h"
 
 namespace lbm {
@@ -91,6 +94,7 @@ struct SolverImpl {
     int64_t steps;
     double mass0;
     double last_res;
+    std::vector<std::pair<int64_t, double>> res_history;   // (steps, residual) of the last steady-state run
     double wall_in[2];
     KConsts<float> kf;
     KConsts<double> kd;

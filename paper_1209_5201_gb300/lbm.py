@@ -108,6 +108,8 @@ _SIGS = {
     "lbm_solver_state_bytes": ([_VP, C.POINTER(C.c_size_t)], C.c_int),
     "lbm_solver_get_state": ([_VP, _VP, C.c_size_t], C.c_int),
     "lbm_solver_set_state": ([_VP, _VP, C.c_size_t], C.c_int),
+    "lbm_solver_residual_history": ([_VP, C.POINTER(C.c_int64), _DP, C.c_int32,
+                                     C.POINTER(C.c_int32)], C.c_int),
     "lbm_solver_run_to_residual": ([_VP, C.c_double, C.c_int64, C.c_int32,
                                     C.POINTER(C.c_int64), _DP], C.c_int),
     "lbm_solver_stats": ([_VP, C.POINTER(lbm_stats)], C.c_int),
@@ -318,6 +320,19 @@ def lbm_solver_run_to_residual(h, tol: float, max_steps: int, check_every: int =
                                                   C.byref(steps), C.byref(res)),
                 "lbm_solver_run_to_residual", ok=(LBM_OK, LBM_ENOTCONVERGED))
     return st, steps.value, res.value
+
+
+def lbm_solver_residual_history(h):
+    n = C.c_int32()
+    _check(load().lbm_solver_residual_history(h, None, None, 0, C.byref(n)),
+           "lbm_solver_residual_history")
+    steps = np.zeros(n.value, dtype=np.int64)
+    res = np.zeros(n.value, dtype=np.float64)
+    if n.value:
+        _check(load().lbm_solver_residual_history(
+            h, steps.ctypes.data_as(C.POINTER(C.c_int64)), _dp(res), n.value, C.byref(n)),
+            "lbm_solver_residual_history")
+    return steps, res
 
 
 def lbm_solver_stats(h) -> lbm_stats:
@@ -620,6 +635,10 @@ class Solver:
 
     def stats(self) -> lbm_stats:
         return lbm_solver_stats(self.h)
+
+    def residual_history(self):
+        """(steps, residual) arrays of the checks of the last run_to_residual."""
+        return lbm_solver_residual_history(self.h)
 
     def get_state(self) -> bytes:
         return lbm_solver_get_state(self.h)

@@ -195,6 +195,13 @@ def test_residual_driver_reports_nonconvergence_and_nan(lbm, oracle):
     s.init_fields(np.ones((32, 1)))
     st, steps, res = s.run_to_residual(1e-14, 300, 100)
     assert st == lbm.LBM_ENOTCONVERGED and steps == 300
+    # one (steps, residual) record per check; the middle one against the
+    # oracle's driver stopped at that check
+    hs, hr = s.residual_history()
+    assert list(hs) == [100, 200, 300] and hr[-1] == res
+    f = oracle.init_fields(p, np.ones((32, 1)))
+    ok, osteps, ores = oracle.run_to_residual(p, f, 0.0, 200, 100)
+    assert not ok and osteps == 200 and abs(hr[1] - ores) <= 1e-8 * ores
     f = s.get_f()
     f[3, 5, 0] = np.nan                     # poisoned state, injected on the host
     s.set_f(f)
