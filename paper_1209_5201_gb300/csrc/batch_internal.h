@@ -15,6 +15,9 @@ constexpr int kSlotMaxSteps = 4;
 constexpr int kSlotStagnated = 5;
 constexpr int kSlotCancelled = 6;         // set by the host; the kernel skips the slot
 
+// Most velocities leaving one wall (e.n > 0): 15 for D2Q37.
+constexpr int kMaxOut = 16;
+
 struct SlotDesc {
     int Q;                    // 17, 25 or 37 (0: idle slot)
     int Ny;
@@ -30,10 +33,14 @@ struct SlotDesc {
     // incoming terms of Eq. (12)'s numerator, built on the host: wall w (0
     // bottom, 1 top), term l < nterm is velocity term_a[w][l] at distance
     // term_row[w][l] from the wall
-    int nterm;
-    int pad1;
+    int nterm;                // < 32: lane nterm of the wall warp carries wterm
+    int nout;                 // outgoing velocities per wall (e.n > 0), <= kMaxOut
     signed char term_a[2][32];
     signed char term_row[2][32];
+    signed char out_a[2][kMaxOut];
+    double wterm[2];          // sum over the incoming terms of their weights w_a
+    double out_c[2][kMaxOut]; // g^w_a / D_w of outgoing velocity out_a[w][l]
+    double out_w[2][kMaxOut]; // its weight w_a as the FP32 storage holds it
     KConsts<float> k;         // per-instance constants (Nx = 1, pitch = 1)
 };
 

@@ -14,11 +14,14 @@ __device__ __forceinline__ bool desc_ok(const SlotDesc &d, long long pool_elems,
                                         int code, int *dbg) {
     const bool q_ok = d.Q == 17 || d.Q == 25 || d.Q == 37;
     const long long need = 2LL * d.Q * d.Ny + 2LL * d.Ny;
-    bool terms_ok = d.nterm >= 1 && d.nterm <= 32;
-    for (int w = 0; w < 2 && terms_ok; ++w)
+    bool terms_ok = d.nterm >= 1 && d.nterm < 32 && d.nout >= 1 && d.nout <= kMaxOut;
+    for (int w = 0; w < 2 && terms_ok; ++w) {
         for (int l = 0; l < d.nterm; ++l)
             terms_ok = terms_ok && d.term_a[w][l] >= 0 && d.term_a[w][l] < d.Q &&
                        d.term_row[w][l] >= 0 && d.term_row[w][l] < 3;
+        for (int l = 0; l < d.nout; ++l)
+            terms_ok = terms_ok && d.out_a[w][l] >= 0 && d.out_a[w][l] < d.Q;
+    }
     bool mirror_ok = true;
     for (int a = 0; a < d.Q && q_ok; ++a)
         mirror_ok = mirror_ok && d.k.mirror[a] >= 0 && d.k.mirror[a] < d.Q;

@@ -32,10 +32,14 @@
 namespace lbm {
 
 // Shared per-step wall data of a slot: the re-emitted deviations of Eq. (12)
-// per wall and velocity and the accommodation of each wall in FP32.
+// per wall and velocity, the accommodation of each wall in FP32, and (state in
+// global memory) the post-collision values of the 3 rows next to each wall,
+// term[w][kk][a] at distance kk from wall w, which the next step's wall sum
+// reads from here instead of from L2.
 struct BatchWallShared {
     float fill[2][kMaxQ];
     float acc[2];
+    float term[2][3][kMaxQ];
 };
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -87,18 +91,48 @@ __device__ __forceinline__ float wall_value(const BatchWallShared &sw, int wall,
     return v;
 }
 
+// Wall rows of a pull (EDGE): f[a] was loaded from the source row clamped into
+// the slot; where the true source lies beyond a wall (e_y > j bottom, j - e_y
+// >= Ny top) it is replaced by that wall's re-emission.  Without specular
+// reflection the replacement is a predicated select, so the pull has no
+// branch between its loads.
+template <int Q, class MirrorFn>
+__device__ __forceinline__ void apply_walls(const BatchWallShared &sw, int j, int Ny,
+                                            float (&f)[Q], MirrorFn &&mirror) {
+    using L = Lat<Q>;
+    if (sw.acc[0] == 1.0f && sw.acc[1] == 1.0f) {
+        StaticFor<0, Q>::run([&](auto ic) {
+            constexpr int a = decltype(ic)::value;
+            if constexpr (L::ey(a) > 0) f[a] = j - L::ey(a) < 0 ? sw.fill[0][a] : f[a];
+            else if constexpr (L::ey(a) < 0) f[a] = j - L::ey(a) >= Ny ? sw.fill[1][a] : f[a];
+        });
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int sj = j - L::ey(a);
+            if (sj < 0 || sj >= Ny)
+                f[a] = wall_value(sw, sj < 0 ? 0 : 1, a, [&] { return mirror(a); });
+        }
+    }
+}
+
 // Slot state in global memory (pool), two buffers of [Q][Ny]; a step reads
 // `src` and writes `dst`, rows of any CTA of the cluster.
 struct GlobalState {
     const float *src;
     float *dst;
     int Ny;
+    float *stage;              // BatchWallShared::term of this CTA
     // population a of slot row `row` of the current state (coherent L2 read:
     // another SM may have written it)
     __device__ __forceinline__ float ld(int a, int row) const {
         return __ldcg(src + (long long)a * Ny + row);
     }
     __device__ __forceinline__ float ld_own(int a, int row) const { return ld(a, row); }
+    // wall w's incoming term (a, kk) of the step just done (staged by store)
+    __device__ __forceinline__ float term(int w, int a, int kk, int) const {
+        return stage[(w * 3 + kk) * kMaxQ + a];
+    }
     // f_in of row j (Eq. (5) pull with the Eq. (12) wall)
     template <int Q, bool EDGE>
     __device__ __forceinline__ void pull(const SlotDesc &d, const BatchWallShared &sw, int j,
@@ -107,16 +141,29 @@ struct GlobalState {
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             const int sj = j - L::ey(a);
-            if (EDGE && (sj < 0 || sj >= Ny))
-                f[a] = wall_value(sw, sj < 0 ? 0 : 1, a, [&] { return ld(d.k.mirror[a], j); });
-            else
-                f[a] = ld(a, sj);
+            f[a] = ld(a, EDGE ? min(max(sj, 0), Ny - 1) : sj);
         }
+        if constexpr (EDGE) apply_walls<Q>(sw, j, Ny, f, [&](int a) { return ld(d.k.mirror[a], j); });
     }
-    template <int Q>
+    template <int Q, bool EDGE>
     __device__ __forceinline__ void store(int j, const float (&o)[Q]) const {
+        using L = Lat<Q>;
 #pragma unroll
         for (int a = 0; a < Q; ++a) dst[(long long)a * Ny + j] = o[a];
+        if constexpr (EDGE) {
+            // the velocities that stream into a wall from its 3 nearest rows
+            if (j < 3) {
+                StaticFor<0, Q>::run([&](auto ic) {
+                    constexpr int a = decltype(ic)::value;
+                    if constexpr (L::ey(a) < 0) stage[j * kMaxQ + a] = o[a];
+                });
+            } else if (j >= Ny - 3) {
+                StaticFor<0, Q>::run([&](auto ic) {
+                    constexpr int a = decltype(ic)::value;
+                    if constexpr (L::ey(a) > 0) stage[(3 + Ny - 1 - j) * kMaxQ + a] = o[a];
+                });
+            }
+        }
     }
     __device__ __forceinline__ void flip() {
         const float *t = src;
@@ -145,6 +192,14 @@ __device__ __forceinline__ float ldsc_f32(uint32_t addr) {
     asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(addr) : "memory");
     return v;
 }
+// The same load without a compiler memory clobber: ordered only against the
+// other volatile asm (the loads, stores and barriers of this file), so the
+// constants read around it can stay in registers.
+__device__ __forceinline__ float ldsc_f32_nc(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(addr));
+    return v;
+}
 // shared::cluster address of the same location in CTA `rank` of the cluster
 __device__ __forceinline__ uint32_t map_rank(uint32_t addr, unsigned rank) {
     uint32_t out;
@@ -163,6 +218,7 @@ template <int Q>
 struct SmemState {
     uint32_t base;             // shared::cta address of buffer 0
     uint32_t lo, hi;           // shared::cluster addresses of the neighbours' buffer 0
+    uint32_t self;             // shared::cluster address of this CTA's buffer 0
     int R, j0, b;
     __device__ __forceinline__ uint32_t row_addr(int buf, int lr) const {
         return base + (uint32_t)((buf * R + lr) * Q) * 4u;
@@ -175,6 +231,10 @@ struct SmemState {
     }
     __device__ __forceinline__ float ld_own(int a, int row) const {
         return lds_f32(row_addr(b, row - j0) + (uint32_t)a * 4u);
+    }
+    // wall w's incoming term (a, kk): row kk from the wall of the current state
+    __device__ __forceinline__ float term(int w, int a, int kk, int Ny) const {
+        return ld_own(a, w == 0 ? kk : Ny - 1 - kk);
     }
     template <int Q_, bool EDGE>
     __device__ __forceinline__ void pull(const SlotDesc &d, const BatchWallShared &sw, int j,
@@ -189,17 +249,20 @@ struct SmemState {
                 f[a] = lds_f32<((3 - L::ey(a)) * Q_ + a) * 4>(r0);
             });
         } else {
+            // source row clamped into the slot, then into this CTA or a
+            // neighbour (selects, no branch): every load goes through the
+            // shared::cluster window and all of them issue back to back
 #pragma unroll
             for (int a = 0; a < Q_; ++a) {
-                const int sj = j - L::ey(a);
-                if (sj < 0 || sj >= d.Ny)
-                    f[a] = wall_value(sw, sj < 0 ? 0 : 1, a, [&] { return ld_own(d.k.mirror[a], j); });
-                else
-                    f[a] = ld(a, sj);
+                const int lr = min(max(j - L::ey(a), 0), d.Ny - 1) - j0;
+                const uint32_t bse = lr < 0 ? lo : (lr >= R ? hi : self);
+                const int rr = lr < 0 ? lr + R : (lr >= R ? lr - R : lr);
+                f[a] = ldsc_f32_nc(bse + (uint32_t)(((b * R + rr) * Q_ + a) * 4));
             }
+            apply_walls<Q_>(sw, j, d.Ny, f, [&](int a) { return ld_own(d.k.mirror[a], j); });
         }
     }
-    template <int Q_>
+    template <int Q_, bool EDGE>
     __device__ __forceinline__ void store(int j, const float (&o)[Q_]) const {
         const uint32_t r = row_addr(b ^ 1, j - j0);
         StaticFor<0, Q_>::run([&](auto ic) {
@@ -212,24 +275,24 @@ struct SmemState {
 
 // Numerator of Eq. (12) for `wall` summed by one full warp in FP64, and the
 // normalised re-emission M_in g^w_a / D_w of each outgoing velocity formed
-// once in FP64 (lanes a and a + 32) and kept as an FP32 deviation from w_a:
-// GB300's FP64 rate is a small fraction of its FP32 rate, so no FP64 work is
-// left in the per-cell update.  The wall rows belong to this CTA.
-template <int Q, class State>
-__device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, const State &S, int wall,
-                                               int lane, float *fill) {
-    const KConsts<float> &k = d.k;
+// once in FP64 (lane l: outgoing velocity out_a[l]) and kept as an FP32
+// deviation from w_a.  Lane l < nterm carries its term's deviation d = f - w,
+// lane nterm the terms' weights summed on the host, so M_in = sum d + sum w;
+// a butterfly of shuffles leaves the same fixed-order sum in every lane.
+// GB300's FP64 rate is a small fraction of its FP32 rate: eight FP64
+// instructions per wall and step, none in the per-cell update.  `term(a, kk)`
+// reads the incoming term (a, kk) of the current state; the wall rows belong
+// to this CTA.
+template <class TermFn>
+__device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, int wall, int lane,
+                                               float *fill, TermFn &&term) {
     double v = 0.0;
-    if (lane < d.nterm) {
-        const int a = d.term_a[wall][lane];
-        const int kk = d.term_row[wall][lane];
-        const int row = wall == 0 ? kk : d.Ny - 1 - kk;
-        v = (double)S.ld_own(a, row) + (double)k.w[a];   // f = d + w
-    }
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const double m = __shfl_sync(0xffffffffu, v, 0);
-    for (int a = lane; a < Q; a += 32)
-        fill[a] = k.wcoef[wall][a] != 0.0 ? (float)(m * k.wcoef[wall][a] - (double)k.w[a]) : 0.0f;
+    if (lane < d.nterm) v = (double)term(d.term_a[wall][lane], d.term_row[wall][lane]);
+    else if (lane == d.nterm) v = d.wterm[wall];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane < d.nout)
+        fill[d.out_a[wall][lane]] = (float)fma(v, d.out_c[wall][lane], -d.out_w[wall][lane]);
     __syncwarp();
 }
 
@@ -255,7 +318,7 @@ __device__ __forceinline__ void cell_update(const SlotDesc &d, const State &S, i
         constexpr int A = decltype(ic)::value;
         col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
     });
-    S.template store<Q>(j, o);
+    S.template store<Q, EDGE>(j, o);
 }
 
 // The chunk's time steps.  Warp 0 of the bottom CTA and warp 1 of the top CTA
@@ -275,7 +338,16 @@ __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWall
     // a wall warp's incoming terms are rows of its own wall block
     const bool wall_warp = (warp == 0 && nb > 0) || (warp == 1 && nt > 0);
     const int wall = warp == 0 ? 0 : 1;
-    if (wall_warp) wall_fill_warp<Q>(d, S, wall, lane, sw.fill[wall]);
+    const int Ny = d.Ny;
+    // the chunk's first wall sums read the state as loaded; later ones the
+    // wall rows just written (staged in shared memory on the global path)
+    if (wall_warp)
+        wall_fill_warp(d, wall, lane, sw.fill[wall],
+                       [&](int a, int kk) { return S.ld_own(a, wall == 0 ? kk : Ny - 1 - kk); });
+    auto fill_next = [&] {
+        wall_fill_warp(d, wall, lane, sw.fill[wall],
+                       [&](int a, int kk) { return S.term(wall, a, kk, Ny); });
+    };
     for (int step = 0; step < chunk; ++step) {
         for (int it = jw >= 0 ? -1 : 0;; ++it) {
             const int j = it < 0 ? jw : jb + it * nth;
@@ -291,14 +363,14 @@ __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWall
         if (CL == 1) {
             __syncthreads();
             S.flip();
-            if (wall_warp && more) wall_fill_warp<Q>(d, S, wall, lane, sw.fill[wall]);
+            if (wall_warp && more) fill_next();
         } else {
             // the next step's wall sums read only rows this warp has just
             // written (visible to it after __syncwarp), so they run between
             // arriving at the cluster barrier and waiting on it
             cluster_arrive();
             S.flip();
-            if (wall_warp && more) wall_fill_warp<Q>(d, S, wall, lane, sw.fill[wall]);
+            if (wall_warp && more) fill_next();
             cluster_wait();
         }
     }
@@ -348,7 +420,7 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
             sm[r * Q + a] = __ldcg(g_cur + (long long)a * Ny + j0 + r);
         }
         const uint32_t base = (uint32_t)__cvta_generic_to_shared(sm);
-        SmemState<Q> S{base, 0u, 0u, R, j0, 0};
+        SmemState<Q> S{base, 0u, 0u, map_rank(base, rank), R, j0, 0};
         if (rank > 0) S.lo = map_rank(base, rank - 1);
         if (rank < CL - 1) S.hi = map_rank(base, rank + 1);
         slot_barrier(CL);                      // every CTA loaded before any neighbour reads
@@ -361,7 +433,7 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         }
     } else {
         __syncthreads();
-        GlobalState S{g_cur, g_oth, Ny};
+        GlobalState S{g_cur, g_oth, Ny, &sw.term[0][0][0]};
         run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me);
         fin = S.src;
     }

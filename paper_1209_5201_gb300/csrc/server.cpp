@@ -219,9 +219,26 @@ struct ServerImpl {
             for (int kk = 0; kk < -L.ey[a]; ++kk) { d.term_a[0][nb] = (signed char)a; d.term_row[0][nb] = (signed char)kk; ++nb; }
             for (int kk = 0; kk < L.ey[a]; ++kk) { d.term_a[1][nt] = (signed char)a; d.term_row[1][nt] = (signed char)kk; ++nt; }
         }
-        if (nb != nt || nb > 32) std::abort();   // lattices are symmetric, <= 26 terms
+        if (nb != nt || nb >= 32) std::abort();  // lattices are symmetric, <= 26 terms
         d.nterm = nb;
         fill_consts(d.k, L, p, 1);
+        // the wall warp sums the terms' deviations d = f - w and adds their
+        // weights once (wterm); it then forms M_in g^w_a / D_w - w_a for the
+        // outgoing velocities of its wall (e_y > 0 bottom, e_y < 0 top)
+        int no[2] = {0, 0};
+        for (int a = 0; a < L.Q; ++a) {
+            for (int kk = 0; kk < -L.ey[a]; ++kk) d.wterm[0] += (double)d.k.w[a];
+            for (int kk = 0; kk < L.ey[a]; ++kk) d.wterm[1] += (double)d.k.w[a];
+            const int wl = L.ey[a] > 0 ? 0 : (L.ey[a] < 0 ? 1 : -1);
+            if (wl < 0) continue;
+            if (no[wl] >= kMaxOut || !(d.k.wcoef[wl][a] > 0.0)) std::abort();
+            d.out_a[wl][no[wl]] = (signed char)a;
+            d.out_c[wl][no[wl]] = d.k.wcoef[wl][a];
+            d.out_w[wl][no[wl]] = (double)d.k.w[a];
+            ++no[wl];
+        }
+        if (no[0] != no[1] || no[0] < 1) std::abort();
+        d.nout = no[0];
         // the kernels reject anything else; the host must never produce it
         if (!(d.Ny >= 6 && d.Ny <= kMaxNy && d.f_off >= 0 &&
               d.f_off + 2LL * d.Q * d.Ny + 2LL * d.Ny <= pool_elems &&
