@@ -341,9 +341,11 @@ typedef struct lbm_server_cfg {
     size_t mem_budget_bytes; /* device pool for the requests' f-arrays        */
     int32_t max_slots;       /* CTAs the running requests may occupy at once
                                 (1..4096): a column of Ny rows runs on a
-                                cluster of CL = 1, 2, 4 or 8 CTAs of 256
+                                cluster of CL = 1, 2, 4, 8 or 16 CTAs of 256
                                 threads, the smallest CL with ceil(Ny / CL) <=
-                                cluster_rows (8 if none), at most max_slots  */
+                                cluster_rows (the largest if none), at most
+                                max_slots; 16-CTA clusters only where the
+                                device schedules them (else at most 8)       */
     int32_t chunk_steps;     /* steps per chunk launch                         */
     int32_t precision;       /* LBM_FP32                                       */
     int32_t use_graph;       /* replay the chunk launch as a CUDA graph        */
@@ -359,6 +361,10 @@ typedef struct lbm_server_metrics {
     double solves_per_s;     /* completed / (last completion - first submit)  */
     double mean_occupancy;   /* mean fraction of max_slots busy per chunk     */
     size_t pool_bytes, pool_used_bytes;
+    int64_t promoted;        /* running requests moved to a larger cluster once
+                                CTAs were spare (results unchanged)           */
+    int64_t demoted;         /* ... to a smaller one to make room for queued
+                                requests (results unchanged)                  */
 } lbm_server_metrics;
 
 typedef struct lbm_server lbm_server;

@@ -17,6 +17,12 @@ constexpr int kSlotCancelled = 6;         // set by the host; the kernel skips t
 
 // Most velocities leaving one wall (e.n > 0): 15 for D2Q37.
 constexpr int kMaxOut = 16;
+// Most chunks one launch runs for one slot.
+constexpr int kMaxSub = 16;
+// Chunks per launch of a slot on a cluster of cl CTAs: about the factor by
+// which the cluster shortens a step of a tall column, conservatively, so that
+// a cluster slot is rarely the one a launch waits for.
+inline int batch_sub_chunks(int cl) { return cl <= 2 ? 1 : cl / 2; }
 
 struct SlotDesc {
     int Q;                    // 17, 25 or 37 (0: idle slot)
@@ -24,7 +30,9 @@ struct SlotDesc {
     int cur;                  // buffer holding the current state (0 / 1)
     int check_every;          // residual every check_every chunks
     int chunk_steps;          // steps this slot runs per chunk launch
-    int cl;                   // CTAs of the slot's cluster: 1, 2, 4 or 8
+    int cl;                   // CTAs of the slot's cluster: 1, 2, 4, 8 or 16
+    int sub;                  // chunks per launch (a cluster runs several, so
+                              // that it keeps pace with one-CTA slots' launches)
     long long f_off;          // element offset of buffer 0 in the pool
     long long prev_off;       // element offset of the previous-check u_x, T
     double tol;               // target of the extrapolated distance to steady state
@@ -58,8 +66,8 @@ struct SlotStatus {
 };
 
 // Cluster sizes of the slot classes.
-constexpr int kBatchClasses = 4;
-constexpr int kBatchClassCL[kBatchClasses] = {1, 2, 4, 8};
+constexpr int kBatchClasses = 5;
+constexpr int kBatchClassCL[kBatchClasses] = {1, 2, 4, 8, 16};
 // Rows of the residual's partial sums (one warp each) and their most per slot.
 constexpr int kResidualChunk = 32;
 constexpr int kMaxResidualChunks = 8192 / kResidualChunk;
@@ -76,19 +84,22 @@ __host__ __device__ inline int batch_rows_per_cta(int Ny, int CL) {
 __host__ __device__ inline bool batch_split_ok(int Ny, int CL) {
     if (CL == 1) return Ny >= 6;
     const int R = batch_rows_per_cta(Ny, CL);
-    return (CL == 2 || CL == 4 || CL == 8) && (CL - 1) * R + 32 <= Ny;
+    return (CL == 2 || CL == 4 || CL == 8 || CL == 16) && (CL - 1) * R + 32 <= Ny;
 }
 // The largest cluster a column of Ny rows may use: the smallest CL whose CTAs
-// get at most `rows` rows each (8 if none does), reduced until the split is
-// usable and fits the CTA budget.
-inline int batch_cluster_size(int Ny, int rows, int max_ctas) {
+// get at most `rows` rows each (max_cl if none does), reduced until the split
+// is usable and fits the CTA budget.
+inline int batch_cluster_size(int Ny, int rows, int max_ctas, int max_cl) {
     int cl = 1;
-    while (cl < 8 && batch_rows_per_cta(Ny, cl) > rows) cl *= 2;
+    while (cl < max_cl && batch_rows_per_cta(Ny, cl) > rows) cl *= 2;
     while (cl > 1 && (cl > max_ctas || !batch_split_ok(Ny, cl))) cl /= 2;
     return cl;
 }
 
 int preload_batch_kernels();
+// 16 when the device can schedule a 16-CTA cluster of the chunk kernel (a
+// non-portable size), else 8.
+int batch_max_cluster();
 // dbg: 8 device ints; dbg[0] != 0 records the first invalid descriptor or
 // read-out offset a kernel met (and skipped).
 // One chunk of the slots [slot0, slot0 + nlanes), each on a cluster of CL

@@ -27,6 +27,7 @@ __device__ __forceinline__ bool desc_ok(const SlotDesc &d, long long pool_elems,
         mirror_ok = mirror_ok && d.k.mirror[a] >= 0 && d.k.mirror[a] < d.Q;
     const bool cl_ok = batch_split_ok(d.Ny, d.cl);
     const bool ok = q_ok && terms_ok && mirror_ok && cl_ok && d.Ny >= 6 && d.Ny <= 8192 &&
+                    d.sub >= 1 && d.sub <= kMaxSub &&
                     d.f_off >= 0 &&
                     d.f_off + need <= pool_elems && d.prev_off == d.f_off + 2LL * d.Q * d.Ny &&
                     (d.cur == 0 || d.cur == 1) && d.chunk_steps >= 1 && d.check_every >= 1;
@@ -61,25 +62,31 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
     __shared__ SlotDesc sd;
     __shared__ BatchWallShared sw;
     __shared__ int s_chunks;
+    __shared__ long long s_steps;
     extern __shared__ __align__(16) float batch_sm[];
     const int slot = slot0 + blockIdx.x / CL;
     const int rank = CL == 1 ? 0 : (int)cluster_rank();
     load_desc(desc + slot, &sd);
-    if (threadIdx.x == 0) s_chunks = status[slot].chunks + 1;
+    if (threadIdx.x == 0) {
+        s_chunks = status[slot].chunks;
+        s_steps = status[slot].steps;
+    }
     __syncthreads();
     if (sd.Q == 0 || status[slot].state != kSlotRunning) return;
     if (!desc_ok(sd, pool_elems, slot, 1, dbg) || sd.cl != CL) return;
     double *pp = part + (long long)slot * (6 * kMaxResidualChunks);
+    int done = 0;
     switch (sd.Q) {
-    case 17: batch_slot<17>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp, batch_sm); break;
-    case 25: batch_slot<25>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp, batch_sm); break;
-    case 37: batch_slot<37>(sd, pool, status + slot, sw, rank, CL, s_chunks, pp, batch_sm); break;
+    case 17: done = batch_slot<17>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, pp, batch_sm); break;
+    case 25: done = batch_slot<25>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, pp, batch_sm); break;
+    case 37: done = batch_slot<37>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, pp, batch_sm); break;
     default: break;
     }
     // the global-memory path leaves the state in the other buffer after an odd
-    // chunk; the shared-memory path writes it back where it came from
+    // number of steps; the shared-memory path writes it back where it came from
     const bool smem = batch_uses_smem(sd.Ny, CL);
-    if (!smem && rank == 0 && threadIdx.x == 0) desc[slot].cur = (sd.cur + sd.chunk_steps) & 1;
+    if (!smem && rank == 0 && threadIdx.x == 0)
+        desc[slot].cur = (int)((sd.cur + (long long)done * sd.chunk_steps) & 1);
 }
 
 // Rest equilibrium f~* = rho0 w_a of newly admitted slots, stored as the
@@ -177,10 +184,33 @@ int preload_batch_kernels() {
     cudaFuncAttributes a;
     cudaError_t e = cudaFuncSetAttribute(k_batch_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_chunk, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_batch_chunk);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_batch_init);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_batch_macros);
     return (int)e;
+}
+
+int batch_max_cluster() {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, (const void *)k_batch_chunk, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();                    // not an error of the caller's
+        return 8;
+    }
+    return n >= 1 ? 16 : 8;
 }
 
 int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, float *pool,
@@ -192,7 +222,7 @@ int launch_batch_chunk(cudaStream_t st, SlotDesc *desc, SlotStatus *status, floa
                                                                  1, pool_elems, dbg);
         return (int)cudaGetLastError();
     }
-    if (CL != 2 && CL != 4 && CL != 8) return (int)cudaErrorInvalidValue;
+    if (CL != 2 && CL != 4 && CL != 8 && CL != 16) return (int)cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nlanes * CL));
     cfg.blockDim = dim3(kBatchThreads);

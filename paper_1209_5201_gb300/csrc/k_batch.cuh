@@ -4,8 +4,8 @@
 // FP64 steady-state residual per slot.
 //
 // With Nx = 1 the pull of Eq. (5) only shifts in y: f_in(j, a) =
-// f~*(j - e_ay, a).  A slot runs on a cluster of CL CTAs (CL = 1, 2, 4 or 8,
-// fixed by its height): CTA `rank` owns rows [rank R, rank R + R), R =
+// f~*(j - e_ay, a).  A slot runs on a cluster of CL CTAs (CL = 1, 2, 4, 8 or
+// 16, fixed by its height): CTA `rank` owns rows [rank R, rank R + R), R =
 // ceil(Ny / CL), and a cluster barrier with release / acquire semantics
 // separates the steps.  When R <= kSmemRows the CTA keeps its rows' two state
 // buffers in shared memory for the whole chunk (loaded from the pool at the
@@ -376,15 +376,19 @@ __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWall
     }
 }
 
-// One chunk of one slot on CTA `rank` of its CL-CTA cluster.  `chunks` is the
-// slot's chunk counter after this chunk (read by every CTA before the first
-// barrier); `part` the slot's per-chunk FP64 partial sums of the residual; `sm` the
-// CTA's kSmemBytes of dynamic shared memory (used when R <= kSmemRows).
+// Up to d.sub chunks of one slot on CTA `rank` of its CL-CTA cluster
+// (fewer when the slot stops: converged, stagnated, non-finite or at
+// max_steps); returns the chunks run.  chunks0 / steps0 are the slot's
+// counters before the launch (read by every CTA before the first barrier);
+// `part` the slot's per-chunk FP64 partial sums of the residual; `sm` the
+// CTA's kSmemBytes of dynamic shared memory (used when R <= kSmemRows).  A
+// residual check follows every check_every-th chunk of the slot's count, so
+// the checks fall on the same steps whatever the number of chunks per launch.
 template <int Q>
-__device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict__ pool,
-                                           SlotStatus *__restrict__ st, BatchWallShared &sw,
-                                           int rank, int CL, int chunks,
-                                           double *__restrict__ part, float *sm) {
+__device__ __forceinline__ int batch_slot(const SlotDesc &d, float *__restrict__ pool,
+                                          SlotStatus *__restrict__ st, BatchWallShared &sw,
+                                          int rank, int CL, int chunks0, long long steps0,
+                                          double *__restrict__ part, float *sm) {
     using L = Lat<Q>;
     const int chunk = d.chunk_steps;
     const KConsts<float> &k = d.k;
@@ -407,12 +411,119 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         nt = min(32, span);
     }
     const int mb = j0 + nb, me = j1 - nt;
+    const bool smem = batch_uses_smem(Ny, CL);
+
+    // Residual over the slot's cells (Eq. (3) moments of the state `fin`
+    // after chunk ck).  Partial sums per 32-row chunk (one warp each, fixed
+    // lane order) in global memory, then one warp of CTA 0 adds the chunks in
+    // a fixed order: the result does not depend on how the rows were split
+    // across CTAs.  Returns whether the slot keeps running (the same answer
+    // in every thread of the cluster).
+    auto check = [&](const float *fin, int ck, long long steps_k) -> bool {
+        float *prev_u = (float *)(pool + d.prev_off);
+        float *prev_T = prev_u + Ny;
+        const double r = (double)k.r;
+        const int nwarps = nth >> 5;
+        for (int c = j0 / kResidualChunk + warp; c * kResidualChunk < j1; c += nwarps) {
+            const int j = c * kResidualChunk + lane;
+            double acc[6] = {0, 0, 0, 0, 0, 0};
+            if (j < j1) {
+                // deviations d = f - w: rho = 1 + sum d, sum e w = 0, sum e^2 w = e2w
+                double s0 = 0, sx = 0, sy = 0, se = (double)k.e2w;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    const double fa = smem ? (double)fin[(j - j0) * Q + a]
+                                           : (double)__ldcg(fin + (long long)a * Ny + j);
+                    s0 += fa;
+                    sx += L::ex(a) * fa;
+                    sy += L::ey(a) * fa;
+                    se += L::e2(a) * fa;
+                }
+                const double rh = 1.0 + s0;
+                const double u = r * sx / rh, v = r * sy / rh;
+                const double T = ((double)k.r2 * se - rh * (u * u + v * v)) / (2.0 * rh);
+                const double du = u - prev_u[j], dT = T - prev_T[j];
+                acc[0] = du * du;
+                acc[1] = u * u;
+                acc[2] = dT * dT;
+                acc[3] = T * T;
+                acc[4] = rh;
+                acc[5] = (!isfinite(u) || !isfinite(T)) ? 1.0 : 0.0;
+                prev_u[j] = (float)u;
+                prev_T[j] = (float)T;
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+            if (lane == 0)
+                for (int i = 0; i < 6; ++i) part[c * 6 + i] = acc[i];
+        }
+        slot_barrier(CL);                      // every chunk's partials written
+        if (rank == 0) {
+            double tot[6] = {0, 0, 0, 0, 0, 0};
+            if (warp == 0) {
+                const int nch = (Ny + kResidualChunk - 1) / kResidualChunk;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    double v = 0.0;
+                    for (int c = lane; c < nch; c += 32) v += part[c * 6 + i];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                    tot[i] = v;
+                }
+            }
+            if (tid == 0) {
+                SlotStatus &s = *st;
+                s.chunks = ck;
+                s.steps = steps_k;
+                s.checks += 1;
+                s.mass = tot[4];
+                double res = sqrt(tot[0]) / fmax(sqrt(tot[1]), 1e-30);
+                if (k.thermal) res = fmax(res, sqrt(tot[2]) / fmax(sqrt(tot[3]), 1e-30));
+                // geometric extrapolation of the remaining change: with a
+                // per-check contraction q = res / res_prev < 1, the distance
+                // to the steady state is about res q / (1 - q); q from the
+                // last two checks, the slower of the two contractions
+                const double q1 = s.res > 0 ? res / s.res : 1.0;
+                const double q0 = s.res_prev > 0 ? s.res / s.res_prev : 1.0;
+                const double q = fmax(q1, q0);
+                const double prev_est = s.err_est;
+                s.res_prev = s.res;
+                s.res = res;
+                s.err_est = (q < 0.999) ? res * q / (1.0 - q) : 1e30;
+                if (res < s.best_res) { s.best_res = res; s.since_best = 0; }
+                else s.since_best += 1;
+                if (tot[5] > 0 || !isfinite(res)) s.state = kSlotNonFinite;
+                else if (s.checks >= 4 && s.err_est <= d.tol && prev_est <= d.tol) s.state = kSlotConverged;
+                // the residual stopped improving far below tol: the column
+                // has reached the FP32 round-off floor (the check interval
+                // makes the slowest mode's decay visible, so a flat, tiny
+                // residual is noise, not slow convergence)
+                else if (s.since_best >= 8 && s.best_res <= 0.05 * d.tol) s.state = kSlotConverged;
+                else if (s.since_best >= 50) s.state = kSlotStagnated;
+                else if (s.steps >= d.max_steps) s.state = kSlotMaxSteps;
+            }
+        }
+        slot_barrier(CL);                      // the new state visible to the cluster
+        return __ldcg(&st->state) == kSlotRunning;
+    };
+    // after sub-chunk kk of this launch: a check when the slot's chunk count
+    // calls for one, else the counters (and the max_steps stop)
+    auto after_chunk = [&](const float *fin, int kk) -> bool {
+        const int ck = chunks0 + kk;
+        const long long steps_k = steps0 + (long long)kk * chunk;
+        if (ck % d.check_every == 0) return check(fin, ck, steps_k);
+        if (rank == 0 && tid == 0) {
+            st->chunks = ck;
+            st->steps = steps_k;
+            if (steps_k >= d.max_steps) st->state = kSlotMaxSteps;
+        }
+        return steps_k < d.max_steps;
+    };
 
     float *g_cur = pool + d.f_off + (d.cur ? (long long)Q * Ny : 0);
     float *g_oth = pool + d.f_off + (d.cur ? 0 : (long long)Q * Ny);
-    const bool smem = batch_uses_smem(Ny, CL);
-    const float *fin;                          // the state after the chunk
     if (tid < 2) sw.acc[tid] = (float)k.accom[tid];
+    int done = 0;
     if (smem) {
         // own rows into buffer 0, transposed to rows of Q populations
         for (int i = tid; i < Q * span; i += nth) {
@@ -424,9 +535,13 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
         if (rank > 0) S.lo = map_rank(base, rank - 1);
         if (rank < CL - 1) S.hi = map_rank(base, rank + 1);
         slot_barrier(CL);                      // every CTA loaded before any neighbour reads
-        run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me);
-        fin = sm + S.b * Q * R;
+        while (done < d.sub) {
+            run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me);
+            ++done;
+            if (!after_chunk(sm + S.b * Q * R, done)) break;
+        }
         // write the final state back to the pool buffer it came from
+        const float *fin = sm + S.b * Q * R;
         for (int i = tid; i < Q * span; i += nth) {
             const int a = i / span, r = i - a * span;
             g_cur[(long long)a * Ny + j0 + r] = fin[r * Q + a];
@@ -434,104 +549,13 @@ __device__ __forceinline__ void batch_slot(const SlotDesc &d, float *__restrict_
     } else {
         __syncthreads();
         GlobalState S{g_cur, g_oth, Ny, &sw.term[0][0][0]};
-        run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me);
-        fin = S.src;
-    }
-
-    if (chunks % d.check_every != 0) {
-        if (rank == 0 && tid == 0) {
-            st->chunks = chunks;
-            st->steps += chunk;
-            if (st->steps >= d.max_steps) st->state = kSlotMaxSteps;
-        }
-        return;
-    }
-
-    // Residual over the slot's cells (Eq. (3) moments of the current state).
-    // Partial sums per 32-row chunk (one warp each, fixed lane order) in
-    // global memory, then one warp of CTA 0 adds the chunks in a fixed order:
-    // the result does not depend on how the rows were split across CTAs.
-    float *prev_u = (float *)(pool + d.prev_off);
-    float *prev_T = prev_u + Ny;
-    const double r = (double)k.r;
-    const int nwarps = nth >> 5;
-    for (int c = j0 / kResidualChunk + warp; c * kResidualChunk < j1; c += nwarps) {
-        const int j = c * kResidualChunk + lane;
-        double acc[6] = {0, 0, 0, 0, 0, 0};
-        if (j < j1) {
-            // deviations d = f - w: rho = 1 + sum d, sum e w = 0, sum e^2 w = e2w
-            double s0 = 0, sx = 0, sy = 0, se = (double)k.e2w;
-#pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                const double fa = smem ? (double)fin[(j - j0) * Q + a]
-                                       : (double)__ldcg(fin + (long long)a * Ny + j);
-                s0 += fa;
-                sx += L::ex(a) * fa;
-                sy += L::ey(a) * fa;
-                se += L::e2(a) * fa;
-            }
-            const double rh = 1.0 + s0;
-            const double u = r * sx / rh, v = r * sy / rh;
-            const double T = ((double)k.r2 * se - rh * (u * u + v * v)) / (2.0 * rh);
-            const double du = u - prev_u[j], dT = T - prev_T[j];
-            acc[0] = du * du;
-            acc[1] = u * u;
-            acc[2] = dT * dT;
-            acc[3] = T * T;
-            acc[4] = rh;
-            acc[5] = (!isfinite(u) || !isfinite(T)) ? 1.0 : 0.0;
-            prev_u[j] = (float)u;
-            prev_T[j] = (float)T;
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-            for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
-        if (lane == 0)
-            for (int i = 0; i < 6; ++i) part[c * 6 + i] = acc[i];
-    }
-    slot_barrier(CL);                          // every chunk's partials written
-    if (rank != 0) return;
-    double tot[6] = {0, 0, 0, 0, 0, 0};
-    if (warp == 0) {
-        const int nch = (Ny + kResidualChunk - 1) / kResidualChunk;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            double v = 0.0;
-            for (int c = lane; c < nch; c += 32) v += part[c * 6 + i];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            tot[i] = v;
+        while (done < d.sub) {
+            run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me);
+            ++done;
+            if (!after_chunk(S.src, done)) break;
         }
     }
-    if (tid == 0) {
-        SlotStatus &s = *st;
-        s.chunks = chunks;
-        s.steps += chunk;
-        s.checks += 1;
-        s.mass = tot[4];
-        double res = sqrt(tot[0]) / fmax(sqrt(tot[1]), 1e-30);
-        if (k.thermal) res = fmax(res, sqrt(tot[2]) / fmax(sqrt(tot[3]), 1e-30));
-        // geometric extrapolation of the remaining change: with a per-check
-        // contraction q = res / res_prev < 1, the distance to the steady state
-        // is about res q / (1 - q); q from the last two checks, the slower of
-        // the two contractions
-        const double q1 = s.res > 0 ? res / s.res : 1.0;
-        const double q0 = s.res_prev > 0 ? s.res / s.res_prev : 1.0;
-        const double q = fmax(q1, q0);
-        const double prev_est = s.err_est;
-        s.res_prev = s.res;
-        s.res = res;
-        s.err_est = (q < 0.999) ? res * q / (1.0 - q) : 1e30;
-        if (res < s.best_res) { s.best_res = res; s.since_best = 0; }
-        else s.since_best += 1;
-        if (tot[5] > 0 || !isfinite(res)) s.state = kSlotNonFinite;
-        else if (s.checks >= 4 && s.err_est <= d.tol && prev_est <= d.tol) s.state = kSlotConverged;
-        // the residual stopped improving far below tol: the column has reached
-        // the FP32 round-off floor (the check interval makes the slowest mode's
-        // decay visible, so a flat, tiny residual is noise, not slow convergence)
-        else if (s.since_best >= 8 && s.best_res <= 0.05 * d.tol) s.state = kSlotConverged;
-        else if (s.since_best >= 50) s.state = kSlotStagnated;
-        else if (s.steps >= d.max_steps) s.state = kSlotMaxSteps;
-    }
+    return done;
 }
 
 }  // namespace lbm

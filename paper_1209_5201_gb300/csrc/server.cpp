@@ -4,8 +4,8 @@
 // Requests (one single-column Couette instance each: lattice, height, Kn,
 // wall speeds and temperatures, tolerance) queue on the host.  A worker
 // thread owns the GPU side: a device memory pool of the configured budget,
-// a slot table (SlotDesc / SlotStatus) in four classes by cluster size (a
-// column runs on 1, 2, 4 or 8 CTAs, by height) and the chunk kernel.  Every
+// a slot table (SlotDesc / SlotStatus) in five classes by cluster size (a
+// column runs on 1, 2, 4, 8 or 16 CTAs, by height) and the chunk kernel.  Every
 // loop it
 //   1. admits queued requests into idle slots of their class while the CTA
 //      budget (max_slots) and the pool (first-fit allocator) have room for
@@ -89,6 +89,7 @@ struct ServerImpl {
     // slot classes: slots [cls_base[c], cls_base[c] + cls_cap[c]) run on
     // clusters of kBatchClassCL[c] CTAs, each class launched on its own stream
     int cls_base[kBatchClasses] = {}, cls_cap[kBatchClasses] = {};
+    int max_cl = 8;            // largest cluster the device schedules (8 or 16)
     cudaStream_t side[kBatchClasses] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kBatchClasses] = {};
     int *d_idx = nullptr;                    // slot lists for init / read-out
@@ -120,6 +121,7 @@ struct ServerImpl {
     int64_t submitted = 0, completed = 0;
     int running = 0;
     int used_ctas = 0;                       // CTAs of the running slots (<= max_slots)
+    int64_t promoted = 0, demoted = 0;       // running requests moved to a larger / smaller cluster
     int64_t chunks = 0;
     double occupancy_sum = 0;
     double t_first_submit = -1, t_last_done = 0;
@@ -190,6 +192,7 @@ struct ServerImpl {
         d.Ny = r.Ny;
         d.cur = 0;
         d.cl = cl;
+        d.sub = batch_sub_chunks(cl);
         // Steps per chunk launch: cheaper slots run more steps, so that every
         // CTA of a launch takes about as long (cfg.chunk_steps x 333 cost
         // units); the cost model is the velocity count times the rows per
@@ -285,7 +288,6 @@ struct ServerImpl {
         return LBM_ECUDA;
     }
 
-    // a free slot of the class that runs a column of Ny rows, or -1
     // Whether a request may be split over a cluster, with its cluster size and
     // estimated work.  A split column moves fewer lattice updates per SM than
     // one CTA (a barrier per step across the cluster), so it is only worth its
@@ -295,15 +297,24 @@ struct ServerImpl {
     // cell update is the same arithmetic on the same values, chunk lengths and
     // checks ignore the cluster, and the residual is summed over 32-row chunks
     // in a fixed order.
-    bool long_split(const lbm_request &r, int &cl, double &work) const {
-        cl = batch_cluster_size(r.Ny, cfg.cluster_rows, cfg.max_slots);
-        if (cl == 1) return false;
+    // Steps to steady state: 14 e-folding times of the slowest mode, the
+    // viscous decay of the shear profile (0.127 Ny r / Kn steps) plus, at
+    // large Kn, about one crossing of the channel at the thermal speed
+    // (r Ny steps; measured: 1.1e5 steps for 4019 rows at Kn 0.98).
+    double est_steps(const lbm_request &r) const {
         const LatticeHost &L = lattice(r.lattice);
-        const double efold = r.tau > 0 ? r.Ny / (9.8696 * r.tau * L.r) : 0.127 * r.Ny * L.r / r.Kn;
-        work = 14.0 * efold * std::ceil(r.Ny / 256.0);
+        const double efold = r.tau > 0 ? r.Ny / (9.8696 * r.tau * L.r)
+                                       : 0.127 * r.Ny * L.r / r.Kn + 1.2 * r.Ny * L.r;
+        return 14.0 * efold;
+    }
+    bool long_split(const lbm_request &r, int &cl, double &work) const {
+        cl = batch_cluster_size(r.Ny, cfg.cluster_rows, cfg.max_slots, max_cl);
+        if (cl == 1) return false;
+        work = est_steps(r) * std::ceil(r.Ny / 256.0);
         return work >= kLongRowSteps;
     }
 
+    // a free slot of the class of clusters of cl CTAs, or -1
     int free_slot(int cl) const {
         int c = 0;
         while (c + 1 < kBatchClasses && kBatchClassCL[c] != cl) ++c;
@@ -329,9 +340,108 @@ struct ServerImpl {
         return e;
     }
 
+    // Elastic clusters.  A running request's slot can move to a class of
+    // another cluster size between chunks: its state stays where it is in the
+    // pool (a slot of any cluster size reads the same [Q][Ny] buffers), only
+    // the descriptor and the status move, so the results are those of an
+    // unmoved run, bit for bit.  When queued requests wait for CTAs
+    // (short_ctas > 0), clusters shrink, least remaining work first, until
+    // they fit; otherwise CTAs beyond one per queued request and a small
+    // reserve for arrivals go to the long requests with the most remaining
+    // work, which would otherwise keep the size they were admitted with (one
+    // CTA on a full GPU) and set the latency tail.
+    double remaining(int s) const {
+        // remaining row-steps on one CTA; a request past its estimate keeps a
+        // quarter of it
+        const double est = est_steps(slots[s].req);
+        return std::max(est - (double)h_status[s].steps, 0.25 * est) *
+               std::ceil(slots[s].req.Ny / 256.0);
+    }
+    cudaError_t rebalance(long long spare, int short_ctas, const std::vector<int> &fresh) {
+        struct Cand { double rem; int s; };
+        struct Move { int from, to, cl; };
+        std::vector<Cand> cand;
+        std::vector<Move> moves;
+        auto movable = [&](int s) {
+            return slots[s].busy && h_status[s].state == kSlotRunning &&
+                   std::find(fresh.begin(), fresh.end(), s) == fresh.end();
+        };
+        if (short_ctas > 0) {
+            for (int s = 0; s < (int)slots.size(); ++s)
+                if (movable(s) && h_desc[s].cl > 1) cand.push_back({remaining(s), s});
+            std::sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.rem < y.rem; });
+            int freed = 0;
+            for (const Cand &c : cand) {
+                if (freed >= short_ctas) break;
+                const int cur = h_desc[c.s].cl, Ny = slots[c.s].req.Ny;
+                int cl = cur / 2;
+                while (cl > 1 && (freed + cur - cl < short_ctas || !batch_split_ok(Ny, cl))) cl /= 2;
+                const int to = free_slot(cl);
+                if (to < 0) continue;
+                slots[to].busy = true;               // taken for this move
+                freed += cur - cl;
+                moves.push_back({c.s, to, cl});
+            }
+        } else {
+            spare -= cfg.max_slots / 64;
+            if (spare <= 0) return cudaSuccess;
+            for (int s = 0; s < (int)slots.size(); ++s) {
+                if (!movable(s)) continue;
+                int cl;
+                double work;
+                if (!long_split(slots[s].req, cl, work) || cl <= h_desc[s].cl) continue;
+                const double rem = remaining(s);
+                if (rem >= kLongRowSteps) cand.push_back({rem, s});
+            }
+            std::sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.rem > y.rem; });
+            for (const Cand &c : cand) {
+                const int cur = h_desc[c.s].cl, Ny = slots[c.s].req.Ny;
+                int cl = batch_cluster_size(Ny, cfg.cluster_rows, cfg.max_slots, max_cl);
+                int to = -1;
+                for (; cl > cur; cl /= 2) {
+                    if (cl - cur > spare || !batch_split_ok(Ny, cl)) continue;
+                    if ((to = free_slot(cl)) >= 0) break;
+                }
+                if (to < 0) continue;
+                slots[to].busy = true;               // taken for this move
+                spare -= cl - cur;
+                moves.push_back({c.s, to, cl});
+                if (spare <= 0) break;
+            }
+        }
+        if (moves.empty()) return cudaSuccess;
+        // the buffer index of a slot on the global-memory path lives on the device
+        cudaError_t e = cudaSuccess;
+        for (const Move &m : moves)
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&h_desc[m.from].cur, &d_desc[m.from].cur, sizeof(int),
+                                    cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        std::unique_lock<std::mutex> lk(mu);         // the counters are read by stats
+        for (const Move &m : moves) {
+            const int from_cl = h_desc[m.from].cl;
+            h_desc[m.to] = h_desc[m.from];
+            h_desc[m.to].cl = m.cl;
+            h_desc[m.to].sub = batch_sub_chunks(m.cl);
+            h_status[m.to] = h_status[m.from];
+            slots[m.to] = slots[m.from];
+            used_ctas += m.cl - from_cl;
+            slots[m.from].busy = false;
+            h_desc[m.from].Q = 0;
+            h_status[m.from].state = kSlotIdle;
+            if (m.cl > from_cl) ++promoted;
+            else ++demoted;
+            if (e == cudaSuccess) e = upload_slot(m.to);
+            if (e == cudaSuccess) e = upload_slot(m.from);
+        }
+        return e;
+    }
+
     // one loop of the worker; returns false when there is nothing to do
     int loop_once(bool &idle) {
         std::vector<int> admitted, stopped;
+        long long spare = 0;
+        int short_ctas = 0;                          // CTAs the budget lacked for queued requests
         {
             std::unique_lock<std::mutex> lk(mu);
             // running requests cancelled since the last chunk: marked stopped
@@ -374,8 +484,10 @@ struct ServerImpl {
             for (auto it = queue.begin(); it != queue.end() && scanned < 64; ++scanned) {
                 const auto sp = split.find(it->id);
                 const int cl = sp == split.end() ? 1 : sp->second;
-                const int s = used_ctas + cl + reserve <= cfg.max_slots ? free_slot(cl) : -1;
+                const bool fits = used_ctas + cl + reserve <= cfg.max_slots;
+                const int s = fits ? free_slot(cl) : -1;
                 if (s < 0) {
+                    if (!fits) short_ctas += 1;      // one CTA is all it needs
                     if (reserve == 0) reserve = cl;
                     ++it;
                     continue;
@@ -390,6 +502,7 @@ struct ServerImpl {
                 used_ctas += cl;
             }
             idle = running == 0;
+            spare = (long long)cfg.max_slots - used_ctas - (long long)queue.size();
         }
         cudaError_t e;
         for (int s : stopped)
@@ -397,6 +510,7 @@ struct ServerImpl {
                                      cudaMemcpyHostToDevice, stream)))
                 return fail("upload cancelled status", e);
         if (idle) return LBM_OK;
+        if ((e = rebalance(spare, short_ctas, admitted))) return fail("rebalance", e);
         if (!admitted.empty()) {
             // only the admitted entries: running slots' buffer index lives on the device
             for (int s : admitted)
@@ -591,10 +705,18 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
         for (int i = 0; i < 4; ++i)
             if (lattice_build(kinds[i], S.lat[i])) { delete h; set_error("lattice build"); return LBM_EINVAL; }
         // slot classes: max_slots / CL slots of each cluster size, so that any
-        // class alone can fill the CTA budget
+        // class alone can fill the CTA budget; none for clusters larger than
+        // the budget or than the device schedules
+        if (int rc = preload_batch_kernels()) {
+            delete h;
+            set_error(std::string("batch kernels: ") + cudaGetErrorString((cudaError_t)rc));
+            return LBM_ECUDA;
+        }
+        S.max_cl = batch_max_cluster();
         int ns = 0;
         for (int c = 0; c < kBatchClasses; ++c) {
-            S.cls_cap[c] = std::max(1, cfg->max_slots / kBatchClassCL[c]);
+            const int cl = kBatchClassCL[c];
+            S.cls_cap[c] = cl > S.max_cl || cl > cfg->max_slots ? 0 : cfg->max_slots / cl;
             S.cls_base[c] = ns;
             ns += S.cls_cap[c];
         }
@@ -631,7 +753,6 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
             std::memset(S.h_dbg, 0, sizeof(int) * 8);
             ck(cudaStreamSynchronize(S.stream));
         }
-        if (e == cudaSuccess) ck((cudaError_t)preload_batch_kernels());
         if (e == cudaSuccess && cfg->use_graph) {
             // capture: chunk kernels of every class, then the status read-back
             cudaStream_t cs;
@@ -768,6 +889,8 @@ int lbm_server_stats(lbm_server *h, lbm_server_metrics *st) {
     st->pool_bytes = (size_t)S.pool_elems * sizeof(float);
     st->pool_used_bytes = (size_t)S.used_elems * sizeof(float);
     st->mean_occupancy = S.chunks ? S.occupancy_sum / (S.chunks * (double)S.cfg.max_slots) : 0.0;
+    st->promoted = S.promoted;
+    st->demoted = S.demoted;
     if (!S.latencies.empty()) {
         std::vector<double> l = S.latencies;
         std::sort(l.begin(), l.end());

@@ -73,7 +73,8 @@ class lbm_server_metrics(C.Structure):
                 ("queued", C.c_int64), ("chunks", C.c_int64), ("p50_latency_s", C.c_double),
                 ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double),
                 ("solves_per_s", C.c_double), ("mean_occupancy", C.c_double),
-                ("pool_bytes", C.c_size_t), ("pool_used_bytes", C.c_size_t)]
+                ("pool_bytes", C.c_size_t), ("pool_used_bytes", C.c_size_t),
+                ("promoted", C.c_int64), ("demoted", C.c_int64)]
 
 
 _lib = None

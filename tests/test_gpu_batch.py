@@ -245,11 +245,12 @@ def test_graph_and_plain_launches_agree(lbm):
         assert all(np.array_equal(u, v) for u, v in zip(x[1:], y[1:])), it
 
 
-@pytest.mark.parametrize("Ny", [257, 300, 511, 513, 1023, 1025, 1100, 2047, 2049, 4096, 8192])
+@pytest.mark.parametrize("Ny", [257, 300, 511, 513, 1023, 1025, 1100, 2047, 2049, 2431, 2432,
+                                2500, 4095, 4096, 4097, 8192])
 def test_split_at_class_boundaries(lbm, Ny):
     # heights around every cluster-size boundary, up to the largest: the rows
-    # split over 2, 4 or 8 CTAs (shared memory or global memory) step exactly
-    # like one CTA holding them all
+    # split over 2, 4, 8 or 16 CTAs (shared memory or global memory) step
+    # exactly like one CTA holding them all
     item = [("D2Q17", Ny, 0.002, 0.1, 1.0)]
     split = fixed_steps(lbm, item, 300, max_slots=16)[0]
     whole = fixed_steps(lbm, item, 300, max_slots=16, cluster_rows=8192)[0]
@@ -257,6 +258,51 @@ def test_split_at_class_boundaries(lbm, Ny):
     for x, y in zip(split[1:], whole[1:]):
         assert np.array_equal(x, y)
     assert abs(np.sum(split[1]) - Ny) < 1e-3 * Ny          # rho: the walls conserve mass
+
+
+def test_running_request_promoted_to_a_cluster(lbm):
+    # 16 CTAs of budget filled at once by 15 short requests (3000 steps each)
+    # and a long one, which therefore starts on one CTA; once the short ones
+    # are done the server moves it to a cluster (its state stays in place),
+    # and its result equals that of a run on one CTA throughout, bit for bit
+    item = ("D2Q37", 1024, 0.01, 0.1, 1.0)
+    s = lbm.Server(mem_budget_bytes=1 << 28, max_slots=16, chunk_steps=50)
+    for _ in range(15):
+        s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-30, max_steps=3000))
+    rid = s.submit(lbm.make_request(*item, tol=1e-30, max_steps=20000))
+    s.drain(300)
+    promoted = s.stats().promoted
+    r = {x.id: x for x in s.poll(64)}[rid]
+    fields = s.fetch(rid, item[1])
+    s.close()
+    assert promoted >= 1
+    whole = fixed_steps(lbm, [item], 20000, max_slots=16, cluster_rows=8192)[0]
+    assert r.steps == whole[0].steps and r.residual == whole[0].residual
+    for x, y in zip(fields, whole[1:]):
+        assert np.array_equal(x, y)
+
+
+def test_cluster_shrinks_for_queued_requests(lbm):
+    # a long request alone on 16 CTAs of budget gets a 4-CTA cluster; 15
+    # requests arriving later need 3 of its CTAs, so it shrinks to one CTA
+    # and grows again once they are done; its result is that of a run on one
+    # CTA throughout, bit for bit
+    item = ("D2Q37", 1024, 0.01, 0.1, 1.0)
+    s = lbm.Server(mem_budget_bytes=1 << 28, max_slots=16, chunk_steps=50)
+    rid = s.submit(lbm.make_request(*item, tol=1e-30, max_steps=100000))
+    time.sleep(0.05)
+    for _ in range(15):
+        s.submit(lbm.make_request("D2Q17", 24, 0.5, 0.1, tol=1e-30, max_steps=3000))
+    s.drain(300)
+    st = s.stats()
+    r = {x.id: x for x in s.poll(64)}[rid]
+    fields = s.fetch(rid, item[1])
+    s.close()
+    assert st.demoted >= 1 and st.promoted >= 1 and st.completed == 16
+    whole = fixed_steps(lbm, [item], 100000, max_slots=16, cluster_rows=8192)[0]
+    assert r.steps == whole[0].steps and r.residual == whole[0].residual
+    for x, y in zip(fields, whole[1:]):
+        assert np.array_equal(x, y)
 
 
 def test_cancel_running_and_queued_requests(lbm):
