@@ -53,6 +53,11 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
         s_nt = nb;
     }
     __syncwarp();
+    // launched with programmatic stream serialization: the previous step may
+    // still be running; let the next step's launch begin, then wait for the
+    // previous grid to complete (its stores visible) before touching the state
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     const int j = blockIdx.x / k.Nx, x = blockIdx.x - j * k.Nx;
     // BF16: step count of the stochastic rounding (block 0 advances it)
     uint32_t seed = 0;
@@ -138,22 +143,53 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
     col.omc = C(1) - om;
     col.sx = k.r * ux;
     col.sy = k.r * uy;
-    col.set_coefficients(u2, th, om * col.rho, drho * inv, k);
+    // Eq. (4) coefficients: the c2-independent factors in every lane, those
+    // of shell s in lane s only (the per-shell work is not repeated by every
+    // lane, which matters where FP64 instructions are slow); each lane then
+    // takes its velocities' shells' values by shuffle
+    // (FP64 only: in FP32 the replicated per-shell work is cheaper than the
+    // shuffles, measured)
+    const int sh0 = a0 < Q ? s_sh[a0] : 0, sh1 = a1 < Q ? s_sh[a1] : 0;
+    C A0v[2], A1v[2], A2v[2], cwv[2];
+    if constexpr (sizeof(C) == 8) {
+        C pw[8];
+        col.powers(u2, th, drho * inv, k, pw);
+        C sA0 = 0, sA1 = 0, sA2 = 0, scw = 0;
+        if (lane < Lat<Q>::NSH)
+            Collision<Q, C, SHIFT>::shell(pw, om * col.rho, k, lane, sA0, sA1, sA2, scw);
+        const int shv[2] = {sh0, sh1};
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            A0v[i] = __shfl_sync(0xffffffffu, sA0, shv[i]);
+            A1v[i] = __shfl_sync(0xffffffffu, sA1, shv[i]);
+            A2v[i] = __shfl_sync(0xffffffffu, sA2, shv[i]);
+            cwv[i] = __shfl_sync(0xffffffffu, scw, shv[i]);
+        }
+    } else {
+        col.set_coefficients(u2, th, om * col.rho, drho * inv, k);
+        const int shv[2] = {sh0, sh1};
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            A0v[i] = col.A0[shv[i]];
+            A1v[i] = col.A1[shv[i]];
+            A2v[i] = col.A2[shv[i]];
+            cwv[i] = col.cw[shv[i]];
+        }
+    }
 
-    // relax and store this lane's velocities (Eq. (4)-(5))
-    auto relax_store = [&](int a, C f) {
-        const int s = s_sh[a];
+    // relax and store this lane's velocities (Eq. (4)-(5)); i: 0 for a0, 1 for a1
+    auto relax_store = [&](int a, int i, C f) {
         const C sv = C(s_ex[a]) * col.sx + C(s_ey[a]) * col.sy;
         const C s2 = sv * sv;
-        const C E = col.A0[s] + s2 * (col.A2[s] + col.A4 * s2);
-        const C O = sv * (col.A1[s] + col.A3 * s2);
-        C v = col.omc * f + col.cw[s] * (E + O);
+        const C E = A0v[i] + s2 * (A2v[i] + col.A4 * s2);
+        const C O = sv * (A1v[i] + col.A3 * s2);
+        C v = col.omc * f + cwv[i] * (E + O);
         if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
         store_with_images<S>(fout + (long long)a * k.plane + (long long)j * k.pitch, x, k.Nx,
                              store_rounded<S>(v, sr_bits(hcell, a)));
     };
-    if (a0 < Q) relax_store(a0, f0);
-    if (a1 < Q) relax_store(a1, f1);
+    if (a0 < Q) relax_store(a0, 0, f0);
+    if (a1 < Q) relax_store(a1, 1, f1);
     if constexpr (Store<PREC>::dev)
         if (lane == 0) store_with_images<float>(rout + (long long)j * k.pitch, x, k.Nx, (float)col.rho);
 }

@@ -81,9 +81,26 @@ int Launch<PREC>::step_cellwarp(SolverImpl &s, int src, int dst) {
     const auto &k = Consts<PREC>::get(s);
     const long long cells = (long long)s.p.Nx * s.p.Ny;
     if (cells > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-    LBM_DISPATCH_Q(s.L.Q, (k_step_cellwarp<QQ, PREC><<<(unsigned)cells, 32, 0, s.stream>>>(
-                               (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k)));
-    return (int)cudaGetLastError();
+    // programmatic dependent launch: a step's grid is launched while the
+    // previous one runs and waits for it on the device (griddepcontrol.wait),
+    // which hides the launch latency that dominates a step of a few thousand
+    // cells
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cells);
+    cfg.blockDim = dim3(32);
+    cfg.stream = s.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const S *fin = (const S *)s.f[src];
+    S *fout = (S *)s.f[dst];
+    const float *rin = s.rho[src];
+    float *rout = s.rho[dst];
+    LBM_DISPATCH_Q(s.L.Q, return (int)cudaLaunchKernelEx(&cfg, k_step_cellwarp<QQ, PREC>, fin, fout,
+                                                          rin, rout, k));
+    return (int)cudaErrorInvalidValue;
 }
 
 // ---- TMA-staged kernel variants (tile TX x TY, ring of STAGES, CPT cells per

@@ -189,6 +189,13 @@ struct Collision {
     // orho = omega rho; drr = (rho - 1) / rho (used when SHIFT)
     __device__ __forceinline__ void set_coefficients(C u2, C th, C orho, C drr,
                                                      const KConsts<C> &k) {
+        C p[8];
+        powers(u2, th, drr, k, p);
+#pragma unroll
+        for (int s = 0; s < L::NSH; ++s) shell(p, orho, k, s, A0[s], A1[s], A2[s], cw[s]);
+    }
+    // the c2-independent factors a00, a01, a02, a10, a11, a20, a21 (and A3, A4)
+    __device__ __forceinline__ void powers(C u2, C th, C drr, const KConsts<C> &k, C (&p)[8]) {
         const bool o3 = k.eq_order >= 3, o4 = k.eq_order >= 4;
         C a00 = (SHIFT ? drr : C(1)) - C(0.5) * u2 - th, a01 = C(0.5) * th, a02 = C(0);
         C a10 = C(1), a11 = C(0), a20 = C(0.5), a21 = C(0);
@@ -205,14 +212,17 @@ struct Collision {
         }
         A3 = o3 ? C(1) / C(6) : C(0);
         A4 = o4 ? C(1) / C(24) : C(0);
-#pragma unroll
-        for (int s = 0; s < L::NSH; ++s) {
-            const C c2 = k.c2sh[s];
-            A0[s] = (a02 * c2 + a01) * c2 + a00;
-            A1[s] = a11 * c2 + a10;
-            A2[s] = a21 * c2 + a20;
-            cw[s] = orho * k.wsh[s];
-        }
+        p[0] = a00; p[1] = a01; p[2] = a02; p[3] = a10; p[4] = a11; p[5] = a20; p[6] = a21;
+        p[7] = C(0);
+    }
+    // the coefficients of shell s
+    __device__ __forceinline__ static void shell(const C (&p)[8], C orho, const KConsts<C> &k, int s,
+                                                 C &A0s, C &A1s, C &A2s, C &cws) {
+        const C c2 = k.c2sh[s];
+        A0s = (p[2] * c2 + p[1]) * c2 + p[0];
+        A1s = p[4] * c2 + p[3];
+        A2s = p[6] * c2 + p[5];
+        cws = orho * k.wsh[s];
     }
 
     // post-collision values of the rest velocity and of pair (a, a+1)
