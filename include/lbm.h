@@ -380,7 +380,10 @@ int lbm_request_bytes(const lbm_request *req, size_t *bytes);
  * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out);
 /* Queue a request (thread-safe, non-blocking); it is admitted as soon as a
- * slot and pool memory are free, while other requests keep running.
+ * slot and pool memory are free, while other requests keep running.  A long
+ * request may run on a cluster of CTAs, and between chunks a running one may
+ * move to a larger cluster (CTAs spare) or a smaller one (queued requests
+ * lack CTAs); its result does not depend on where it ran.
  * Errors: LBM_EINVAL (bad request), LBM_EBUDGET (larger than the budget). */
 int lbm_server_submit(lbm_server *srv, const lbm_request *req, uint64_t *id);
 /* Non-blocking: copy up to max finished results (oldest first) to out. */
@@ -390,7 +393,7 @@ int lbm_server_poll(lbm_server *srv, lbm_result *out, int32_t max, int32_t *n);
 int lbm_server_fetch(lbm_server *srv, uint64_t id, double *rho, double *ux,
                      double *uy, double *T);
 /* Cancel request `id`: a queued request is dropped, a running one stops at
- * the end of its current chunk.  Either completes with status LBM_ECANCELLED
+ * the end of its current launch (one or a few chunks).  Either completes with status LBM_ECANCELLED
  * (poll returns it, drain counts it); fetch then gives the fields where a
  * running request stopped, and zeros for one that never ran.  Thread-safe.
  * Errors: LBM_EINVAL (no queued or running request with this id). */
