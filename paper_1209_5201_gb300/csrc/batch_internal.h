@@ -68,9 +68,11 @@ struct SlotStatus {
 // Cluster sizes of the slot classes.
 constexpr int kBatchClasses = 5;
 constexpr int kBatchClassCL[kBatchClasses] = {1, 2, 4, 8, 16};
+// Tallest column a request may have.
+constexpr int kMaxNy = 8192;
 // Rows of the residual's partial sums (one warp each) and their most per slot.
 constexpr int kResidualChunk = 32;
-constexpr int kMaxResidualChunks = 8192 / kResidualChunk;
+constexpr int kMaxResidualChunks = kMaxNy / kResidualChunk;
 
 // Rows per CTA of a column of Ny rows on a cluster of CL CTAs: all of them on
 // one CTA, else ceil(Ny / CL) rounded up to whole residual chunks, so that no

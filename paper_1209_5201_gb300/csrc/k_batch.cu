@@ -26,7 +26,7 @@ __device__ __forceinline__ bool desc_ok(const SlotDesc &d, long long pool_elems,
     for (int a = 0; a < d.Q && q_ok; ++a)
         mirror_ok = mirror_ok && d.k.mirror[a] >= 0 && d.k.mirror[a] < d.Q;
     const bool cl_ok = batch_split_ok(d.Ny, d.cl);
-    const bool ok = q_ok && terms_ok && mirror_ok && cl_ok && d.Ny >= 6 && d.Ny <= 8192 &&
+    const bool ok = q_ok && terms_ok && mirror_ok && cl_ok && d.Ny >= 6 && d.Ny <= kMaxNy &&
                     d.sub >= 1 && d.sub <= kMaxSub &&
                     d.f_off >= 0 &&
                     d.f_off + need <= pool_elems && d.prev_off == d.f_off + 2LL * d.Q * d.Ny &&

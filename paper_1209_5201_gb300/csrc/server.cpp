@@ -39,7 +39,6 @@
 namespace lbm {
 namespace {
 
-constexpr int kMaxNy = 8192;
 // work above which a request counts as long for the cluster choice: row-steps
 // per thread on one CTA (~1 s at ~4 us per step and 256 rows)
 constexpr double kLongRowSteps = 2.5e5;
