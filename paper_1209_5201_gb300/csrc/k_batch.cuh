@@ -72,10 +72,9 @@ __device__ __forceinline__ void slot_barrier(int CL) {
 constexpr int kSmemRows = 256;
 constexpr int kSmemBytes = 2 * kMaxQ * kSmemRows * (int)sizeof(float);
 
-// The shared-memory path serves split columns whose CTAs' rows fit; a column on
-// one CTA keeps its state in global memory (L2), which measured faster there.
+// The shared-memory path serves every column whose CTAs' rows fit.
 __host__ __device__ inline bool batch_uses_smem(int Ny, int CL) {
-    return CL > 1 && batch_rows_per_cta(Ny, CL) <= kSmemRows;
+    return batch_rows_per_cta(Ny, CL) <= kSmemRows;
 }
 
 // Population a of the wall re-emission (Eq. (9) with R = accom R_D + (1 -
