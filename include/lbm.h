@@ -151,8 +151,9 @@ int lbm_solver_required_bytes(const lbm_lattice *lat, const lbm_params *p,
  * caller owns and keeps alive until lbm_solver_destroy (the Python binding
  * passes a torch allocation); if NULL the library allocates (and frees) its
  * own with cudaMallocAsync on `stream`.  The lattice may be destroyed after
- * this call.  Errors: LBM_EINVAL (parameters; Ny < 2 N, eq_order, precision),
- * LBM_ENOMEM, LBM_ECUDA. */
+ * this call.  Errors: LBM_EINVAL (parameters; Ny < 2 N, eq_order, precision,
+ * or Q x Ny x padded row >= 2^31 elements per state buffer), LBM_ENOMEM,
+ * LBM_ECUDA. */
 int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
                       void *device_mem, size_t device_bytes, lbm_solver **out);
 int lbm_solver_destroy(lbm_solver *s);
