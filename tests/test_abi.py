@@ -104,6 +104,13 @@ def test_params_default_and_checks(lbm):
         p.Nx, p.Ny, p.precision = 4096, 2048, lbm.LBM_FP32
         n = lbm.lbm_solver_required_bytes(h, p)
         assert 2 * 37 * 2048 * 4096 * 4 < n < 2 * 37 * 2048 * 4224 * 4 + 7 * 4096 * 2048 * 8
+        # the largest buffer the kernels' 32-bit offsets address, and one past it
+        p.Nx, p.Ny = 8192, 7000
+        lbm.lbm_solver_required_bytes(h, p)
+        p.Ny = 7100
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_solver_required_bytes(h, p)
+        assert ei.value.status == lbm.LBM_EINVAL
     finally:
         lbm.lbm_lattice_destroy(h)
 
