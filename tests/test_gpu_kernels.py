@@ -142,3 +142,30 @@ def test_full_size_workload_sampled_columns(lbm, oracle):
     st = s.stats()
     assert st.mass_drift < 1e-6
     s.close()
+
+
+def test_largest_grid_the_offsets_address(lbm, oracle):
+    # D2Q37 FP32 at 8192 x 7000: a state buffer just under 2^31 elements, so
+    # the velocity-plane offsets of the step kernel reach their largest
+    # values; no density noise, so every column equals the oracle's
+    # single-column solve of the same height
+    Nx, Ny, n = 8192, 7000, 8
+    cfg = lbm.Config(lattice="D2Q37", Nx=Nx, Ny=Ny, eq_order=4, thermal=True, Kn=0.05,
+                     u_wall=(-0.3, 0.3), precision="fp32", kernel=lbm.LBM_KERNEL_DIRECT)
+    s = lbm.Solver(cfg)
+    s.init()
+    s.step(n)
+    s.sync()
+    _, ux, _, T = s.macros()
+    st = s.stats()
+    s.close()
+    p = oracle.Problem(lattice="D2Q37", Nx=1, Ny=Ny, eq_order=4, thermal=True, Kn=0.05,
+                       u_wall=(-0.3, 0.3))
+    fo = oracle.init_fields(p, np.ones((Ny, 1)))
+    oracle.run(p, fo, n)
+    _, oux, _, oT = oracle.macros(p, fo)
+    for c in (0, 3, 4096, 8188, 8191):
+        assert np.max(np.abs(ux[:, c] - oux[:, 0])) < 1e-5 * 0.3, c
+        assert np.max(np.abs(T[:, c] - oT[:, 0])) < 1e-5, c
+    assert np.max(np.abs(ux - ux[:, :1])) < 1e-6
+    assert st.mass_drift < 1e-6
