@@ -86,35 +86,20 @@ __device__ __forceinline__ void store_cs<__nv_bfloat16>(__nv_bfloat16 *p, __nv_b
     __stcs((unsigned short *)p, __bfloat16_as_ushort(v));
 }
 
-// BX threads per block (one row segment); MINB blocks per SM requested from
-// the register allocator; CS: streaming stores for the interior columns.
-template <int Q, int PREC, int BX, int MINB, bool CS>
-__global__ void __launch_bounds__(BX, MINB)
-k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
-              typename Store<PREC>::S *__restrict__ fout, const float *__restrict__ rin,
-              float *__restrict__ rout,
-              const __grid_constant__ KConsts<typename Store<PREC>::C> k) {
+// One cell's update: pull (in the N rows next to a wall, with the wall's
+// re-emission from s_min, that wall's incoming-mass sums), collide, store.
+template <int Q, int PREC, bool CS>
+__device__ __forceinline__ void step_cell(const typename Store<PREC>::S *__restrict__ fin,
+                                          typename Store<PREC>::S *__restrict__ fout,
+                                          const float *__restrict__ rin, float *__restrict__ rout,
+                                          const KConsts<typename Store<PREC>::C> &k, int x, int j,
+                                          const double *s_min, uint32_t seed) {
     using L = Lat<Q>;
     using S = typename Store<PREC>::S;
     using C = typename Store<PREC>::C;
-    __shared__ double s_min[BX + 6];
-    const int j = blockIdx.y;
-    const int x0 = blockIdx.x * BX;
-    const int x = x0 + threadIdx.x;
-    const bool bot = j < L::N, top = j >= k.Ny - L::N;
-    if (bot || top) {
-        wall_prologue<Q, PREC, BX>(fin, rin, k, bot ? 0 : 1, x0, s_min);
-        __syncthreads();
-    }
-    // BF16: step count of the stochastic rounding (block 0 advances it)
-    uint32_t seed = 0;
-    if constexpr (Store<PREC>::dev)
-        seed = step_count(fin, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
-    if (x >= k.Nx) return;
     const uint32_t hcell = Store<PREC>::dev ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
-
     C f[Q];
-    if (bot || top) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, f);
+    if (j < L::N || j >= k.Ny - L::N) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, f);
     else pull<Q, PREC, false>(fin, rin, k, x, j, s_min, f);
 
     Collision<Q, C, Store<PREC>::shifted> col;
@@ -149,6 +134,36 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
         }
         if constexpr (Store<PREC>::dev) store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);
     }
+}
+
+// BX threads per block (one row segment); MINB blocks per SM requested from
+// the register allocator; CS: streaming stores for the interior columns; RS
+// rows per block, walked in order (rows [RS blockIdx.y, RS blockIdx.y + RS)).
+template <int Q, int PREC, int BX, int MINB, bool CS, int RS>
+__global__ void __launch_bounds__(BX, MINB)
+k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
+              typename Store<PREC>::S *__restrict__ fout, const float *__restrict__ rin,
+              float *__restrict__ rout,
+              const __grid_constant__ KConsts<typename Store<PREC>::C> k) {
+    using L = Lat<Q>;
+    using S = typename Store<PREC>::S;
+    using C = typename Store<PREC>::C;
+    __shared__ double s_min[2][BX + 6];
+    const int x0 = blockIdx.x * BX;
+    const int x = x0 + threadIdx.x;
+    const int j0 = blockIdx.y * RS;
+    const int j1 = min(k.Ny, j0 + RS);
+    const bool bot = j0 < L::N, top = j1 > k.Ny - L::N;
+    if (bot) wall_prologue<Q, PREC, BX>(fin, rin, k, 0, x0, s_min[0]);
+    if (top) wall_prologue<Q, PREC, BX>(fin, rin, k, 1, x0, s_min[1]);
+    if (bot || top) __syncthreads();
+    // BF16: step count of the stochastic rounding (block 0 advances it)
+    uint32_t seed = 0;
+    if constexpr (Store<PREC>::dev)
+        seed = step_count(fin, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
+    if (x >= k.Nx) return;
+    for (int j = j0; j < j1; ++j)
+        step_cell<Q, PREC, CS>(fin, fout, rin, rout, k, x, j, s_min[j < L::N ? 0 : 1], seed);
 }
 
 }  // namespace lbm

@@ -36,18 +36,20 @@ inline int aux_blocks(long long n) {
     default: return (int)cudaErrorInvalidValue;                 \
     }
 
-// ---- direct kernel variants {BX, MINB, CS} --------------------------------------
+// ---- direct kernel variants {BX, MINB, CS, RS} ----------------------------------
+// RS: rows per block
 struct DirectVariants {
-    static constexpr int n = 5;
-    static constexpr int v[n][3] = {{128, 0, 0}, {64, 0, 0}, {128, 8, 0}, {256, 0, 0}, {128, 0, 1}};
+    static constexpr int n = 7;
+    static constexpr int v[n][4] = {{128, 0, 0, 1}, {64, 0, 0, 1},  {128, 8, 0, 1}, {256, 0, 0, 1},
+                                    {128, 0, 1, 1}, {192, 0, 0, 1}, {128, 0, 0, 2}};
 };
 
-template <int Q, int PREC, int BX, int MINB, bool CS>
+template <int Q, int PREC, int BX, int MINB, bool CS, int RS>
 int launch_direct(SolverImpl &s, int src, int dst) {
     using S = typename Store<PREC>::S;
     const auto &k = Consts<PREC>::get(s);
-    dim3 grid((s.p.Nx + BX - 1) / BX, s.p.Ny);
-    k_step_direct<Q, PREC, BX, MINB, CS><<<grid, BX, 0, s.stream>>>(
+    dim3 grid((s.p.Nx + BX - 1) / BX, (s.p.Ny + RS - 1) / RS);
+    k_step_direct<Q, PREC, BX, MINB, CS, RS><<<grid, BX, 0, s.stream>>>(
         (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
     return (int)cudaGetLastError();
 }
@@ -58,7 +60,7 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
 #define LBM_DIRECT_CASE(I)                                                                 \
     case I:                                                                                \
         LBM_DISPATCH_Q(s.L.Q, return (launch_direct<QQ, PREC, V::v[I][0], V::v[I][1],       \
-                                                    (V::v[I][2] != 0)>(s, src, dst)));     \
+                                                    (V::v[I][2] != 0), V::v[I][3]>(s, src, dst))); \
         break;
     switch (variant) {
         LBM_DIRECT_CASE(0)
@@ -66,6 +68,8 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
         LBM_DIRECT_CASE(2)
         LBM_DIRECT_CASE(3)
         LBM_DIRECT_CASE(4)
+        LBM_DIRECT_CASE(5)
+        LBM_DIRECT_CASE(6)
     default: break;
     }
 #undef LBM_DIRECT_CASE
