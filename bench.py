@@ -369,7 +369,8 @@ def run_reference(args):
 
 
 # kernel sources whose change invalidates recorded DRAM counters
-TRAFFIC_SOURCES = ["k_step_direct.cuh", "k_step_staged.cuh", "lbm_device.cuh", "lbm_internal.h"]
+TRAFFIC_SOURCES = ["k_step_direct.cuh", "k_step_staged.cuh", "lbm_device.cuh", "lbm_internal.h",
+                   "launchers_impl.cuh"]
 
 
 def kernel_sources_sha256() -> str:
