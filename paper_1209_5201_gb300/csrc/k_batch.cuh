@@ -186,12 +186,8 @@ template <int OFF>
 __device__ __forceinline__ void sts_f32(uint32_t addr, float v) {
     asm volatile("st.shared.f32 [%0+%1], %2;\n" ::"r"(addr), "n"(OFF), "f"(v) : "memory");
 }
-__device__ __forceinline__ float ldsc_f32(uint32_t addr) {
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(addr) : "memory");
-    return v;
-}
-// The same load without a compiler memory clobber: ordered only against the
+// Load through the shared::cluster window (this CTA's or a neighbour's
+// shared memory), without a compiler memory clobber: ordered only against the
 // other volatile asm (the loads, stores and barriers of this file), so the
 // constants read around it can stay in registers.
 __device__ __forceinline__ float ldsc_f32_nc(uint32_t addr) {
@@ -221,12 +217,6 @@ struct SmemState {
     int R, j0, b;
     __device__ __forceinline__ uint32_t row_addr(int buf, int lr) const {
         return base + (uint32_t)((buf * R + lr) * Q) * 4u;
-    }
-    __device__ __forceinline__ float ld(int a, int row) const {
-        const int lr = row - j0;
-        if (lr < 0) return ldsc_f32(lo + (uint32_t)(((b * R + lr + R) * Q + a) * 4));
-        if (lr >= R) return ldsc_f32(hi + (uint32_t)(((b * R + lr - R) * Q + a) * 4));
-        return lds_f32(row_addr(b, lr) + (uint32_t)a * 4u);
     }
     __device__ __forceinline__ float ld_own(int a, int row) const {
         return lds_f32(row_addr(b, row - j0) + (uint32_t)a * 4u);
