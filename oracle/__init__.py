@@ -12,7 +12,8 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   lattice.*                 pinned: Gaussian moment isotropy, closed forms
   orc_equilibrium           pinned: Maxwellian moments through the kept order
   orc_collide               pinned: exact conservation of rho, rho u (, energy)
-  orc_run (stream + wall)   pinned: rest / uniform-flow fixed points, per-step
+  orc_run (stream + wall)   pinned: free streaming by e_a (periodic in x),
+                            rest / uniform-flow fixed points, per-step
                             zero net wall mass flux, slot bookkeeping,
                             positivity, Couette antisymmetry, NS slip limit
                             (Eq. (13)), NS temperature profile (Eq. (14), read

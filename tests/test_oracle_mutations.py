@@ -13,6 +13,11 @@ import pytest
 import test_oracle_pins as pins
 
 MUTATIONS = {
+    # push-stream of Eq. (5) in the wrong x direction (invisible to every
+    # x-independent Couette pin)
+    "stream_x_reversed": (
+        "int tx = ((x + L->ex[a]) % Nx + Nx) % Nx;", "int tx = ((x - L->ex[a]) % Nx + Nx) % Nx;",
+        lambda o: pins.test_free_streaming_moves_each_population_by_its_velocity(o, "D2Q25")),
     # dropped (T-1)^2/8 term of Eq. (4)
     "drop_theta2_term": (
         "g += th * th / 8.0 * (c2 * c2 - 2.0 * (D + 2.0) * c2 + D * (D + 2.0));", "",

@@ -190,6 +190,30 @@ def test_rest_state_is_fixed_point(oracle, name):
 
 
 @pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
+def test_free_streaming_moves_each_population_by_its_velocity(oracle, name):
+    # Eq. (5) with tau -> infinity: omega = dt / (tau + dt/2) ~ 1e-14, so the
+    # collision leaves f as it is and a step is the pure stream.  A bump on
+    # population a of one interior cell reappears, unchanged, e_a cells away
+    # (periodic in x: the cell sits next to the right edge), and nothing else
+    # moves (the rest state is a fixed point).
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    Nx, Ny, x0, j0 = 16, 20, 14, 9
+    p = oracle.Problem(lattice=name, Nx=Nx, Ny=Ny, eq_order=order, thermal=thermal,
+                       tau=1e12, Kn=0.0, u_wall=(0.0, 0.0))
+    base = oracle.init_fields(p, np.ones((Ny, Nx)))
+    e = p.lat.e
+    for a in range(p.lat.Q):
+        f = base.copy()
+        f[a, j0, x0] += 1e-3
+        oracle.run(p, f, 1)
+        d = f - base
+        tx, tj = (x0 + int(e[a, 0])) % Nx, j0 + int(e[a, 1])
+        assert abs(d[a, tj, tx] - 1e-3) < 1e-12, (name, a)
+        d[a, tj, tx] = 0.0
+        assert np.max(np.abs(d)) < 1e-12, (name, a)
+
+
+@pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
 def test_uniform_flow_is_fixed_point(oracle, name):
     # both walls move with the gas: the diffuse wall re-emits exactly g^eq(U, T_w)
     order, thermal = (4, True) if name == "D2Q37" else (2, False)
