@@ -13,6 +13,7 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   orc_equilibrium           pinned: Maxwellian moments through the kept order
   orc_collide               pinned: exact conservation of rho, rho u (, energy)
   orc_run (stream + wall)   pinned: free streaming by e_a (periodic in x),
+                            re-emission from each ghost column by e_a,
                             rest / uniform-flow fixed points, per-step
                             zero net wall mass flux, slot bookkeeping,
                             positivity, Couette antisymmetry, NS slip limit

@@ -214,6 +214,41 @@ def test_free_streaming_moves_each_population_by_its_velocity(oracle, name):
 
 
 @pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
+def test_wall_re_emission_lands_from_its_ghost_column(oracle, name):
+    # Free streaming again (tau -> infinity; the step is linear in f): a bump
+    # on the population with e = (1, -1) in row 0 enters the bottom wall's
+    # ghost layer 0 at column x0 + 1 (reading 6: M_in per ghost column) and
+    # comes back as the diffuse re-emission of Eq. (12) from that column:
+    # velocity a with e_ay > 0 receives bump g^w_a / D_w on every row
+    # e_ay - 1 - l, l < e_ay, at column x0 + 1 + e_ax (periodic), where
+    # g^w = g^eq(u_w, T_w) and D_w = sum_{e_y > 0} e_y g^w (Eq. (11)).
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    Nx, Ny, x0, bump = 12, 12, 10, 1e-3
+    uw, Tw = -0.2, 1.05
+    p = oracle.Problem(lattice=name, Nx=Nx, Ny=Ny, eq_order=order, thermal=thermal,
+                       tau=1e12, Kn=0.0, u_wall=(uw, 0.1), T_wall=(Tw, 1.0))
+    e = p.lat.e.astype(int)
+    b = [i for i in range(p.lat.Q) if e[i, 0] == 1 and e[i, 1] == -1][0]
+    base = oracle.init_fields(p, inputs.rho_field(Nx, Ny, 0.02, seed=5))
+    f0, f1 = base.copy(), base.copy()
+    f1[b, 0, x0] += bump
+    oracle.run(p, f0, 1)
+    oracle.run(p, f1, 1)
+    d = f1 - f0
+    gw = oracle.equilibrium(p, 1.0, uw, 0.0, Tw if thermal else 1.0)
+    den = sum(e[a, 1] * gw[a] for a in range(p.lat.Q) if e[a, 1] > 0)
+    gw_o, den_o = oracle.wall_distribution(p, 0)
+    assert np.allclose(gw, gw_o, rtol=1e-13, atol=0) and abs(den - den_o) < 1e-13 * den
+    want = np.zeros_like(d)
+    xg = (x0 + 1) % Nx
+    for a in range(p.lat.Q):
+        for l in range(max(0, e[a, 1])):
+            want[a, e[a, 1] - 1 - l, (xg + e[a, 0]) % Nx] = bump * gw[a] / den
+    assert np.max(np.abs(d - want)) < 1e-13, name
+    assert abs(d.sum() - bump) < 1e-15
+
+
+@pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
 def test_uniform_flow_is_fixed_point(oracle, name):
     # both walls move with the gas: the diffuse wall re-emits exactly g^eq(U, T_w)
     order, thermal = (4, True) if name == "D2Q37" else (2, False)
