@@ -172,3 +172,19 @@ def test_custom_lattice_from_tables(lbm):
     # a weight set that is not a quadrature is accepted but its degree says so
     w = np.full(25, 1.0 / 25)
     assert lbm.Lattice("custom", custom=(ref.e, w, ref.r)).degree < 3
+
+
+def test_binding_covers_every_declaration_with_its_arity(lbm):
+    # every function include/lbm.h declares has a ctypes signature in the
+    # binding with the same number of parameters (marshalling only)
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = {}
+    for m in re.finditer(r"\b(?:const char\s*\*|int|void|double|int32_t|int64_t|size_t)\s*\**\s*"
+                         r"(lbm_\w+)\s*\(([^)]*)\)\s*;", src, flags=re.S):
+        params = m.group(2).strip()
+        decls[m.group(1)] = 0 if params in ("", "void") else len(params.split(","))
+    assert len(decls) >= 40 and set(decls) == set(declared_symbols())
+    for name, n in decls.items():
+        assert name in lbm._SIGS, name
+        assert len(lbm._SIGS[name][0]) == n, (name, n, len(lbm._SIGS[name][0]))
