@@ -1,12 +1,14 @@
 // One-pass pull kernel of a full time step (Eq. (5) with the Eq. (12) wall).
 //
 // One thread per fluid cell (x, j); a block covers BX consecutive columns of
-// one row.  Every population is read once, straight from global memory at the
+// RS consecutive rows (one in the fastest shapes), which each thread walks in
+// order.  Every population is read once, straight from global memory at the
 // source cell (x - e_ax, j - e_ay): SoA rows are contiguous in x, so a warp's
 // 32 loads of one velocity plane are one contiguous (possibly 4..12-byte
 // shifted) segment.  Periodic images in the padded row remove the modulo in x.
-// Blocks of the N rows next to a wall first sum the incoming mass M_in of the
-// BX + 6 ghost columns their fill populations come from (FP64, fixed order).
+// Blocks holding any of the N rows next to a wall first sum that wall's
+// incoming mass M_in for the BX + 6 ghost columns their fill populations come
+// from (FP64, fixed order).
 #pragma once
 
 #include <type_traits>
