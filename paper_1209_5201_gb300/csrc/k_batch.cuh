@@ -1,17 +1,18 @@
 // Batched chunk kernel: many independent single-column Couette instances
 // (Nx = 1, each with its own lattice, height, Kn, wall speeds and wall
-// temperatures) advanced together, `chunk` time steps per launch, then an
-// FP64 steady-state residual per slot.
+// temperatures) advanced together, `sub` chunks of `chunk` time steps per
+// launch, with an FP64 steady-state residual after every check_every-th
+// chunk of a slot.
 //
 // With Nx = 1 the pull of Eq. (5) only shifts in y: f_in(j, a) =
 // f~*(j - e_ay, a).  A slot runs on a cluster of CL CTAs (CL = 1, 2, 4, 8 or
 // 16, fixed by its height): CTA `rank` owns rows [rank R, rank R + R), R =
 // ceil(Ny / CL), and a cluster barrier with release / acquire semantics
 // separates the steps.  When R <= kSmemRows the CTA keeps its rows' two state
-// buffers in shared memory for the whole chunk (loaded from the pool at the
+// buffers in shared memory for the whole launch (loaded from the pool at the
 // start, written back at the end; rows of Q populations) and pulls the <= 3
 // rows it needs from each neighbour through distributed shared memory
-// (ld.shared::cluster); taller slots keep the state in global memory
+// (ld.shared::cluster); taller blocks keep the state in global memory
 // (L2-resident) and read it with ld.global.cg.
 //
 // Row mapping inside a CTA: warp 0 of the bottom CTA owns the (up to) 32
@@ -20,7 +21,8 @@
 // warp shuffle in a fixed lane order - lane l loads the l-th (velocity, row)
 // term of the wall's list, built on the host and carried in the slot
 // descriptor - forms the normalised re-emission of every outgoing velocity
-// once, and then updates its rows.  The other rows never need a wall value,
+// once, and then updates its rows (branch-free: sources clamped into the
+// slot, the wall's values selected afterwards).  The other rows never need a wall value,
 // so no block barrier separates the wall sums from the bulk update.  Every
 // slot's arithmetic depends only on the slot itself (its cluster size is a
 // function of its height), never on the slot index, the grid or other slots.

@@ -10,10 +10,12 @@
 //   1. admits queued requests into idle slots of their class while the CTA
 //      budget (max_slots) and the pool (first-fit allocator) have room for
 //      them, initialises them;
-//   2. runs one chunk launch per class, the four concurrently (a CUDA graph:
-//      fork, kernels, join, status read-back), so admitted work overlaps with
+//   2. moves running requests between cluster sizes when CTAs are spare or
+//      queued requests lack them (the state stays in place);
+//   3. runs one launch per class, the five concurrently (a CUDA graph: fork,
+//      kernels, join, status read-back), so admitted work overlaps with
 //      slots already running;
-//   3. retires slots whose status left "running": reads their Eq. (3)
+//   4. retires slots whose status left "running": reads their Eq. (3)
 //      profiles back, frees their memory, records the latency.
 // The f-arrays of a request stay resident on the device from admission to
 // retirement.  A request too large for the whole budget is refused with
