@@ -5,7 +5,9 @@
 //
 // Lane l carries velocities l and l + 32 (Q <= 37): it pulls them, the warp
 // sums the moments with a butterfly of shuffles (every lane gets the totals),
-// every lane forms the Eq. (4) coefficients and relaxes its own velocities.
+// every lane forms the shell-independent Eq. (4) factors (FP64: lane s the
+// coefficients of shell s, shuffled to the lanes that need them) and relaxes
+// its own velocities.  Steps are launched with programmatic dependent launch.
 // A wall row's warp first sums the incoming mass of the ghost columns its
 // fills come from, one term per lane (the wall's term list, <= 26 terms).
 // The moments are summed in another order than the one-thread kernels use,
