@@ -16,7 +16,7 @@ MUTATIONS = {
     # diffuse re-emission pushed from the ghost column the wrong way in x
     "re_emission_x_reversed": (
         "int tx = ((xw + L->ex[a]) % Nx + Nx) % Nx;", "int tx = ((xw - L->ex[a]) % Nx + Nx) % Nx;",
-        lambda o: pins.test_wall_re_emission_lands_from_its_ghost_column(o, "D2Q37")),
+        lambda o: pins.test_wall_re_emission_lands_from_its_ghost_column(o, "D2Q37", 1)),
     # push-stream of Eq. (5) in the wrong x direction (invisible to every
     # x-independent Couette pin)
     "stream_x_reversed": (

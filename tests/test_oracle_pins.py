@@ -213,38 +213,45 @@ def test_free_streaming_moves_each_population_by_its_velocity(oracle, name):
         assert np.max(np.abs(d)) < 1e-12, (name, a)
 
 
+@pytest.mark.parametrize("wall", [0, 1])
 @pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
-def test_wall_re_emission_lands_from_its_ghost_column(oracle, name):
+def test_wall_re_emission_lands_from_its_ghost_column(oracle, name, wall):
     # Free streaming again (tau -> infinity; the step is linear in f): a bump
-    # on the population with e = (1, -1) in row 0 enters the bottom wall's
-    # ghost layer 0 at column x0 + 1 (reading 6: M_in per ghost column) and
-    # comes back as the diffuse re-emission of Eq. (12) from that column:
-    # velocity a with e_ay > 0 receives bump g^w_a / D_w on every row
-    # e_ay - 1 - l, l < e_ay, at column x0 + 1 + e_ax (periodic), where
-    # g^w = g^eq(u_w, T_w) and D_w = sum_{e_y > 0} e_y g^w (Eq. (11)).
+    # on the population with e = (1, -1) in row 0 (bottom wall; (1, 1) in row
+    # Ny - 1 for the top wall) enters the wall's ghost layer 0 at column
+    # x0 + 1 (reading 6: M_in per ghost column) and comes back as the diffuse
+    # re-emission of Eq. (12) from that column: velocity a leaving the wall
+    # (e_ay n > 0) receives bump g^w_a / D_w on each of the |e_ay| rows its
+    # layers l < |e_ay| reach, at column x0 + 1 + e_ax (periodic), where
+    # g^w = g^eq(u_w, T_w) and D_w = sum_{e.n > 0} |e.n| g^w (Eq. (11)).
     order, thermal = (4, True) if name == "D2Q37" else (2, False)
     Nx, Ny, x0, bump = 12, 12, 10, 1e-3
-    uw, Tw = -0.2, 1.05
+    u_wall, T_wall = (-0.2, 0.15), (1.05, 0.96)
     p = oracle.Problem(lattice=name, Nx=Nx, Ny=Ny, eq_order=order, thermal=thermal,
-                       tau=1e12, Kn=0.0, u_wall=(uw, 0.1), T_wall=(Tw, 1.0))
+                       tau=1e12, Kn=0.0, u_wall=u_wall, T_wall=T_wall)
     e = p.lat.e.astype(int)
-    b = [i for i in range(p.lat.Q) if e[i, 0] == 1 and e[i, 1] == -1][0]
+    n = 1 if wall == 0 else -1                  # wall normal, into the gas
+    b = [i for i in range(p.lat.Q) if e[i, 0] == 1 and e[i, 1] == -n][0]
+    row = 0 if wall == 0 else Ny - 1
     base = oracle.init_fields(p, inputs.rho_field(Nx, Ny, 0.02, seed=5))
     f0, f1 = base.copy(), base.copy()
-    f1[b, 0, x0] += bump
+    f1[b, row, x0] += bump
     oracle.run(p, f0, 1)
     oracle.run(p, f1, 1)
     d = f1 - f0
-    gw = oracle.equilibrium(p, 1.0, uw, 0.0, Tw if thermal else 1.0)
-    den = sum(e[a, 1] * gw[a] for a in range(p.lat.Q) if e[a, 1] > 0)
-    gw_o, den_o = oracle.wall_distribution(p, 0)
+    gw = oracle.equilibrium(p, 1.0, u_wall[wall], 0.0, T_wall[wall] if thermal else 1.0)
+    den = sum(n * e[a, 1] * gw[a] for a in range(p.lat.Q) if n * e[a, 1] > 0)
+    gw_o, den_o = oracle.wall_distribution(p, wall)
     assert np.allclose(gw, gw_o, rtol=1e-13, atol=0) and abs(den - den_o) < 1e-13 * den
     want = np.zeros_like(d)
     xg = (x0 + 1) % Nx
     for a in range(p.lat.Q):
-        for l in range(max(0, e[a, 1])):
-            want[a, e[a, 1] - 1 - l, (xg + e[a, 0]) % Nx] = bump * gw[a] / den
-    assert np.max(np.abs(d - want)) < 1e-13, name
+        depth = n * e[a, 1]
+        for l in range(max(0, depth)):
+            # ghost layer l sits at row -1 - l (bottom) or Ny + l (top)
+            ghost = -1 - l if wall == 0 else Ny + l
+            want[a, ghost + e[a, 1], (xg + e[a, 0]) % Nx] = bump * gw[a] / den
+    assert np.max(np.abs(d - want)) < 1e-13, (name, wall)
     assert abs(d.sum() - bump) < 1e-15
 
 
