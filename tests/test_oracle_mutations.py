@@ -13,6 +13,11 @@ import pytest
 import test_oracle_pins as pins
 
 MUTATIONS = {
+    # specular partner taken from the neighbouring ghost column
+    "specular_partner_shifted": (
+        "fspec[a * N + l] = ext[b * eplane + (long)(grow + N) * Nx + xw];",
+        "fspec[a * N + l] = ext[b * eplane + (long)(grow + N) * Nx + (xw + 1) % Nx];",
+        lambda o: pins.test_specular_wall_mirrors_each_incoming_population(o, "D2Q25")),
     # diffuse re-emission pushed from the ghost column the wrong way in x
     "re_emission_x_reversed": (
         "int tx = ((xw + L->ex[a]) % Nx + Nx) % Nx;", "int tx = ((xw - L->ex[a]) % Nx + Nx) % Nx;",

@@ -256,6 +256,38 @@ def test_wall_re_emission_lands_from_its_ghost_column(oracle, name, wall):
 
 
 @pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
+def test_specular_wall_mirrors_each_incoming_population(oracle, name):
+    # Eq. (9) with R = R_S (accommodation 0) and free streaming: a bump on
+    # velocity (e_x, -m) in row r < m reaches ghost layer m - 1 - r at column
+    # x0 + e_x, and the mirrored velocity (e_x, m) leaves that node on the same
+    # layer: it lands back in row r, 2 e_x columns further (periodic), and
+    # nothing else changes.
+    order, thermal = (4, True) if name == "D2Q37" else (2, False)
+    Nx, Ny, x0, bump = 12, 14, 5, 1e-3
+    p = oracle.Problem(lattice=name, Nx=Nx, Ny=Ny, eq_order=order, thermal=thermal,
+                       tau=1e12, Kn=0.0, u_wall=(0.0, 0.0), accom=(0.0, 0.0))
+    e = p.lat.e.astype(int)
+    base = oracle.init_fields(p, np.ones((Ny, Nx)))
+    for b in range(p.lat.Q):
+        if e[b, 1] >= 0:
+            continue
+        m = -e[b, 1]
+        for r in range(m):                       # rows whose e_b step crosses the wall
+            f = base.copy()
+            f[b, r, x0] += bump
+            oracle.run(p, f, 1)
+            d = f - base
+            layer = m - r - 1
+            xg = (x0 + e[b, 0]) % Nx
+            a = [i for i in range(p.lat.Q) if e[i, 0] == e[b, 0] and e[i, 1] == m][0]
+            tj = -1 - layer + m
+            tx = (xg + e[b, 0]) % Nx
+            assert abs(d[a, tj, tx] - bump) < 1e-13, (name, b, r)
+            d[a, tj, tx] = 0.0
+            assert np.max(np.abs(d)) < 1e-13, (name, b, r)
+
+
+@pytest.mark.parametrize("name", ["D2Q17", "D2Q25", "D2Q37"])
 def test_uniform_flow_is_fixed_point(oracle, name):
     # both walls move with the gas: the diffuse wall re-emits exactly g^eq(U, T_w)
     order, thermal = (4, True) if name == "D2Q37" else (2, False)
