@@ -13,6 +13,10 @@ import pytest
 import test_oracle_pins as pins
 
 MUTATIONS = {
+    # viscosity law ignoring the temperature exponent (mu = T always)
+    "mu_exponent_ignored": (
+        "double mu = pow(T, P->mu_exp);", "double mu = T;",
+        lambda o: pins.test_stress_follows_the_viscosity_law_across_a_temperature_gradient(o)),
     # specular partner taken from the neighbouring ghost column
     "specular_partner_shifted": (
         "fspec[a * N + l] = ext[b * eplane + (long)(grow + N) * Nx + xw];",

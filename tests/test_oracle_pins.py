@@ -504,10 +504,10 @@ def test_maxwell_slip_length(oracle):
 
 # ---- stress and heat flux (Sec. II: f recovered from f~) ------------------------
 
-def _steady_couette(oracle, name, Ny, Kn, Uw):
+def _steady_couette(oracle, name, Ny, Kn, Uw, **kw):
     order, thermal = (4, True) if name == "D2Q37" else (2, False)
     p = oracle.Problem(lattice=name, Nx=1, Ny=Ny, eq_order=order, thermal=thermal, Kn=Kn,
-                       u_wall=(-Uw, Uw))
+                       u_wall=(-Uw, Uw), **kw)
     f = oracle.init_fields(p, np.ones((Ny, 1)))
     ok, _, _ = oracle.run_to_residual(p, f, 1e-12, 800000, 100)
     assert ok
@@ -555,6 +555,24 @@ def test_stress_newtonian_limit(oracle, name):
     # steady momentum balance: the shear stress is uniform across the bulk (the
     # wall rows carry a discretisation error that shrinks with the grid)
     assert np.ptp(sxy[mid]) < 1e-4 * np.max(np.abs(sxy))
+
+
+def test_stress_follows_the_viscosity_law_across_a_temperature_gradient(oracle):
+    # tau of Sec. II with mu = T^0.7 (the option of a temperature-dependent
+    # viscosity) between walls at 1.1 and 0.9: the Newtonian relation
+    # sigma_xy = -sqrt(2/pi) Kn T^0.7 du/dy holds at every bulk row with its own
+    # T, while mu = T (or T^0.7 misapplied) would miss it by the T variation
+    Ny, Kn, Uw, m = 40, 0.01, 0.1, 0.7
+    p, f = _steady_couette(oracle, "D2Q37", Ny, Kn, Uw, mu_exp=m, T_wall=(1.1, 0.9))
+    _, ux, _, T = [a[:, 0] for a in oracle.macros(p, f)]
+    sxy = oracle.fluxes(p, f)[1][:, 0]
+    y = (np.arange(Ny) + 0.5) / Ny
+    mid = slice(Ny // 4, 3 * Ny // 4)
+    assert np.ptp(T[mid]) > 0.05                 # the law is tested across a real gradient
+    ratio = sxy / (-math.sqrt(2 / math.pi) * Kn * T ** m * np.gradient(ux, y))
+    assert np.max(np.abs(ratio[mid] - 1)) < 3e-3, ratio[mid]
+    wrong = sxy / (-math.sqrt(2 / math.pi) * Kn * T * np.gradient(ux, y))
+    assert np.max(np.abs(wrong[mid] - 1)) > 1e-2
 
 
 def test_heat_flux_fourier_limit_and_energy_balance(oracle):
