@@ -4,8 +4,9 @@
  * condition for high-order lattice Boltzmann model with streaming-collision
  * mechanism" (arXiv:1209.5201).
  *
- * TEST INFRASTRUCTURE ONLY.  The test-suite, the smoke check and the CPU
- * baseline leg of the benchmark are the only code allowed to load it.  It
+ * TEST INFRASTRUCTURE ONLY.  The test-suite, the smoke check, and the CPU
+ * baseline leg and reference arm of the benchmark are the only code allowed
+ * to load it.  It
  * shares no code, header, table or helper with the CUDA library: it takes the
  * lattice tables as plain arrays from its own Python generator, and it
  * follows the paper's push / ghost-layer description step by step, with no
