@@ -54,3 +54,22 @@ def test_serving_workload_recipe():
     assert abs(below - 0.5) < 0.05
     again = inputs.serving_requests(2000, seed=11, rate=200.0)
     assert [(r.lattice, r.Ny, r.Kn) for r in reqs] == [(r.lattice, r.Ny, r.Kn) for r in again]
+
+
+def test_batched_workload_recipe():
+    insts = inputs.batched_instances(256, seed=7)
+    assert len(insts) == 256 and {i.lattice for i in insts} == set(inputs.LATTICES)
+    assert all(32 <= i.Ny <= 2048 and 0.01 <= i.Kn <= 1.0 and 0.05 <= i.U_w <= 0.3 for i in insts)
+    for i in insts:
+        # the wall temperature is drawn for every instance but only the thermal
+        # lattice uses it (isothermal lattices keep T_w = 1)
+        if i.thermal:
+            assert 0.9 <= i.T_w <= 1.1 and i.lattice == "D2Q37" and i.eq_order == 4
+        else:
+            assert i.T_w == 1.0 and i.eq_order == 2
+    # Kn log-uniform: about half below the geometric mean of the range
+    below = sum(i.Kn < 0.1 for i in insts) / len(insts)
+    assert abs(below - 0.5) < 0.1
+    again = inputs.batched_instances(256, seed=7)
+    assert [(i.lattice, i.Ny, i.Kn, i.T_w) for i in insts] == \
+        [(i.lattice, i.Ny, i.Kn, i.T_w) for i in again]
