@@ -38,3 +38,27 @@ def test_no_gpu_no_solver():
         lbm.Solver(lbm.Config(lattice="D2Q25", Nx=1, Ny=64, Kn=0.1, precision="fp64"))
     with pytest.raises(Exception):
         lbm.Server(mem_budget_bytes=1 << 20, max_slots=4)
+
+
+def test_no_gpu_c_abi_reports_cuda_errors():
+    # the C ABI itself, with no stream from PyTorch: an error status and no
+    # handle, never a host computation
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes as C
+    import __graft_entry__ as ge
+    ge.build_library()
+    from paper_1209_5201_gb300 import lbm
+    lib = lbm.load()
+    cfg = lbm.lbm_server_cfg_default()
+    h = C.c_void_p()
+    assert lib.lbm_server_create(C.byref(cfg), None, C.byref(h)) == lbm.LBM_ECUDA and not h.value
+    lat = lbm.lbm_lattice_create(25)
+    try:
+        s = C.c_void_p()
+        p = lbm.lbm_params_default()
+        assert lib.lbm_solver_create(lat, C.byref(p), None, None, 0, C.byref(s)) == lbm.LBM_ECUDA
+        assert not s.value
+    finally:
+        lbm.lbm_lattice_destroy(lat)
