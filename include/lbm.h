@@ -234,9 +234,13 @@ typedef struct lbm_stats {
 /* Synchronous (one reduction over the state). */
 int lbm_solver_stats(lbm_solver *s, lbm_stats *st);
 
-/* Step-kernel selection.  LBM_KERNEL_DIRECT: one thread per cell, populations
- * pulled straight from global memory; its variants differ in block width,
- * register cap and store cache policy.  LBM_KERNEL_STAGED: persistent tile
+/* Step-kernel selection.  LBM_KERNEL_DIRECT: populations pulled straight
+ * from global memory; variants 0..6 update one cell per thread and differ in
+ * block width, register cap, rows per block and store cache policy; with FP32
+ * and BF16DEV storage variants 7..9 update two adjacent cells per thread with
+ * packed FP32x2 arithmetic, paired loads and stores (and, for BF16DEV, one
+ * stochastic-rounding conversion per pair of values), with results equal bit
+ * for bit to the one-cell variants.  LBM_KERNEL_STAGED: persistent tile
  * kernel whose producer warp stages each velocity's shifted source window
  * (tile plus the +-3-cell halo, rounded to 16 bytes in x) into shared memory
  * with TMA; `variant` picks one of the compiled tile shapes, 0 <= variant <
@@ -244,6 +248,19 @@ int lbm_solver_stats(lbm_solver *s, lbm_stats *st);
  * another.  Both compute the
  * same step (Eq. (5) with Eq. (12)).  Errors: LBM_EINVAL. */
 int lbm_solver_set_kernel(lbm_solver *s, int32_t kernel, int32_t variant);
+
+/* Limit, in nanoseconds of the GPU's global timer, of each bounded wait of
+ * the staged kernel (its mbarrier waits between the producer warp and the
+ * consumer warps; default 2 s).  The paper has no counterpart: it is the
+ * library's failure detection.  A wait that runs out records a device flag,
+ * the CTA stops taking tiles and its producer waits for its copies in flight
+ * (with a fixed 2 s limit of its own) before the CTA exits; the next
+ * lbm_solver_sync (or a synchronous call) returns LBM_ETIMEOUT and clears the
+ * flag.  The state of that step is then incomplete: reload one (set_state,
+ * set_f or init) before stepping on.  0 makes every such wait give up at
+ * once, met or not (the failure path on demand; the drain before exit still
+ * waits).  The other kernels have no waits.  Errors: LBM_EINVAL. */
+int lbm_solver_set_wait_limit(lbm_solver *s, uint64_t ns);
 /* Number of compiled variants of `kernel` (DIRECT or STAGED) for this
  * solver's precision.  Errors: LBM_EINVAL. */
 int lbm_solver_variant_count(lbm_solver *s, int32_t kernel, int32_t *n);
@@ -285,9 +302,13 @@ int lbm_solver_wall_mass(lbm_solver *s, double *m_in);
  * libraries from allocating on their own.  Its scratch (1024 block partials
  * of 5 FP64 sums plus the totals, 41 KB) is a file-scope device array of the
  * library, created on every GPU that loads the library and kept until the
- * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress, with that device current); make this first
- * call before any stream capture begins.  All calls on a device share the
+ * process exits.  The first call in a CUDA context looks up that array's
+ * device address there (cudaGetSymbolAddress); the address is cached with the
+ * context's unique ID (cuCtxGetId), so a call in another context - one the
+ * caller created and made current, or the primary context re-created after
+ * cudaDeviceReset - looks it up again instead of using an address of a
+ * context that no longer holds it.  Make the first call in each context
+ * before any stream capture begins.  All calls on a device share the
  * array and it keeps the last call's contents: calls whose kernels overlap on
  * the GPU (different streams, no ordering between them) race and return
  * garbage; calls ordered on one stream are safe.
@@ -302,14 +323,21 @@ int lbm_residual_noalloc(const double *ux, const double *T, double *ux_prev, dou
  * lattice, height, Kn (or tau), wall speeds and temperatures, FP32 storage
  * and arithmetic, FP64 wall-flux and residual reductions.  The solve starts
  * from rest (rho = 1, u = 0, T = 1) and stops when the extrapolated distance
- * to the steady state, res q / (1 - q), is at most `tol`: res is the
- * relative change over one check, max(||u_x - u_x'|| / ||u_x||, thermal:
- * ||T - T'|| / ||T||), and q the ratio of successive residuals; checks run
- * about four times per e-folding time of the slowest shear mode,
- * 0.127 Ny r / Kn steps.  A residual that has stopped improving for 8 checks
- * at no more than tol / 20 also counts as converged (the FP32 round-off
- * floor); one that has not improved for 50 checks above that ends the request
- * with LBM_ENOTCONVERGED. */
+ * to the steady state, res q / (1 - q), is at most `tol` at two checks in a
+ * row: res is the largest change of the column's fields over one check in
+ * the units of the requested accuracy - over the column's 32-row blocks, the
+ * largest change of a block's mean u_x divided by U = max |u_wall| and, when
+ * thermal, of a block's mean T (u_x and T compared as FP32 values) - and q
+ * the ratio of successive changes; so `tol` is the accuracy asked for, the
+ * L-inf distance of u_x / U (and of T) from the steady state, e.g. 1e-5.
+ * The stored FP32 values are rounded stochastically (unbiased), so that the
+ * steady state carries no systematic round-off.
+ * (This differs from lbm_solver_run_to_residual's relative L2 residual,
+ * which keeps the solver's definition.)  Checks run about four times per
+ * e-folding time of the slowest shear mode, 0.127 Ny r / Kn steps.  A change
+ * that has stopped shrinking for 8 checks at no more than tol / 20 also
+ * counts as converged (the FP32 round-off floor); one that has not shrunk for
+ * 50 checks above that ends the request with LBM_ENOTCONVERGED. */
 typedef struct lbm_request {
     int32_t lattice;      /* LBM_LATTICE_*                                     */
     int32_t Ny;           /* rows, 6 <= Ny <= 8192                             */
@@ -320,7 +348,8 @@ typedef struct lbm_request {
     double mu_exp;        /* mu = T^mu_exp                                     */
     double u_wall[2];     /* bottom, top wall x-velocity                       */
     double T_wall[2];     /* bottom, top wall temperature (thermal only)       */
-    double tol;           /* target distance to the steady state, e.g. 1e-5    */
+    double tol;           /* target L-inf distance to the steady state of u_x / U
+                             (and T), e.g. 1e-5                                */
     int64_t max_steps;    /* give up after this many steps                     */
     uint64_t tag;         /* caller's tag, returned in the result              */
     double accom[2];      /* wall accommodation, as in lbm_params (1: diffuse) */
@@ -332,8 +361,9 @@ typedef struct lbm_result {
                              stagnation), LBM_ENONFINITE                       */
     int32_t Ny;
     int64_t steps;
-    double residual;      /* last relative change over one check              */
-    double err_est;       /* extrapolated distance to the steady state        */
+    double residual;      /* last change over one check (units of tol)        */
+    double err_est;       /* extrapolated distance to the steady state (units
+                             of tol)                                         */
     double mass;          /* sum of rho over the column at the last check     */
     double t_submit, t_admit, t_done;   /* seconds since server creation      */
 } lbm_result;

@@ -181,6 +181,7 @@ void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int p
     k.Ny = p.Ny;
     k.pitch = pitch;
     k.plane = (long long)p.Ny * pitch;
+    k.wait_ns = kDefaultWaitNs;
     k.thermal = p.thermal;
     k.eq_order = p.eq_order;
     k.const_tau = p.tau > 0;
@@ -820,6 +821,19 @@ int lbm_solver_set_kernel(lbm_solver *h, int32_t kernel, int32_t variant) {
     if (variant < 0 || variant >= nv) { set_error("bad variant"); return LBM_EINVAL; }
     s.p.kernel = kernel;
     s.variant = variant;
+    return LBM_OK;
+}
+
+int lbm_solver_set_wait_limit(lbm_solver *h, uint64_t ns) {
+    if (!h) { set_error("NULL solver"); return LBM_EINVAL; }
+    SolverImpl &s = h->s;
+    s.kf.wait_ns = s.kd.wait_ns = (unsigned long long)ns;
+    // the replayed step graph holds the kernel constants of its capture
+    if (s.step_graph) {
+        CU(cudaStreamSynchronize(s.stream));
+        cudaGraphExecDestroy(s.step_graph);
+        s.step_graph = nullptr;
+    }
     return LBM_OK;
 }
 

@@ -37,7 +37,7 @@ struct SlotDesc {
     long long prev_off;       // element offset of the previous-check u_x, T
     double tol;               // target of the extrapolated distance to steady state
     long long max_steps;
-    double T_ref;             // mean wall temperature
+    double u_ref;             // velocity scale of the change measure: max |u_wall|
     // incoming terms of Eq. (12)'s numerator, built on the host: wall w (0
     // bottom, 1 top), term l < nterm is velocity term_a[w][l] at distance
     // term_row[w][l] from the wall
@@ -54,10 +54,11 @@ struct SlotDesc {
 
 struct SlotStatus {
     long long steps;          // steps run since admission
-    double res;               // last residual (relative change over one check)
-    double res_prev;          // residual of the check before
-    double err_est;           // extrapolated distance to the steady state
-    double best_res;          // smallest residual so far
+    double res;               // last change over one check: max(L-inf |du_x| / u_ref,
+                              // thermal: L-inf |dT|)
+    double res_prev;          // change over the check before
+    double err_est;           // extrapolated distance to the steady state (same units)
+    double best_res;          // smallest change so far
     double mass;              // sum of rho (FP64) at the last check
     int state;                // kSlot*
     int checks;

@@ -28,7 +28,7 @@ __device__ __forceinline__ void equilibrium_all(C rho, C drho, C ux, C uy, C T,
     // A collision with omega = 1 from f = 0 leaves exactly rho g^eq.
     Collision<Q, C, SHIFT> col;
     const C u2 = ux * ux + uy * uy;
-    col.omc = C(0);
+    col.set_omega(C(1));
     col.sx = k.r * ux;
     col.sy = k.r * uy;
     col.rho = rho;

@@ -72,7 +72,7 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
     auto load = [&](int a, int row, int xp) -> C {
         const long long idx = (long long)row * k.pitch + xp;
         C v = to_c(fin[(long long)a * k.plane + idx]);
-        if constexpr (Store<PREC>::dev) v += k.w[a] * rin[idx];
+        if constexpr (Store<PREC>::dev) v = dev_to_f(v, k.w[a], rin[idx]);
         return v;
     };
 
@@ -142,7 +142,7 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
     else if (k.mu_is_one || !k.thermal) taul = k.K * inv;
     else taul = k.K * inv * pow(T, k.mu_m1);
     const C om = C(1) / (taul + C(0.5));
-    col.omc = C(1) - om;
+    col.set_omega(om);
     col.sx = k.r * ux;
     col.sy = k.r * uy;
     // Eq. (4) coefficients: the c2-independent factors in every lane, those
@@ -185,8 +185,8 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
         const C s2 = sv * sv;
         const C E = A0v[i] + s2 * (A2v[i] + col.A4 * s2);
         const C O = sv * (A1v[i] + col.A3 * s2);
-        C v = col.omc * f + cwv[i] * (E + O);
-        if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
+        C v = col.relax(f, cwv[i] * (E + O));
+        if constexpr (Store<PREC>::dev) v = f_to_dev(v, k.w[a], col.rho);
         store_with_images<S>(fout + (long long)a * k.plane + (long long)j * k.pitch, x, k.Nx,
                              store_rounded<S>(v, sr_bits(hcell, a)));
     };

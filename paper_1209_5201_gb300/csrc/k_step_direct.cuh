@@ -20,7 +20,8 @@ namespace lbm {
 // M_in(x') for x' = x0 - 3 + t, t in [0, BX + 6): post-collision populations
 // of the N rows next to `wall` that stream into ghost column x' (Sec. III:
 // incoming at layer l when e.n < -l; summed over all layers, Eq. (12)).
-template <int Q, int PREC, int BX>
+// BX: the block's columns; NT: its threads.
+template <int Q, int PREC, int BX, int NT = BX>
 __device__ __forceinline__ void wall_prologue(const typename Store<PREC>::S *__restrict__ fin,
                                               const float *__restrict__ rin,
                                               const KConsts<typename Store<PREC>::C> &k,
@@ -28,7 +29,7 @@ __device__ __forceinline__ void wall_prologue(const typename Store<PREC>::S *__r
     using L = Lat<Q>;
     // ghost columns x0 - 3 .. x0 + active + 2 (fewer than BX when Nx is small)
     const int ncols = min(BX, k.Nx - x0) + 6;
-    for (int t = threadIdx.x; t < ncols; t += BX) {
+    for (int t = threadIdx.x; t < ncols; t += NT) {
         const int xw = wrap(x0 - 3 + t, k.Nx);
         double m = 0.0;
 #pragma unroll
@@ -74,7 +75,7 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
         } else {
             C v = to_c(src[k.off_src[a]]);
             if constexpr (Store<PREC>::dev)
-                v += k.w[a] * rin[cell - L::ey(a) * k.pitch - L::ex(a)];
+                v = dev_to_f(v, k.w[a], rin[cell - L::ey(a) * k.pitch - L::ex(a)]);
             f[a] = v;
         }
     }
@@ -119,7 +120,7 @@ __device__ __forceinline__ void step_cell(const typename Store<PREC>::S *__restr
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             C v = o[a];
-            if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
+            if constexpr (Store<PREC>::dev) v = f_to_dev(v, k.w[a], col.rho);
             const S sv = store_rounded<S>(v, sr_bits(hcell, a));
             if (CS) store_cs<S>(dst + k.off_dst[a], sv);
             else dst[k.off_dst[a]] = sv;
@@ -130,7 +131,7 @@ __device__ __forceinline__ void step_cell(const typename Store<PREC>::S *__restr
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             C v = o[a];
-            if constexpr (Store<PREC>::dev) v -= k.w[a] * col.rho;
+            if constexpr (Store<PREC>::dev) v = f_to_dev(v, k.w[a], col.rho);
             store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx,
                                  store_rounded<S>(v, sr_bits(hcell, a)));
         }

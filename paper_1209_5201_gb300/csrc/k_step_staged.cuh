@@ -12,9 +12,10 @@
 // the buffer, collide and write the Q post-collision values with coalesced
 // stores.  BF16DEV also stages the FP32 density plane with its +-3-row halo.
 //
-// Every mbarrier wait is bounded: on expiry the thread records an error code
-// in *err and the CTA stops taking tiles; the producer then waits (bounded)
-// for its copies in flight before exiting.
+// Every mbarrier wait is bounded (KConsts::wait_ns, 2 s unless the host sets
+// another limit): on expiry the thread records an error code in *err and the
+// CTA stops taking tiles; the producer then waits for its copies in flight
+// before exiting, with a fixed 2 s limit of its own.
 #pragma once
 
 #include <cuda.h>
@@ -24,7 +25,7 @@
 namespace lbm {
 
 constexpr int kStagedErrTimeout = 1;
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait at most
+constexpr unsigned long long kDrainWaitNs = kDefaultWaitNs;   // copies in flight at exit
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -56,14 +57,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait: false when kWaitNs ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait: false when limit_ns ran out; a zero limit gives up at once,
+// whether or not the phase has completed (the failure path, on demand)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns) {
+    if (limit_ns == 0) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -155,7 +159,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+                if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, k.wait_ns)) {
                     atomicOr(err, kStagedErrTimeout);
                     *(volatile int *)stop = 1;
                     break;
@@ -171,9 +175,11 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                     tma_load_2d(st + Q * Cfg::kPlaneStride, &tm_r, &full[s], x0, j0 - 3);
             }
             // drain: every issued stage must have landed before the CTA exits
+            // (its own fixed limit, whatever the limit of the other waits)
             const int issued = it;
             for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i)
-                mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u);
+                if (!mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u, kDrainWaitNs))
+                    atomicOr(err, kStagedErrTimeout);
         }
         return;
     }
@@ -183,7 +189,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
     uint32_t wphase = 0;
     auto wall_sync = [&]() -> bool {
         mbar_arrive(wbar);
-        const bool ok = mbar_wait(wbar, wphase);
+        const bool ok = mbar_wait(wbar, wphase, k.wait_ns);
         wphase ^= 1u;
         return ok;
     };
@@ -231,7 +237,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                 break;
             }
         }
-        if (!mbar_wait(&full[s], ph)) {
+        if (!mbar_wait(&full[s], ph, k.wait_ns)) {
             atomicOr(err, kStagedErrTimeout);
             *(volatile int *)stop = 1;
             break;
@@ -259,7 +265,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                     const S *pl = (const S *)(st + a * Cfg::kPlaneStride);
                     C v = to_c(pl[kr * Cfg::kW + i + kPadL - L::ex(a)]);
                     if constexpr (Cfg::kDev)
-                        v += k.w[a] * srho[(kr + 3 - L::ey(a)) * Cfg::kW + i + kPadL - L::ex(a)];
+                        v = dev_to_f(v, k.w[a], srho[(kr + 3 - L::ey(a)) * Cfg::kW + i + kPadL - L::ex(a)]);
                     fv[q][a] = v;
                 }
             }
@@ -286,7 +292,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 C v = o[a];
-                if constexpr (Cfg::kDev) v -= k.w[a] * col.rho;
+                if constexpr (Cfg::kDev) v = f_to_dev(v, k.w[a], col.rho);
                 store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx,
                                      store_rounded<S>(v, sr_bits(hcell, a)));
             }

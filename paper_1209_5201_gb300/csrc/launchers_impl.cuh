@@ -5,6 +5,7 @@
 #include "k_fluxes.cuh"
 #include "k_step_cellwarp.cuh"
 #include "k_step_direct.cuh"
+#include "k_step_pair.cuh"
 #include "k_step_staged.cuh"
 #include "launchers.h"
 
@@ -54,9 +55,40 @@ int launch_direct(SolverImpl &s, int src, int dst) {
     return (int)cudaGetLastError();
 }
 
+// ---- two-cells-per-thread variants {BX, MINB} (FP32 and BF16DEV storage),
+// numbered after the direct ones -----------------------------------------------
+struct PairVariants {
+    static constexpr int n = 3;
+    static constexpr int v[n][2] = {{64, 0}, {128, 0}, {64, 8}};
+};
+
+template <int Q, int PREC, int BX, int MINB>
+int launch_pair(SolverImpl &s, int src, int dst) {
+    using S = typename Store<PREC>::S;
+    const auto &k = Consts<PREC>::get(s);
+    dim3 grid((s.p.Nx + 2 * BX - 1) / (2 * BX), s.p.Ny);
+    k_step_pair<Q, PREC, BX, MINB><<<grid, BX, 0, s.stream>>>(
+        (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
+    return (int)cudaGetLastError();
+}
+
 template <int PREC>
 int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
     using V = DirectVariants;
+    if constexpr (PREC != LBM_FP64) {
+        using P = PairVariants;
+        switch (variant - V::n) {
+#define LBM_PAIR_CASE(I)                                                                   \
+        case I:                                                                            \
+            LBM_DISPATCH_Q(s.L.Q, return (launch_pair<QQ, PREC, P::v[I][0], P::v[I][1]>(s, src, dst))); \
+            break;
+            LBM_PAIR_CASE(0)
+            LBM_PAIR_CASE(1)
+            LBM_PAIR_CASE(2)
+#undef LBM_PAIR_CASE
+        default: break;
+        }
+    }
 #define LBM_DIRECT_CASE(I)                                                                 \
     case I:                                                                                \
         LBM_DISPATCH_Q(s.L.Q, return (launch_direct<QQ, PREC, V::v[I][0], V::v[I][1],       \
@@ -77,7 +109,9 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
 }
 
 template <int PREC>
-int Launch<PREC>::direct_variants() { return DirectVariants::n; }
+int Launch<PREC>::direct_variants() {
+    return DirectVariants::n + (PREC == LBM_FP64 ? 0 : PairVariants::n);
+}
 
 template <int PREC>
 int Launch<PREC>::step_cellwarp(SolverImpl &s, int src, int dst) {

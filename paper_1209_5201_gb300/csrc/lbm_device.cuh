@@ -98,6 +98,34 @@ template <> __device__ __forceinline__ __nv_bfloat16 store_rounded<__nv_bfloat16
 template <class S> __device__ __forceinline__ S store_rounded(double v, uint32_t);
 template <> __device__ __forceinline__ double store_rounded<double>(double v, uint32_t) { return v; }
 
+// ---- stochastic rounding of FP32 results (batched path) -----------------------
+// f + t rounded to FP32 stochastically, from 23 uniform random bits: a uniform
+// dither of one unit in the last place U of the round-to-nearest sum, in
+// [-U/2, U/2), is added to the small term before the final addition, so the
+// result is the lower or the upper FP32 neighbour of the exact sum with
+// probabilities that make it unbiased (Connolly, Higham & Mary, SIAM J. Sci.
+// Comput. 43 (2021): stochastic rounding, mode 1).  Round-to-nearest leaves
+// the same round-off at every step of a steady state, a constant forcing
+// that the slowest relaxation time amplifies (up to ~1e-4 U_w in u_x for tall
+// or dense columns); stochastic rounding makes it zero-mean noise.  t + dither
+// is itself rounded on t's grid, which keeps the rounding unbiased to within
+// ~ulp(t) / 2 of a unit: exact where |t| << |f + t|, the case of a long
+// relaxation time, where the amplification is largest.
+__device__ __forceinline__ float add_sr(float f, float t, uint32_t r23) {
+    const float s = f + t;
+    // exponent bits of ulp(s) = 2^(E - 23) for s in [2^E, 2^(E+1)); clamped to
+    // the smallest normal for |s| < 2^-103
+    const uint32_t e = max(__float_as_uint(s) & 0x7f800000u, 24u << 23) - (23u << 23);
+    const float U = __uint_as_float(e);
+    const float m = __uint_as_float(e | r23);          // uniform in [U, 2U)
+    return f + (t + fmaf(-1.5f, U, m));
+}
+// 23 random bits of velocity a from the cell's hash (top bits of a product
+// with an odd multiplier that depends on a)
+__device__ __forceinline__ uint32_t sr_bits23(uint32_t hcell, int a) {
+    return (hcell * (0x9E3779B9u * (2u * (uint32_t)a + 1u))) >> 9;
+}
+
 // Step count of this launch's source buffer; block 0 writes the count of the
 // destination buffer (read by the next step only).
 template <class C>
@@ -110,10 +138,86 @@ __device__ __forceinline__ uint32_t step_count(const void *fin, const KConsts<C>
     return n;
 }
 
+// BF16DEV: f = d + w rho on the pull side and d = f - w rho on the store
+// side, each with one rounding (an explicit FMA in every kernel, so that all
+// of them round alike)
+__device__ __forceinline__ float dev_to_f(float d, float w, float rho) { return __fmaf_rn(w, rho, d); }
+__device__ __forceinline__ float f_to_dev(float f, float w, float rho) { return __fmaf_rn(-w, rho, f); }
+
 __device__ __forceinline__ int wrap(int v, int n) {
     int m = v % n;
     return m < 0 ? m + n : m;
 }
+
+// ---- explicit arithmetic on one cell (float, double) or two (float2) ---------
+// The collision below is written with explicit fma / mul / add / sub, which
+// the compiler never contracts or reorders, so a kernel that updates one cell
+// per thread (V = float or double) and one that updates two adjacent cells
+// per thread with Blackwell's packed FP32x2 instructions (V = float2: one
+// FFMA2 / FMUL2 / FADD2 does the same operation for both cells) execute the
+// same roundings: their results agree bit for bit.
+template <class V> struct Ar;
+template <> struct Ar<float> {
+    using S = float;
+    __device__ __forceinline__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ __forceinline__ static float rcp(float a) { return __frcp_rn(a); }
+    __device__ __forceinline__ static float pw(float a, float e) { return powf(a, e); }
+    __device__ __forceinline__ static float bc(float c) { return c; }
+};
+template <> struct Ar<double> {
+    using S = double;
+    __device__ __forceinline__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ __forceinline__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ __forceinline__ static double rcp(double a) { return __drcp_rn(a); }
+    __device__ __forceinline__ static double pw(double a, double e) { return pow(a, e); }
+    __device__ __forceinline__ static double bc(double c) { return c; }
+};
+template <> struct Ar<float2> {
+    using S = float;
+    __device__ __forceinline__ static float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    __device__ __forceinline__ static float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    __device__ __forceinline__ static float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    // a - b = fma(b, -1, a), rounded once like __fsub_rn
+    __device__ __forceinline__ static float2 sub(float2 a, float2 b) {
+        return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+    }
+    __device__ __forceinline__ static float2 rcp(float2 a) {
+        return make_float2(__frcp_rn(a.x), __frcp_rn(a.y));
+    }
+    __device__ __forceinline__ static float2 pw(float2 a, float e) {
+        return make_float2(powf(a.x, e), powf(a.y, e));
+    }
+    __device__ __forceinline__ static float2 bc(float c) { return make_float2(c, c); }
+};
+
+// compile-time loop a = A, A + 1, ..., N - 1
+template <int A, int N>
+struct StaticFor {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&fn) {
+        if constexpr (A < N) {
+            fn(std::integral_constant<int, A>{});
+            StaticFor<A + 1, N>::run(fn);
+        }
+    }
+};
+
+// compile-time loop over the velocity pairs (a = 1, 3, 5, ...)
+template <int A, int Q>
+struct PairLoop {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&fn) {
+        if constexpr (A < Q) {
+            fn(std::integral_constant<int, A>{});
+            PairLoop<A + 2, Q>::run(fn);
+        }
+    }
+};
 
 // ---- Eq. (3)-(5): moments, relaxation factor, equilibrium coefficients --------
 // g_a^eq of Eq. (4) for a velocity of shell k, with s = c_a . u, written as
@@ -129,114 +233,248 @@ __device__ __forceinline__ int wrap(int v, int n) {
 // rho = 1 + sum d, and w (rho g - 1) = rho w (g - 1 + drho / rho) replaces
 // rho w g, i.e. A0 - 1 + drho / rho replaces A0 (no cancellation: the
 // constant 1 of A0 is never formed).
-template <int Q, class C, bool SHIFT = false>
+//
+// Relaxation (Eq. (5)): f~* = f~ - omega (f~ - rho g) = f~ + (omega rho g - omega f~).
+// In FP32 the factor 1 - omega is never formed: for a long relaxation time
+// (omega ~ 1e-4 .. 1e-3 in tall, rarefied columns) fl(1 - omega) carries an
+// absolute round-off of up to 2^-25, i.e. a systematic relative error of up to
+// 2^-25 / omega in the effective omega of the f~ term, which moves the FP32
+// steady state by about that relative amount.  FP64 keeps the form
+// (1 - omega) f~ + omega rho g.
+//
+// V: float or double (one cell), float2 (two cells, packed FP32x2).
+template <int Q, class V, bool SHIFT = false>
 struct Collision {
     using L = Lat<Q>;
-    C omc;                  // 1 - omega
-    C cw[L::NSH];           // omega rho w_k
-    C A0[L::NSH], A1[L::NSH], A2[L::NSH];
-    C A3, A4;
-    C sx, sy;               // r u: s_a = e_ax sx + e_ay sy
-    C rho;
+    using O = Ar<V>;
+    using C = typename O::S;                // scalar type of the constants
+    static constexpr bool kExactOmega = sizeof(C) == 4;
+    V om;                   // omega
+    V nom;                  // -omega (FP32)
+    V omc;                  // 1 - omega (FP64)
+    V cw[L::NSH];           // omega rho w_k
+    V A0[L::NSH], A1[L::NSH], A2[L::NSH];
+    V A3, A4;
+    V sx, sy;               // r u: s_a = e_ax sx + e_ay sy
+    V rho;
 
-    __device__ __forceinline__ void setup(const C (&f)[Q], const KConsts<C> &k) {
+    __device__ __forceinline__ void setup(const V (&f)[Q], const KConsts<C> &k) {
         // moments from the sums and differences of opposite pairs
-        C r0 = f[0], jx = 0, jy = 0;
+        V r0 = f[0], jx = O::bc(C(0)), jy = O::bc(C(0));
 #pragma unroll
         for (int a = 1; a < Q; a += 2) {
-            const C sum = f[a] + f[a + 1], dif = f[a] - f[a + 1];
-            r0 += sum;
-            if (L::ex(a) == 1) jx += dif;
-            else if (L::ex(a) == -1) jx -= dif;
-            else if (L::ex(a) != 0) jx += C(L::ex(a)) * dif;
-            if (L::ey(a) == 1) jy += dif;
-            else if (L::ey(a) == -1) jy -= dif;
-            else if (L::ey(a) != 0) jy += C(L::ey(a)) * dif;
+            const V sum = O::add(f[a], f[a + 1]), dif = O::sub(f[a], f[a + 1]);
+            r0 = O::add(r0, sum);
+            if (L::ex(a) == 1) jx = O::add(jx, dif);
+            else if (L::ex(a) == -1) jx = O::sub(jx, dif);
+            else if (L::ex(a) != 0) jx = O::fma(O::bc(C(L::ex(a))), dif, jx);
+            if (L::ey(a) == 1) jy = O::add(jy, dif);
+            else if (L::ey(a) == -1) jy = O::sub(jy, dif);
+            else if (L::ey(a) != 0) jy = O::fma(O::bc(C(L::ey(a))), dif, jy);
         }
-        const C drho = r0;
-        rho = SHIFT ? C(1) + r0 : r0;
-        const C inv = C(1) / rho;
-        const C ux = k.r * jx * inv, uy = k.r * jy * inv;
-        const C u2 = ux * ux + uy * uy;
-        C th = 0, T = 1;
+        const V drho = r0;
+        rho = SHIFT ? O::add(O::bc(C(1)), r0) : r0;
+        const V inv = O::rcp(rho);
+        const V ux = O::mul(O::mul(O::bc(k.r), jx), inv);
+        const V uy = O::mul(O::mul(O::bc(k.r), jy), inv);
+        const V u2 = O::fma(ux, ux, O::mul(uy, uy));
+        V th = O::bc(C(0)), T = O::bc(C(1));
         if (k.thermal) {
-            C e2 = C(0);
+            V e2 = O::bc(C(0));
 #pragma unroll
-            for (int a = 1; a < Q; a += 2) e2 += C(L::e2(a)) * (f[a] + f[a + 1]);
+            for (int a = 1; a < Q; a += 2)
+                e2 = O::fma(O::bc(C(L::e2(a))), O::add(f[a], f[a + 1]), e2);
             if (SHIFT) {
                 // deviations: 2 rho theta = (r^2 e2w - 2) + r^2 sum e^2 d - rho u^2
                 // - 2 drho, every term small (no cancellation against 2)
-                th = (k.th0 + k.r2 * e2 - rho * u2 - C(2) * drho) * (C(0.5) * inv);
-                T = C(1) + th;
+                V t = O::fma(O::bc(k.r2), e2, O::bc(k.th0));
+                t = O::sub(t, O::mul(rho, u2));
+                t = O::fma(O::bc(C(-2)), drho, t);
+                th = O::mul(t, O::mul(O::bc(C(0.5)), inv));
+                T = O::add(O::bc(C(1)), th);
             } else {
-                T = (k.r2 * e2 * inv - u2) * C(0.5);
-                th = T - C(1);
+                T = O::mul(O::sub(O::mul(O::mul(O::bc(k.r2), e2), inv), u2), O::bc(C(0.5)));
+                th = O::sub(T, O::bc(C(1)));
             }
         }
-        C taul;
-        if (k.const_tau) taul = k.tau_lat;
-        else if (k.mu_is_one || !k.thermal) taul = k.K * inv;
-        else taul = k.K * inv * pow(T, k.mu_m1);
-        const C om = C(1) / (taul + C(0.5));
-        omc = C(1) - om;
-        sx = k.r * ux;
-        sy = k.r * uy;
-        set_coefficients(u2, th, om * rho, drho * inv, k);
+        V taul;
+        if (k.const_tau) taul = O::bc(k.tau_lat);
+        else if (k.mu_is_one || !k.thermal) taul = O::mul(O::bc(k.K), inv);
+        else taul = O::mul(O::mul(O::bc(k.K), inv), O::pw(T, k.mu_m1));
+        set_omega(O::rcp(O::add(taul, O::bc(C(0.5)))));
+        sx = O::mul(O::bc(k.r), ux);
+        sy = O::mul(O::bc(k.r), uy);
+        set_coefficients(u2, th, O::mul(om, rho), O::mul(drho, inv), k);
     }
 
     // A0 = a00 + a01 c2 + a02 c2^2, A1 = a10 + a11 c2, A2 = a20 + a21 c2: the
     // Eq. (4) coefficients above, collected in powers of c2 (D = 2)
     // orho = omega rho; drr = (rho - 1) / rho (used when SHIFT)
-    __device__ __forceinline__ void set_coefficients(C u2, C th, C orho, C drr,
+    __device__ __forceinline__ void set_coefficients(V u2, V th, V orho, V drr,
                                                      const KConsts<C> &k) {
-        C p[8];
+        V p[8];
         powers(u2, th, drr, k, p);
 #pragma unroll
         for (int s = 0; s < L::NSH; ++s) shell(p, orho, k, s, A0[s], A1[s], A2[s], cw[s]);
     }
     // the c2-independent factors a00, a01, a02, a10, a11, a20, a21 (and A3, A4)
-    __device__ __forceinline__ void powers(C u2, C th, C drr, const KConsts<C> &k, C (&p)[8]) {
+    __device__ __forceinline__ void powers(V u2, V th, V drr, const KConsts<C> &k, V (&p)[8]) {
         const bool o3 = k.eq_order >= 3, o4 = k.eq_order >= 4;
-        C a00 = (SHIFT ? drr : C(1)) - C(0.5) * u2 - th, a01 = C(0.5) * th, a02 = C(0);
-        C a10 = C(1), a11 = C(0), a20 = C(0.5), a21 = C(0);
+        V a00 = O::sub(O::fma(O::bc(C(-0.5)), u2, SHIFT ? drr : O::bc(C(1))), th);
+        V a01 = O::mul(O::bc(C(0.5)), th), a02 = O::bc(C(0));
+        V a10 = O::bc(C(1)), a11 = O::bc(C(0)), a20 = O::bc(C(0.5)), a21 = O::bc(C(0));
         if (o3) {
-            a10 += C(-0.5) * u2 - C(2) * th;
-            a11 = C(0.5) * th;
+            a10 = O::sub(O::fma(O::bc(C(-0.5)), u2, a10), O::mul(O::bc(C(2)), th));
+            a11 = O::mul(O::bc(C(0.5)), th);
         }
         if (o4) {
-            a00 += C(0.125) * u2 * u2 + th * u2 + th * th;
-            a01 += C(-0.25) * th * u2 - th * th;
-            a02 = C(0.125) * th * th;
-            a20 += C(-0.25) * u2 - C(1.5) * th;
-            a21 = C(0.25) * th;
+            a00 = O::fma(O::mul(O::bc(C(0.125)), u2), u2, a00);
+            a00 = O::fma(th, u2, a00);
+            a00 = O::fma(th, th, a00);
+            a01 = O::fma(O::mul(O::bc(C(-0.25)), th), u2, a01);
+            a01 = O::sub(a01, O::mul(th, th));
+            a02 = O::mul(O::mul(O::bc(C(0.125)), th), th);
+            a20 = O::sub(O::fma(O::bc(C(-0.25)), u2, a20), O::mul(O::bc(C(1.5)), th));
+            a21 = O::mul(O::bc(C(0.25)), th);
         }
-        A3 = o3 ? C(1) / C(6) : C(0);
-        A4 = o4 ? C(1) / C(24) : C(0);
+        A3 = O::bc(o3 ? C(1) / C(6) : C(0));
+        A4 = O::bc(o4 ? C(1) / C(24) : C(0));
         p[0] = a00; p[1] = a01; p[2] = a02; p[3] = a10; p[4] = a11; p[5] = a20; p[6] = a21;
-        p[7] = C(0);
+        p[7] = O::bc(C(0));
     }
     // the coefficients of shell s
-    __device__ __forceinline__ static void shell(const C (&p)[8], C orho, const KConsts<C> &k, int s,
-                                                 C &A0s, C &A1s, C &A2s, C &cws) {
-        const C c2 = k.c2sh[s];
-        A0s = (p[2] * c2 + p[1]) * c2 + p[0];
-        A1s = p[4] * c2 + p[3];
-        A2s = p[6] * c2 + p[5];
-        cws = orho * k.wsh[s];
+    __device__ __forceinline__ static void shell(const V (&p)[8], V orho, const KConsts<C> &k, int s,
+                                                 V &A0s, V &A1s, V &A2s, V &cws) {
+        const V c2 = O::bc(k.c2sh[s]);
+        A0s = O::fma(O::fma(p[2], c2, p[1]), c2, p[0]);
+        A1s = O::fma(p[4], c2, p[3]);
+        A2s = O::fma(p[6], c2, p[5]);
+        cws = O::mul(orho, O::bc(k.wsh[s]));
     }
 
-    // post-collision values of the rest velocity and of pair (a, a+1)
-    __device__ __forceinline__ C rest(C f0) const { return omc * f0 + cw[0] * A0[0]; }
+    __device__ __forceinline__ void set_omega(V omega) {
+        om = omega;
+        nom = O::mul(O::bc(C(-1)), omega);
+        omc = O::sub(O::bc(C(1)), omega);
+    }
+    // f + omega (g - f) given the equilibrium term omega rho g = eq
+    __device__ __forceinline__ V relax(V f, V eq) const {
+        if constexpr (kExactOmega) return O::add(f, O::fma(nom, f, eq));
+        else return O::fma(omc, f, eq);
+    }
+    // s_a = c_a . u of velocity A
     template <int A>
-    __device__ __forceinline__ void pair(C fa, C fb, C &oa, C &ob) const {
+    __device__ __forceinline__ V s_of() const {
+        constexpr int ex = L::ex(A), ey = L::ey(A);
+        if constexpr (ex == 0) return O::mul(O::bc(C(ey)), sy);
+        else if constexpr (ey == 0) return O::mul(O::bc(C(ex)), sx);
+        else return O::fma(O::bc(C(ex)), sx, O::mul(O::bc(C(ey)), sy));
+    }
+    // omega rho w g of the pair (A, A+1): the shared even part P and the odd part R
+    template <int A>
+    __device__ __forceinline__ void eq_pair(V &P, V &R) const {
         constexpr int s = L::sh(A);
-        const C sv = C(L::ex(A)) * sx + C(L::ey(A)) * sy;
-        const C s2 = sv * sv;
-        const C E = A0[s] + s2 * (A2[s] + A4 * s2);
-        const C O = sv * (A1[s] + A3 * s2);
-        const C P = cw[s] * E, R = cw[s] * O;
-        oa = omc * fa + (P + R);
-        ob = omc * fb + (P - R);
+        const V sv = s_of<A>();
+        const V s2 = O::mul(sv, sv);
+        const V E = O::fma(s2, O::fma(A4, s2, A2[s]), A0[s]);
+        const V Od = O::mul(sv, O::fma(A3, s2, A1[s]));
+        P = O::mul(cw[s], E);
+        R = O::mul(cw[s], Od);
+    }
+    // post-collision values of the rest velocity and of pair (a, a+1)
+    __device__ __forceinline__ V rest(V f0) const { return relax(f0, O::mul(cw[0], A0[0])); }
+    template <int A>
+    __device__ __forceinline__ void pair(V fa, V fb, V &oa, V &ob) const {
+        V P, R;
+        eq_pair<A>(P, R);
+        oa = relax(fa, O::add(P, R));
+        ob = relax(fb, O::sub(P, R));
+    }
+    // the same with the FP32 result rounded stochastically (add_sr; one cell)
+    __device__ __forceinline__ float relax_sr(float f, float eq, uint32_t r23) const {
+        return add_sr(f, __fmaf_rn(nom, f, eq), r23);
+    }
+    __device__ __forceinline__ float rest_sr(float f0, uint32_t hcell) const {
+        return relax_sr(f0, __fmul_rn(cw[0], A0[0]), sr_bits23(hcell, 0));
+    }
+    template <int A>
+    __device__ __forceinline__ void pair_sr(float fa, float fb, float &oa, float &ob,
+                                            uint32_t hcell) const {
+        float P, R;
+        eq_pair<A>(P, R);
+        oa = relax_sr(fa, __fadd_rn(P, R), sr_bits23(hcell, A));
+        ob = relax_sr(fb, __fsub_rn(P, R), sr_bits23(hcell, A + 1));
+    }
+
+    // Relaxation of one FP32 cell whose increments t_a = omega (rho w g_a - f_a)
+    // conserve mass, momentum and (thermal) energy as exactly as FP32 sums
+    // allow, then added to f_a with stochastic rounding.  In exact arithmetic
+    // the BGK step conserves them (Sec. II: the equilibrium has the cell's rho,
+    // u and T), so the correction below is zero; in FP32 the rounding of rho, u
+    // and T and of the lattice constants leaves each collision a small source
+    // of mass and momentum that is the same at every step of a steady state,
+    // and the conserved quantities are the ones whose modes decay slowest, so
+    // such a source moves the steady state by up to ~1e-5 U_w.  The sums M, Jx,
+    // Jy, E of the increments are removed through the rest velocity (mass) and
+    // the four unit velocities (1,0), (-1,0), (0,1), (0,-1) (velocities 1..4
+    // of every lattice here): -J/2 and +J/2 on the two of an axis (momentum,
+    // no mass or energy), -E/4 on each of the four (energy, no momentum), and
+    // the remaining mass on the rest velocity.
+    __device__ __forceinline__ void relax_conserving_sr(const float (&f)[Q], float (&o)[Q],
+                                                        uint32_t hcell, bool thermal) const {
+        static_assert(L::ex(1) == 1 && L::ey(1) == 0 && L::ex(2) == -1 && L::ey(2) == 0 &&
+                          L::ex(3) == 0 && L::ey(3) == 1 && L::ex(4) == 0 && L::ey(4) == -1,
+                      "velocities 1..4 must be the unit velocities");
+        float M = 0.0f, Jx = 0.0f, Jy = 0.0f, E = 0.0f;
+        float t1 = 0.0f, t2 = 0.0f, t3 = 0.0f, t4 = 0.0f;
+        PairLoop<1, Q>::run([&](auto ic) {
+            constexpr int A = decltype(ic)::value;
+            float P, R;
+            eq_pair<A>(P, R);
+            const float ta = __fmaf_rn(nom, f[A], __fadd_rn(P, R));
+            const float tb = __fmaf_rn(nom, f[A + 1], __fsub_rn(P, R));
+            const float ts = __fadd_rn(ta, tb), td = __fsub_rn(ta, tb);
+            M = __fadd_rn(M, ts);
+            // e(A + 1) = -e(A): the pair's momentum is e(A) (ta - tb)
+            if constexpr (L::ex(A) == 1) Jx = __fadd_rn(Jx, td);
+            else if constexpr (L::ex(A) == -1) Jx = __fsub_rn(Jx, td);
+            else if constexpr (L::ex(A) != 0) Jx = __fmaf_rn(float(L::ex(A)), td, Jx);
+            if constexpr (L::ey(A) == 1) Jy = __fadd_rn(Jy, td);
+            else if constexpr (L::ey(A) == -1) Jy = __fsub_rn(Jy, td);
+            else if constexpr (L::ey(A) != 0) Jy = __fmaf_rn(float(L::ey(A)), td, Jy);
+            if (thermal) E = __fmaf_rn(float(L::e2(A)), ts, E);
+            if constexpr (A == 1) {
+                t1 = ta;
+                t2 = tb;
+            } else if constexpr (A == 3) {
+                t3 = ta;
+                t4 = tb;
+            } else {
+                o[A] = add_sr(f[A], ta, sr_bits23(hcell, A));
+                o[A + 1] = add_sr(f[A + 1], tb, sr_bits23(hcell, A + 1));
+            }
+        });
+        float t0 = __fmaf_rn(nom, f[0], __fmul_rn(cw[0], A0[0]));
+        M = __fadd_rn(M, t0);
+        const float hx = __fmul_rn(0.5f, Jx), hy = __fmul_rn(0.5f, Jy);
+        t1 = __fsub_rn(t1, hx);
+        t2 = __fadd_rn(t2, hx);
+        t3 = __fsub_rn(t3, hy);
+        t4 = __fadd_rn(t4, hy);
+        if (thermal) {
+            const float q = __fmul_rn(0.25f, E);
+            t1 = __fsub_rn(t1, q);
+            t2 = __fsub_rn(t2, q);
+            t3 = __fsub_rn(t3, q);
+            t4 = __fsub_rn(t4, q);
+            M = __fsub_rn(M, E);
+        }
+        t0 = __fsub_rn(t0, M);
+        o[0] = add_sr(f[0], t0, sr_bits23(hcell, 0));
+        o[1] = add_sr(f[1], t1, sr_bits23(hcell, 1));
+        o[2] = add_sr(f[2], t2, sr_bits23(hcell, 2));
+        o[3] = add_sr(f[3], t3, sr_bits23(hcell, 3));
+        o[4] = add_sr(f[4], t4, sr_bits23(hcell, 4));
     }
 };
 
@@ -273,33 +511,9 @@ specular_source(const typename Store<PREC>::S *__restrict__ fin, const float *__
     const int b = k.mirror[a];
     const long long ro = (long long)j * k.pitch + wrap(x - 2 * ex, k.Nx) + kPadL;
     auto v = to_c(fin[(long long)b * k.plane + ro]);
-    if constexpr (Store<PREC>::dev) v += k.w[b] * rin[ro];
+    if constexpr (Store<PREC>::dev) v = dev_to_f(v, k.w[b], rin[ro]);
     return v;
 }
-
-// compile-time loop a = A, A + 1, ..., N - 1
-template <int A, int N>
-struct StaticFor {
-    template <class F>
-    __device__ __forceinline__ static void run(F &&fn) {
-        if constexpr (A < N) {
-            fn(std::integral_constant<int, A>{});
-            StaticFor<A + 1, N>::run(fn);
-        }
-    }
-};
-
-// compile-time loop over the velocity pairs (a = 1, 3, 5, ...)
-template <int A, int Q>
-struct PairLoop {
-    template <class F>
-    __device__ __forceinline__ static void run(F &&fn) {
-        if constexpr (A < Q) {
-            fn(std::integral_constant<int, A>{});
-            PairLoop<A + 2, Q>::run(fn);
-        }
-    }
-};
 
 // Store one population at logical column x of row j, and at every periodic
 // image of x inside the padded row [-kPadL, Nx + kPadL).

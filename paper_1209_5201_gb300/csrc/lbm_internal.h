@@ -20,6 +20,7 @@ constexpr int kMaxQ = 37;
 constexpr int kMaxShells = 8;
 constexpr int kPadL = 4;          // periodic image columns kept left of x = 0
 constexpr long long kCellwarpAutoCells = 4096;   // LBM_KERNEL_AUTO: one warp per cell up to here
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;   // bounded device waits: 2 s
 
 struct LatticeHost {
     int kind;
@@ -67,6 +68,9 @@ struct KConsts {
     // steps done when state buffer b (base f0 for b = 0) is the source
     const void *f0;
     unsigned *sr;
+    // limit of each bounded mbarrier wait of the staged kernel (ns); the
+    // wait for copies in flight before a CTA exits keeps its own fixed limit
+    unsigned long long wait_ns;
 };
 
 // Kernel constants of one solve (Eq. (4)-(5) factors, Eq. (11)-(12) wall

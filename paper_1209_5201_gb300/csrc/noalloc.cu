@@ -5,6 +5,8 @@
 // device array below instead of memory the library or the caller allocates.
 // The array is created when the library is loaded and lives on every GPU
 // that loads it until the process exits.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "k_aux.cuh"
@@ -22,7 +24,48 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocBlocks * kNoAl
 namespace {
 
 std::mutex g_mu;
-double *g_addr[128] = {};                   // device address of the array, per device
+// The array's device address is a property of the CUDA context it was loaded
+// into: a context the caller created and made current, or the primary context
+// re-created after cudaDeviceReset, holds its own copy at another address.  So
+// the address is cached with the unique ID of the context it was looked up in
+// (cuCtxGetId: unique for the life of the process), and looked up again when
+// the current context's ID differs.
+struct CachedAddr {
+    unsigned long long ctx_id;
+    double *addr;
+};
+CachedAddr g_addr[128] = {};                // per device: last context and address
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// driver entry points, fetched through the runtime (no link against libcuda)
+template <class F>
+F driver_fn(const char *name, int version) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return (F)p;
+}
+
+// unique ID of the calling thread's current context; an error (with a
+// message unless quiet) if none is current
+int current_context_id(unsigned long long &id, bool quiet = false) {
+    static CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 4000);
+    static CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId", 12000);
+    if (!get_current || !get_id) {
+        set_error("lbm_residual_noalloc: driver entry points cuCtxGetCurrent / cuCtxGetId unavailable");
+        return LBM_ECUDA;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, &id) != CUDA_SUCCESS) {
+        if (!quiet) set_error("lbm_residual_noalloc: no current CUDA context");
+        return LBM_ECUDA;
+    }
+    return LBM_OK;
+}
 
 // res = ||u - u'|| / ||u|| (thermal: max with ||T - T'|| / ||T - T_ref||);
 // NaN when any field value was not finite
@@ -56,10 +99,13 @@ extern "C" int lbm_residual_noalloc(const double *ux, const double *T, double *u
     }
     double *scratch;
     {
-        // first call on a device: look up the array's device address (with that
-        // device current); later calls reuse it
+        // first call in a context: look up the array's device address there
+        // (the look-up also binds the runtime's context to this thread when
+        // none is current yet); later calls in the same context reuse it
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
+        unsigned long long ctx_id = 0;
+        const bool bound = current_context_id(ctx_id, true) == LBM_OK;
+        if (!bound || !g_addr[dev].addr || g_addr[dev].ctx_id != ctx_id) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -67,9 +113,11 @@ extern "C" int lbm_residual_noalloc(const double *ux, const double *T, double *u
                           cudaGetErrorString(e));
                 return LBM_ECUDA;
             }
-            g_addr[dev] = (double *)p;
+            if (!bound)
+                if (int rc = current_context_id(ctx_id)) return rc;
+            g_addr[dev] = CachedAddr{ctx_id, (double *)p};
         }
-        scratch = g_addr[dev];
+        scratch = g_addr[dev].addr;
     }
     cudaStream_t st = (cudaStream_t)stream;
     const int nb = reduction_blocks(n);           // capped at kNoAllocBlocks

@@ -214,7 +214,8 @@ struct ServerImpl {
         d.prev_off = off + 2LL * L.Q * r.Ny;
         d.tol = r.tol;
         d.max_steps = r.max_steps;
-        d.T_ref = r.thermal ? 0.5 * (r.T_wall[0] + r.T_wall[1]) : 1.0;
+        d.u_ref = std::max(std::fabs(r.u_wall[0]), std::fabs(r.u_wall[1]));
+        if (!(d.u_ref > 0)) d.u_ref = 1.0;
         // incoming terms per wall (Sec. III: at layer l the velocities with
         // e.n < -l); the bottom list takes e_y < 0 at rows 0..|e_y|-1, the top
         // list e_y > 0 at rows Ny-1.. (distance from the wall)

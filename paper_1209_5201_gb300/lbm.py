@@ -116,6 +116,7 @@ _SIGS = {
     "lbm_solver_stats": ([_VP, C.POINTER(lbm_stats)], C.c_int),
     "lbm_solver_wall_mass": ([_VP, _DP], C.c_int),
     "lbm_solver_set_kernel": ([_VP, C.c_int32, C.c_int32], C.c_int),
+    "lbm_solver_set_wait_limit": ([_VP, C.c_uint64], C.c_int),
     "lbm_solver_kernel_info": ([_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                 C.POINTER(C.c_int32)], C.c_int),
     "lbm_solver_variant_count": ([_VP, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
@@ -349,6 +350,10 @@ def lbm_solver_wall_mass(h, out: np.ndarray) -> np.ndarray:
 
 def lbm_solver_set_kernel(h, kernel: int, variant: int = 0) -> None:
     _check(load().lbm_solver_set_kernel(h, int(kernel), int(variant)), "lbm_solver_set_kernel")
+
+
+def lbm_solver_set_wait_limit(h, ns: int) -> None:
+    _check(load().lbm_solver_set_wait_limit(h, int(ns)), "lbm_solver_set_wait_limit")
 
 
 def lbm_solver_kernel_info(h):
@@ -621,6 +626,9 @@ class Solver:
 
     def kernel_info(self):
         return lbm_solver_kernel_info(self.h)
+
+    def set_wait_limit(self, ns: int):
+        lbm_solver_set_wait_limit(self.h, ns)
 
     def variant_count(self, kernel: int) -> int:
         return lbm_solver_variant_count(self.h, kernel)

@@ -76,5 +76,5 @@ def test_batched_partial_accommodation_steady_state(lbm, oracle):
         ok, _, _ = oracle.run_to_residual(p, f, 1e-13, 2_000_000, 100)
         assert ok
         oux = oracle.macros(p, f)[1][:, 0]
-        assert np.max(np.abs(ux - oux)) / Uw < 2e-5, (lat, acc)
+        assert np.max(np.abs(ux - oux)) / Uw < 1e-5, (lat, acc)
     srv.close()

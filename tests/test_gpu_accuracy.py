@@ -3,9 +3,10 @@ instances of the batched (seed 7) and serving (seed 11) workloads whose oracle
 steady state is cheap enough for the CPU (est. <= 4e6 cell-steps each): the
 first 20 of the batched set and the first 50 of the serving set.
 
-Each request is solved to an extrapolated distance to the steady state of
-1e-5; the L-inf error of u_x / U_w (and of T for the thermal lattice) against
-the oracle's steady state (residual 1e-12) must stay within 2e-5."""
+Each request is solved to an extrapolated L-inf distance to the steady state
+of 5e-6 (the benchmark's target); the L-inf error of u_x / U_w (and of T for
+the thermal lattice) against the oracle's steady state (residual 1e-12) must
+stay within 1e-5, the accuracy the batched and serving workloads ask for."""
 import numpy as np
 import pytest
 
@@ -46,7 +47,7 @@ def test_steady_profiles_within_1e5(oracle, workload):
     sample = cheap(insts, limit=20 if workload == "batched" else 50)
     assert len(sample) >= 10
     srv = lbm.Server(mem_budget_bytes=1 << 28, max_slots=64, chunk_steps=100)
-    ids = [srv.submit(lbm.make_request(it.lattice, it.Ny, it.Kn, it.U_w, it.T_w, tol=1e-5))
+    ids = [srv.submit(lbm.make_request(it.lattice, it.Ny, it.Kn, it.U_w, it.T_w, tol=5e-6))
            for _, it in sample]
     srv.drain(600)
     res = {r.id: r for r in srv.poll(128)}
@@ -64,4 +65,4 @@ def test_steady_profiles_within_1e5(oracle, workload):
     report(f"accuracy_{workload}", rows)
     for row in rows:
         assert row["status"] == lbm.LBM_OK, row
-        assert row["err_u"] < 2e-5 and row["err_T"] < 2e-5, row
+        assert row["err_u"] < 1e-5 and row["err_T"] < 1e-5, row

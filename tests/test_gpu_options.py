@@ -70,9 +70,9 @@ def test_batched_path_follows_the_oracle(lbm, oracle, name):
     f = oracle.init_fields(p, np.ones((Ny, 1)))
     oracle.run(p, f, r.steps)
     _, oux, _, oT = oracle.macros(p, f)
-    assert np.max(np.abs(ux - oux[:, 0])) / Uw < 2e-5, (name, r.steps)
+    assert np.max(np.abs(ux - oux[:, 0])) / Uw < 1e-5, (name, r.steps)
     if c["thermal"]:
-        assert np.max(np.abs(T - oT[:, 0])) < 2e-5, name
+        assert np.max(np.abs(T - oT[:, 0])) < 1e-5, name
 
 
 def test_custom_lattice_runs_like_the_built_in_one(lbm, oracle):

@@ -62,14 +62,14 @@ def test_fp64_couette_d2q25_1x64(lbm, oracle):
     s.close()
 
 
-# FP32: relative error per population after 120-200 steps of the 4th-order
-# thermal lattice; the worst entries are the smallest populations (w = 2.5e-4)
-# near the walls, where ~1e-7 of round-off per step (Q terms of 6e-8 relative
-# each, on values of order w) accumulates to ~2.5e-9 absolute; bound 2e-5.
-# After 1000 steps the same per-step round-off, accumulated linearly in the
-# worst case, gives 5 x that bound.
-@pytest.mark.parametrize("precision,n,tol", [("fp64", 1000, 1e-12), ("fp32", 200, 2e-5),
-                                             ("fp32", 1000, 1e-4)])
+# FP32: relative error per population on the 4th-order thermal lattice, bound
+# 1e-5 after 200 and after 1000 steps (the FP32 tolerance of the config-2
+# domain).  The FP32 store holds deviations d = f - w, theta = T - 1 is formed
+# without cancellation against D and 1 - omega is never formed, so the
+# round-off per step scales with |d|, not with f; measured 3.9e-6 at 1000
+# steps.
+@pytest.mark.parametrize("precision,n,tol", [("fp64", 1000, 1e-12), ("fp32", 200, 1e-5),
+                                             ("fp32", 1000, 1e-5)])
 def test_d2q37_thermal_grid_multi_block(lbm, oracle, precision, n, tol):
     # 300 columns = 2 full 128-column blocks + a ragged 44, 40 rows, noise on rho
     Nx, Ny = 300, 40
