@@ -225,6 +225,30 @@ def resident_ctas() -> int:
     return 2 * torch.cuda.get_device_properties(0).multi_processor_count
 
 
+_TUNED = {}
+
+
+def tuned_server_cfg(lbm):
+    """Server configuration of the batched and serving legs: 40 GB budget,
+    every CTA resident, chunk length, cluster rows and chunks per launch from
+    the library's batched-path autotuner (run once per process, before any
+    timed region)."""
+    if "cfg" not in _TUNED:
+        cfg = lbm.lbm_server_cfg_default()
+        cfg.mem_budget_bytes = 40 << 30
+        cfg.max_slots = resident_ctas()
+        rep = lbm.lbm_server_autotune(cfg)
+        _TUNED["cfg"] = cfg
+        _TUNED["report"] = {"chunk_steps": cfg.chunk_steps, "cluster_rows": cfg.cluster_rows,
+                            "class_sub": list(cfg.class_sub), "seconds": rep["seconds"],
+                            "chunk_glups": dict(zip(rep["chunk_try"], rep["chunk_glups"])),
+                            "lone_us_per_step": {
+                                lat: {ny: [round(v, 3) for v in rep["lone_us"][li][hi]]
+                                      for hi, ny in enumerate(rep["ny"])}
+                                for li, lat in enumerate(("D2Q17", "D2Q25", "D2Q37"))}}
+    return type(_TUNED["cfg"]).from_buffer_copy(_TUNED["cfg"]), _TUNED["report"]
+
+
 def _oracle_problem(orc, it):
     return orc.Problem(lattice=it.lattice, Nx=1, Ny=it.Ny, eq_order=it.eq_order,
                        thermal=it.thermal, Kn=it.Kn, u_wall=(-it.U_w, it.U_w),
@@ -287,9 +311,10 @@ def run_batched(lbm, n=256, seed=7, tol=SOLVE_TOL, baseline_every=16):
     import inputs
     insts = inputs.batched_instances(n, seed=seed)
     ctas = resident_ctas()
+    tuned = tuned_server_cfg(lbm)
 
     def server():
-        return lbm.Server(mem_budget_bytes=40 << 30, max_slots=ctas, chunk_steps=100)
+        return lbm.Server(cfg=tuned_server_cfg(lbm)[0])
     srv = server()
     t0 = time.perf_counter()
     ids = [srv.submit(_request(lbm, it, tol)) for it in insts]
@@ -341,7 +366,7 @@ def run_batched(lbm, n=256, seed=7, tol=SOLVE_TOL, baseline_every=16):
                                "to completion: alone through the same server, and on the "
                                "single-domain FP32 solver (AUTO kernel) for the same steps",
             "max_err_est": max((r.err_est for r in results if r.status == 0), default=None),
-            "cta_budget": ctas,
+            "cta_budget": ctas, "autotune": tuned[1],
             "accuracy": "solves stop at an extrapolated L-inf distance tol of u_x/U_w (and T) "
                         "to the steady state; cpu_baseline.max_err_vs_oracle is the measured "
                         "error on the instances the oracle solved",
@@ -362,7 +387,8 @@ def run_serving(lbm, n=10000, seed=11, rate=200.0, tol=SOLVE_TOL):
     import inputs
     reqs = inputs.serving_requests(n, seed=seed, rate=rate)
     ctas = resident_ctas()
-    srv = lbm.Server(mem_budget_bytes=40 << 30, max_slots=ctas, chunk_steps=100)
+    cfg, tuning = tuned_server_cfg(lbm)
+    srv = lbm.Server(cfg=cfg)
     t0 = time.perf_counter()
     ids = []
     for q in reqs:
@@ -385,6 +411,8 @@ def run_serving(lbm, n=10000, seed=11, rate=200.0, tol=SOLVE_TOL):
             "p50_latency_s": st.p50_latency_s, "p99_latency_s": st.p99_latency_s,
             "mean_latency_s": st.mean_latency_s, "solves_per_s": st.solves_per_s,
             "wall_s": wall, "mean_occupancy": st.mean_occupancy, "cta_budget": ctas,
+            "server_cfg": {"chunk_steps": cfg.chunk_steps, "cluster_rows": cfg.cluster_rows,
+                           "class_sub": list(cfg.class_sub)},
             "cell_steps": int(cell_steps), "GLUPS": cell_steps / wall / 1e9,
             "max_err_est": max((r.err_est for r in results if r.status == 0), default=None),
             "cpu_baseline": oracle_leg(reqs[:head], results[:head], fields, limit=50)}
@@ -515,13 +543,12 @@ def step_traffic(key: str):
 
 
 def kernel_name(kern: int, var: int, prec: str) -> str:
-    """Readable name of a (kernel, variant) choice: direct variants 7.. are the
-    two-cells-per-thread kernels of the FP32 and BF16DEV formats."""
+    """Readable name of a (kernel, variant) choice."""
     if kern == 2:
         return f"staged{var}"
     if kern == 3:
         return "cellwarp"
-    return f"pair{var - 7}" if (var >= 7 and prec != "fp64") else f"direct{var}"
+    return f"direct{var}"
 
 
 def main():

@@ -234,13 +234,9 @@ typedef struct lbm_stats {
 /* Synchronous (one reduction over the state). */
 int lbm_solver_stats(lbm_solver *s, lbm_stats *st);
 
-/* Step-kernel selection.  LBM_KERNEL_DIRECT: populations pulled straight
- * from global memory; variants 0..6 update one cell per thread and differ in
- * block width, register cap, rows per block and store cache policy; with FP32
- * and BF16DEV storage variants 7..9 update two adjacent cells per thread with
- * packed FP32x2 arithmetic, paired loads and stores (and, for BF16DEV, one
- * stochastic-rounding conversion per pair of values), with results equal bit
- * for bit to the one-cell variants.  LBM_KERNEL_STAGED: persistent tile
+/* Step-kernel selection.  LBM_KERNEL_DIRECT: one thread per cell, populations
+ * pulled straight from global memory; its variants differ in block width,
+ * register cap, rows per block and store cache policy.  LBM_KERNEL_STAGED: persistent tile
  * kernel whose producer warp stages each velocity's shifted source window
  * (tile plus the +-3-cell halo, rounded to 16 bytes in x) into shared memory
  * with TMA; `variant` picks one of the compiled tile shapes, 0 <= variant <
@@ -384,6 +380,12 @@ typedef struct lbm_server_cfg {
                                 a cluster (>= 32; default 256): smaller gives
                                 lower latency per request, larger more solves
                                 per second when the GPU is full             */
+    int32_t class_sub[5];    /* chunks per launch of a slot on a cluster of 1,
+                                2, 4, 8, 16 CTAs (0..16; 0: the built-in rule
+                                max(1, CL / 2)); a cluster runs a step faster
+                                than one CTA, so it runs several chunks while
+                                one-CTA slots run one.  lbm_server_autotune
+                                measures them.  Results do not depend on it. */
 } lbm_server_cfg;
 
 typedef struct lbm_server_metrics {
@@ -436,6 +438,40 @@ int lbm_server_drain(lbm_server *srv, double timeout_s);
 int lbm_server_stats(lbm_server *srv, lbm_server_metrics *st);
 /* Stop the worker (running requests are abandoned) and free everything. */
 int lbm_server_destroy(lbm_server *srv);
+/* Step times the batched-path autotuner measured (lbm_server_autotune). */
+typedef struct lbm_server_tuning {
+    int32_t ny[3];              /* column heights timed: 256, 1024, 4096      */
+    double lone_us[3][3][5];    /* us per step of one lone column: lattice
+                                   D2Q17 / D2Q25 / D2Q37, height ny[i], on a
+                                   cluster of 1, 2, 4, 8, 16 CTAs (0: that
+                                   split is not usable or not schedulable)    */
+    int32_t chunk_try[5];       /* chunk lengths timed on a full GPU          */
+    double chunk_glups[5];      /* lattice updates per second (1e9) of
+                                   max_slots one-CTA D2Q25 columns of 128 rows
+                                   at each chunk length, launches included     */
+    double seconds;             /* wall time of the autotuning                */
+} lbm_server_tuning;
+
+/* Autotuner of the batched path (the paper has no counterpart: it is a
+ * service of the library).  Starting from *cfg (budget, max_slots, graph
+ * use), it times on this device, through servers it creates and destroys:
+ *  - one lone column of each lattice at heights 256, 1024 and 4096 on each
+ *    usable cluster size (long runs, so launch overhead is negligible), and
+ *  - max_slots one-CTA columns at chunk lengths 25, 50, 100, 200, 400,
+ * then writes into *cfg: class_sub[c] = the median over lattices and heights
+ * of the step time on one CTA over that on a cluster of class c (how many
+ * chunks a cluster slot runs while a one-CTA slot runs one, 1..16);
+ * cluster_rows = the median over lattices and heights of the rows per CTA
+ * of the smallest cluster within 15 % of the fastest (32 .. 1024); and
+ * chunk_steps = the shortest chunk within 5 % of the best full-GPU rate
+ * (shorter chunks admit and retire requests sooner).  Takes a few seconds;
+ * the device must be otherwise idle for the times to mean anything.  `stream`
+ * as for lbm_server_create; `report` (may be NULL) receives the times.
+ * Results of a solve do not depend on cluster_rows or class_sub; chunk_steps
+ * moves the steps at which its convergence checks fall.
+ * Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_server_autotune(lbm_server_cfg *cfg, void *stream, lbm_server_tuning *report);
+
 /* Batched solve: a server with `cfg`, all n requests submitted at once,
  * drained (timeout_s), results written to out[i] for reqs[i]. */
 int lbm_batch_solve(const lbm_server_cfg *cfg, void *stream, const lbm_request *reqs,

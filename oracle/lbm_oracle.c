@@ -29,8 +29,13 @@
  *    pre-collision rho and T of the cell (Sec. II; Kn as in Eq. (15)).
  *  - The wall equilibrium uses the bulk expansion order; isothermal runs use
  *    T_w = 1 (Eq. (4) with T = 1).
- *  - Walls move tangentially (u_w . n = 0), so the layer criteria of Sec. III
- *    reduce to integer comparisons of e_y.
+ *  - The layer criteria of Sec. III are applied in lattice units: incoming at
+ *    layer l when e_a . n - v_n < -l, outgoing when e_a . n - v_n > l, with
+ *    v_n = u_w . n / r the wall's normal velocity in cells per step (0 for
+ *    the paper's tangential walls, where they are integer comparisons of
+ *    e_y).  A nonzero v_n is applied on the fixed half-way geometry exactly
+ *    as the criteria read; a re-emitted population whose target row is not
+ *    a fluid row is counted as lost (wall statistics).
  *  - The wall acts on the transformed variable f~ as streamed (Eq. (5)).
  */
 #include <math.h>
@@ -60,6 +65,8 @@ typedef struct {
     double T_wall[2];   /* temperature of the bottom and top wall */
     double accom[2];    /* accommodation of the scattering kernel per wall:
                            R = accom R_D + (1 - accom) R_S (1: diffuse) */
+    double vn[2];       /* normal wall velocity u_w . n / r per wall, in cells
+                           per step (n into the gas; |vn| < 1; 0: tangential) */
 } orc_params;
 
 typedef struct {
@@ -69,6 +76,8 @@ typedef struct {
     double m_out[2];
     long long holes_unfilled;   /* fluid slots no population reached */
     long long slots_doubled;    /* fluid slots reached twice */
+    double m_lost[2];           /* re-emitted mass whose target row is no
+                                   fluid row (only with a normal velocity) */
 } orc_wallstats;
 
 #define ORC_D 2  /* space dimension D of Eq. (3)-(4) */
@@ -182,13 +191,14 @@ double orc_wall_distribution(const orc_lattice *L, const orc_params *P,
                              int wall, double *gw)
 {
     double Tw = P->thermal ? P->T_wall[wall] : 1.0;
-    orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[wall], 0.0, Tw, gw);
-    int N = orc_ghost_depth(L);
     int nsgn = wall == 0 ? 1 : -1;     /* normal into the gas: +y / -y */
+    /* the wall velocity: tangential u_wall, normal vn r along n */
+    orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[wall], nsgn * P->vn[wall] * L->r, Tw, gw);
+    int N = orc_ghost_depth(L);
     double den = 0.0;
     for (int l = 0; l < N; ++l)
         for (int a = 0; a < L->Q; ++a)
-            if (nsgn * L->ey[a] > l) den += gw[a];
+            if (nsgn * L->ey[a] - P->vn[wall] > l) den += gw[a];
     return den;
 }
 
@@ -228,17 +238,18 @@ static int orc_one_step(const orc_lattice *L, const orc_params *P, double *f,
     double gw[2][64], den[2];
     den[0] = orc_wall_distribution(L, P, 0, gw[0]);
     den[1] = orc_wall_distribution(L, P, 1, gw[1]);
-    double tot_in[2] = {0.0, 0.0}, tot_out[2] = {0.0, 0.0};
+    double tot_in[2] = {0.0, 0.0}, tot_out[2] = {0.0, 0.0}, lost[2] = {0.0, 0.0};
 
     for (int wall = 0; wall < 2; ++wall) {
         int nsgn = wall == 0 ? 1 : -1;
+        const double vn = P->vn[wall];
         for (int xw = 0; xw < Nx; ++xw) {
             /* ghost layer l sits at fluid row -1-l (bottom) or Ny+l (top) */
             double m_in = 0.0;
             for (int l = 0; l < N; ++l) {
                 int grow = wall == 0 ? -1 - l : Ny + l;
                 for (int a = 0; a < Q; ++a)
-                    if (nsgn * L->ey[a] < -l)       /* incoming at layer l */
+                    if (nsgn * L->ey[a] - vn < -l)  /* incoming at layer l */
                         m_in += ext[a * eplane + (long)(grow + N) * Nx + xw];
             }
             tot_in[wall] += m_in;
@@ -253,7 +264,7 @@ static int orc_one_step(const orc_lattice *L, const orc_params *P, double *f,
                 int grow = wall == 0 ? -1 - l : Ny + l;
                 for (int a = 0; a < Q; ++a) {
                     fspec[a * N + l] = 0.0;
-                    if (!(nsgn * L->ey[a] > l)) continue;
+                    if (!(nsgn * L->ey[a] - vn > l)) continue;
                     for (int b = 0; b < Q; ++b)
                         if (L->ex[b] == L->ex[a] && L->ey[b] == -L->ey[a])
                             fspec[a * N + l] = ext[b * eplane + (long)(grow + N) * Nx + xw];
@@ -262,13 +273,19 @@ static int orc_one_step(const orc_lattice *L, const orc_params *P, double *f,
             for (int l = 0; l < N; ++l) {
                 int grow = wall == 0 ? -1 - l : Ny + l;
                 for (int a = 0; a < Q; ++a) {
-                    if (!(nsgn * L->ey[a] > l)) continue;   /* outgoing */
+                    if (!(nsgn * L->ey[a] - vn > l)) continue;   /* outgoing */
                     double fo = acc * (m_in * gw[wall][a] / den[wall]) +
                                 (1.0 - acc) * fspec[a * N + l];
                     tot_out[wall] += fo;
                     int tj = grow + L->ey[a];
                     int tx = ((xw + L->ex[a]) % Nx + Nx) % Nx;
-                    if (tj < 0 || tj >= Ny) return -1;   /* cannot happen */
+                    if (tj < 0 || tj >= Ny) {
+                        /* only with vn < 0: a population with e.n = l leaving
+                         * layer l lands in a ghost row again */
+                        if (vn == 0.0) return -1;
+                        lost[wall] += fo;
+                        continue;
+                    }
                     ext[a * eplane + (long)(tj + N) * Nx + tx] = fo;
                     hits[a * plane + (long)tj * Nx + tx] += 1;
                 }
@@ -286,7 +303,11 @@ static int orc_one_step(const orc_lattice *L, const orc_params *P, double *f,
                sizeof(double) * plane);
 
     if (st) {
-        for (int k = 0; k < 2; ++k) { st->m_in[k] = tot_in[k]; st->m_out[k] = tot_out[k]; }
+        for (int k = 0; k < 2; ++k) {
+            st->m_in[k] = tot_in[k];
+            st->m_out[k] = tot_out[k];
+            st->m_lost[k] = lost[k];
+        }
         st->holes_unfilled = unfilled;
         st->slots_doubled = doubled;
     }

@@ -40,12 +40,14 @@ class _Params(C.Structure):
     _fields_ = [("Nx", C.c_int), ("Ny", C.c_int), ("eq_order", C.c_int),
                 ("thermal", C.c_int), ("Kn", C.c_double), ("tau", C.c_double),
                 ("mu_exp", C.c_double), ("u_wall", C.c_double * 2),
-                ("T_wall", C.c_double * 2), ("accom", C.c_double * 2)]
+                ("T_wall", C.c_double * 2), ("accom", C.c_double * 2),
+                ("vn", C.c_double * 2)]
 
 
 class _WallStats(C.Structure):
     _fields_ = [("m_in", C.c_double * 2), ("m_out", C.c_double * 2),
-                ("holes_unfilled", C.c_longlong), ("slots_doubled", C.c_longlong)]
+                ("holes_unfilled", C.c_longlong), ("slots_doubled", C.c_longlong),
+                ("m_lost", C.c_double * 2)]
 
 
 def _load():
@@ -100,6 +102,7 @@ class Problem:
     u_wall: tuple = (-0.1, 0.1)
     T_wall: tuple = (1.0, 1.0)
     accom: tuple = (1.0, 1.0)
+    vn: tuple = (0.0, 0.0)      # normal wall velocity u_w . n / r, cells per step
     lat: _lat.OracleLattice = field(init=False, repr=False)
 
     def __post_init__(self):
@@ -112,7 +115,8 @@ class Problem:
                             self._ey.ctypes.data_as(ip), _dp(self._w), float(self.lat.r))
         self._cp = _Params(self.Nx, self.Ny, self.eq_order, int(self.thermal), self.Kn,
                            self.tau, self.mu_exp, (C.c_double * 2)(*self.u_wall),
-                           (C.c_double * 2)(*self.T_wall), (C.c_double * 2)(*self.accom))
+                           (C.c_double * 2)(*self.T_wall), (C.c_double * 2)(*self.accom),
+                           (C.c_double * 2)(*self.vn))
 
     @property
     def Q(self) -> int:
@@ -173,7 +177,7 @@ def run(p: Problem, f: np.ndarray, nsteps: int, stats: bool = False):
     if rc != 0:
         raise RuntimeError(f"oracle run failed: {rc}")
     if stats:
-        return dict(m_in=tuple(st.m_in), m_out=tuple(st.m_out),
+        return dict(m_in=tuple(st.m_in), m_out=tuple(st.m_out), m_lost=tuple(st.m_lost),
                     holes_unfilled=st.holes_unfilled, slots_doubled=st.slots_doubled)
     return None
 

@@ -38,6 +38,9 @@ struct SlotDesc {
     double tol;               // target of the extrapolated distance to steady state
     long long max_steps;
     double u_ref;             // velocity scale of the change measure: max |u_wall|
+    double mass0;             // the column's mass at admission (sum of rho)
+    double precise_from;      // change per check below which the slot switches
+                              // to stochastic rounding and conserving increments
     // incoming terms of Eq. (12)'s numerator, built on the host: wall w (0
     // bottom, 1 top), term l < nterm is velocity term_a[w][l] at distance
     // term_row[w][l] from the wall
@@ -64,6 +67,8 @@ struct SlotStatus {
     int checks;
     int since_best;           // checks without a new smallest residual
     int chunks;               // chunks run since admission
+    int precise;              // 0: round-to-nearest collision; 1: conserving
+                              // increments with stochastic rounding (2: switching)
 };
 
 // Cluster sizes of the slot classes.

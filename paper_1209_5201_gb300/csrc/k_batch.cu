@@ -61,7 +61,7 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
               long long pool_elems, int *dbg) {
     __shared__ SlotDesc sd;
     __shared__ BatchWallShared sw;
-    __shared__ int s_chunks;
+    __shared__ int s_chunks, s_precise;
     __shared__ long long s_steps;
     extern __shared__ __align__(16) float batch_sm[];
     const int slot = slot0 + blockIdx.x / CL;
@@ -70,6 +70,7 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
     if (threadIdx.x == 0) {
         s_chunks = status[slot].chunks;
         s_steps = status[slot].steps;
+        s_precise = status[slot].precise;
     }
     __syncthreads();
     if (sd.Q == 0 || status[slot].state != kSlotRunning) return;
@@ -77,9 +78,9 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
     double *pp = part + (long long)slot * (6 * kMaxResidualChunks);
     int done = 0;
     switch (sd.Q) {
-    case 17: done = batch_slot<17>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, pp, batch_sm); break;
-    case 25: done = batch_slot<25>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, pp, batch_sm); break;
-    case 37: done = batch_slot<37>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, pp, batch_sm); break;
+    case 17: done = batch_slot<17>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, s_precise, pp, batch_sm); break;
+    case 25: done = batch_slot<25>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, s_precise, pp, batch_sm); break;
+    case 37: done = batch_slot<37>(sd, pool, status + slot, sw, rank, CL, s_chunks, s_steps, s_precise, pp, batch_sm); break;
     default: break;
     }
     // the global-memory path leaves the state in the other buffer after an odd

@@ -289,7 +289,7 @@ __device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, int wall, int 
         const double x = fma(v, d.out_c[wall][lane], -d.out_w[wall][lane]);
         const float hi = (float)x, lo = (float)(x - (double)hi);
         const uint32_t h = sr_cell(step, (uint32_t)(d.Ny + wall));
-        fill[d.out_a[wall][lane]] = add_sr(hi, lo, sr_bits23(h, lane));
+        fill[d.out_a[wall][lane]] = add_sr(hi, lo, sr_bits32(h, lane));
     }
     __syncwarp();
 }
@@ -298,7 +298,9 @@ __device__ __forceinline__ void wall_fill_warp(const SlotDesc &d, int wall, int 
 // the row is within 3 rows of its CTA's first or last row, so a source may lie
 // beyond the slot's walls or in a neighbouring CTA; otherwise every source is
 // one of this CTA's rows.
-template <int Q, bool EDGE, class State>
+// PRECISE: conserving increments with stochastic rounding (the steady-state
+// phase of a solve); otherwise the plain relaxation rounded to nearest.
+template <int Q, bool EDGE, bool PRECISE, class State>
 __device__ __forceinline__ void cell_update(const SlotDesc &d, const State &S, int j,
                                             const BatchWallShared &sw, uint32_t step) {
     // the slot's constants live in shared memory; this compiler barrier keeps
@@ -310,12 +312,20 @@ __device__ __forceinline__ void cell_update(const SlotDesc &d, const State &S, i
     S.template pull<Q, EDGE>(d, sw, j, f);
     Collision<Q, float, true> col;
     col.setup(f, k);
-    // increments that conserve mass, momentum (and energy) in FP32, added with
-    // stochastic rounding: random bits from the hash of the request's step
-    // count and the row (the same however the column is split or batched)
-    const uint32_t h = sr_cell(step, (uint32_t)j);
+    // PRECISE: increments that conserve mass, momentum (and energy) in FP32,
+    // added with stochastic rounding: random bits from the hash of the
+    // request's step count and the row (the same however the column is split
+    // or batched)
     float o[Q];
-    col.relax_conserving_sr(f, o, h, k.thermal != 0);
+    if constexpr (PRECISE) {
+        col.relax_conserving_sr(f, o, sr_cell(step, (uint32_t)j), k.thermal != 0);
+    } else {
+        o[0] = col.rest(f[0]);
+        PairLoop<1, Q>::run([&](auto ic) {
+            constexpr int A = decltype(ic)::value;
+            col.template pair<A>(f[A], f[A + 1], o[A], o[A + 1]);
+        });
+    }
     S.template store<Q, EDGE>(j, o);
 }
 
@@ -324,7 +334,7 @@ __device__ __forceinline__ void cell_update(const SlotDesc &d, const State &S, i
 // wall's re-emission; every thread then updates its wall-block row (if any)
 // and its share of the bulk rows [mb, me), handed out from the last thread
 // down so that the wall warps get bulk rows last.
-template <int Q, class State>
+template <int Q, bool PRECISE, class State>
 __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWallShared &sw,
                                           int chunk, int CL, int warp, int lane, int tid,
                                           int nth, int j0, int j1, int nb, int nt, int mb,
@@ -355,8 +365,8 @@ __device__ __forceinline__ void run_steps(const SlotDesc &d, State &S, BatchWall
             // CTA's ends takes the general (EDGE) path for all its rows, so
             // the collision is never executed twice by a diverged warp
             const bool edge = __any_sync(__activemask(), j < j0 + 3 || j >= j1 - 3);
-            if (edge) cell_update<Q, true>(d, S, j, sw, gstep);
-            else cell_update<Q, false>(d, S, j, sw, gstep);
+            if (edge) cell_update<Q, true, PRECISE>(d, S, j, sw, gstep);
+            else cell_update<Q, false, PRECISE>(d, S, j, sw, gstep);
         }
         const bool more = step + 1 < chunk;
         if (CL == 1) {
@@ -387,7 +397,7 @@ template <int Q>
 __device__ __forceinline__ int batch_slot(const SlotDesc &d, float *__restrict__ pool,
                                           SlotStatus *__restrict__ st, BatchWallShared &sw,
                                           int rank, int CL, int chunks0, long long steps0,
-                                          double *__restrict__ part, float *sm) {
+                                          int precise, double *__restrict__ part, float *sm) {
     using L = Lat<Q>;
     const int chunk = d.chunk_steps;
     const KConsts<float> &k = d.k;
@@ -492,6 +502,19 @@ __device__ __forceinline__ int batch_slot(const SlotDesc &d, float *__restrict__
                 s.mass = tot[4];
                 double res = tot[0] / d.u_ref;
                 if (k.thermal) res = fmax(res, tot[2]);
+                if (s.precise == 0 && res <= d.precise_from && tot[5] == 0 && isfinite(res)) {
+                    // close enough to the steady state for round-off to freeze:
+                    // switch to conserving, stochastically rounded increments
+                    // (the mass is restored below) and restart the
+                    // convergence bookkeeping for the remaining approach
+                    s.precise = 2;
+                    s.checks = 0;
+                    s.res = s.res_prev = 0.0;
+                    s.err_est = 1e30;
+                    s.best_res = 1e300;
+                    s.since_best = 0;
+                    if (s.steps >= d.max_steps) s.state = kSlotMaxSteps;
+                } else {
                 // geometric extrapolation of the remaining change: with a
                 // per-check contraction q = res / res_prev < 1, the distance
                 // to the steady state is about res q / (1 - q); q from the
@@ -514,9 +537,26 @@ __device__ __forceinline__ int batch_slot(const SlotDesc &d, float *__restrict__
                 else if (s.since_best >= 8 && s.best_res <= 0.25 * d.tol) s.state = kSlotConverged;
                 else if (s.since_best >= 50) s.state = kSlotStagnated;
                 else if (s.steps >= d.max_steps) s.state = kSlotMaxSteps;
+                }
             }
         }
         slot_barrier(CL);                      // the new state visible to the cluster
+        if (__ldcg(&st->precise) == 2) {
+            // the round-to-nearest phase let the column's mass drift by its
+            // systematic round-off: restore the admission mass, spread over
+            // the cells as rest equilibrium (d_a += dm w_a, no momentum)
+            const float dm = (float)((d.mass0 - __ldcg(&st->mass)) / (double)Ny);
+            float *f = const_cast<float *>(fin);
+            for (int j = j0 + tid; j < j1; j += nth)
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    float &v = smem ? f[(j - j0) * Q + a] : f[(long long)a * Ny + j];
+                    v = __fmaf_rn(dm, k.w[a], v);
+                }
+            slot_barrier(CL);                  // every CTA read precise == 2 and corrected
+            if (rank == 0 && tid == 0) st->precise = 1;
+            precise = 1;
+        }
         return __ldcg(&st->state) == kSlotRunning;
     };
     // after sub-chunk kk of this launch: a check when the slot's chunk count
@@ -549,8 +589,9 @@ __device__ __forceinline__ int batch_slot(const SlotDesc &d, float *__restrict__
         if (rank < CL - 1) S.hi = map_rank(base, rank + 1);
         slot_barrier(CL);                      // every CTA loaded before any neighbour reads
         while (done < d.sub) {
-            run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me,
-                         (uint32_t)(steps0 + (long long)done * chunk));
+            const uint32_t s0 = (uint32_t)(steps0 + (long long)done * chunk);
+            if (precise) run_steps<Q, true>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me, s0);
+            else run_steps<Q, false>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me, s0);
             ++done;
             if (!after_chunk(sm + S.b * Q * R, done)) break;
         }
@@ -564,8 +605,9 @@ __device__ __forceinline__ int batch_slot(const SlotDesc &d, float *__restrict__
         __syncthreads();
         GlobalState S{g_cur, g_oth, Ny, &sw.term[0][0][0]};
         while (done < d.sub) {
-            run_steps<Q>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me,
-                         (uint32_t)(steps0 + (long long)done * chunk));
+            const uint32_t s0 = (uint32_t)(steps0 + (long long)done * chunk);
+            if (precise) run_steps<Q, true>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me, s0);
+            else run_steps<Q, false>(d, S, sw, chunk, CL, warp, lane, tid, nth, j0, j1, nb, nt, mb, me, s0);
             ++done;
             if (!after_chunk(S.src, done)) break;
         }

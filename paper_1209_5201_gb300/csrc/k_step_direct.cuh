@@ -20,8 +20,7 @@ namespace lbm {
 // M_in(x') for x' = x0 - 3 + t, t in [0, BX + 6): post-collision populations
 // of the N rows next to `wall` that stream into ghost column x' (Sec. III:
 // incoming at layer l when e.n < -l; summed over all layers, Eq. (12)).
-// BX: the block's columns; NT: its threads.
-template <int Q, int PREC, int BX, int NT = BX>
+template <int Q, int PREC, int BX>
 __device__ __forceinline__ void wall_prologue(const typename Store<PREC>::S *__restrict__ fin,
                                               const float *__restrict__ rin,
                                               const KConsts<typename Store<PREC>::C> &k,
@@ -29,7 +28,7 @@ __device__ __forceinline__ void wall_prologue(const typename Store<PREC>::S *__r
     using L = Lat<Q>;
     // ghost columns x0 - 3 .. x0 + active + 2 (fewer than BX when Nx is small)
     const int ncols = min(BX, k.Nx - x0) + 6;
-    for (int t = threadIdx.x; t < ncols; t += NT) {
+    for (int t = threadIdx.x; t < ncols; t += BX) {
         const int xw = wrap(x0 - 3 + t, k.Nx);
         double m = 0.0;
 #pragma unroll
@@ -89,22 +88,16 @@ __device__ __forceinline__ void store_cs<__nv_bfloat16>(__nv_bfloat16 *p, __nv_b
     __stcs((unsigned short *)p, __bfloat16_as_ushort(v));
 }
 
-// One cell's update: pull (in the N rows next to a wall, with the wall's
-// re-emission from s_min, that wall's incoming-mass sums), collide, store.
+// Collide the pulled values f of cell (x, j) and store the result.
 template <int Q, int PREC, bool CS>
-__device__ __forceinline__ void step_cell(const typename Store<PREC>::S *__restrict__ fin,
-                                          typename Store<PREC>::S *__restrict__ fout,
-                                          const float *__restrict__ rin, float *__restrict__ rout,
-                                          const KConsts<typename Store<PREC>::C> &k, int x, int j,
-                                          const double *s_min, uint32_t seed) {
-    using L = Lat<Q>;
+__device__ __forceinline__ void collide_store(const typename Store<PREC>::C (&f)[Q],
+                                              typename Store<PREC>::S *__restrict__ fout,
+                                              float *__restrict__ rout,
+                                              const KConsts<typename Store<PREC>::C> &k, int x,
+                                              int j, uint32_t seed) {
     using S = typename Store<PREC>::S;
     using C = typename Store<PREC>::C;
     const uint32_t hcell = Store<PREC>::dev ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
-    C f[Q];
-    if (j < L::N || j >= k.Ny - L::N) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, f);
-    else pull<Q, PREC, false>(fin, rin, k, x, j, s_min, f);
-
     Collision<Q, C, Store<PREC>::shifted> col;
     col.setup(f, k);
     C o[Q];
@@ -139,6 +132,22 @@ __device__ __forceinline__ void step_cell(const typename Store<PREC>::S *__restr
     }
 }
 
+// One cell's update: pull (in the N rows next to a wall, with the wall's
+// re-emission from s_min, that wall's incoming-mass sums), collide, store.
+template <int Q, int PREC, bool CS>
+__device__ __forceinline__ void step_cell(const typename Store<PREC>::S *__restrict__ fin,
+                                          typename Store<PREC>::S *__restrict__ fout,
+                                          const float *__restrict__ rin, float *__restrict__ rout,
+                                          const KConsts<typename Store<PREC>::C> &k, int x, int j,
+                                          const double *s_min, uint32_t seed) {
+    using L = Lat<Q>;
+    using C = typename Store<PREC>::C;
+    C f[Q];
+    if (j < L::N || j >= k.Ny - L::N) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, f);
+    else pull<Q, PREC, false>(fin, rin, k, x, j, s_min, f);
+    collide_store<Q, PREC, CS>(f, fout, rout, k, x, j, seed);
+}
+
 // BX threads per block (one row segment); MINB blocks per SM requested from
 // the register allocator; CS: streaming stores for the interior columns; RS
 // rows per block, walked in order (rows [RS blockIdx.y, RS blockIdx.y + RS)).
@@ -167,6 +176,49 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
     if (x >= k.Nx) return;
     for (int j = j0; j < j1; ++j)
         step_cell<Q, PREC, CS>(fin, fout, rin, rout, k, x, j, s_min[j < L::N ? 0 : 1], seed);
+}
+
+// Software-pipelined row strip: a block owns BX columns of RS consecutive
+// rows; in a strip clear of both walls every thread issues the loads of its
+// next row before it collides the current one, so the next row's 37 loads
+// are in flight while the ALU works (a strip that touches a wall row steps
+// its rows one by one, as k_step_direct does).
+template <int Q, int PREC, int BX, int MINB, int RS>
+__global__ void __launch_bounds__(BX, MINB)
+k_step_direct_pipe(const typename Store<PREC>::S *__restrict__ fin,
+                   typename Store<PREC>::S *__restrict__ fout, const float *__restrict__ rin,
+                   float *__restrict__ rout,
+                   const __grid_constant__ KConsts<typename Store<PREC>::C> k) {
+    using L = Lat<Q>;
+    using C = typename Store<PREC>::C;
+    __shared__ double s_min[2][BX + 6];
+    const int x0 = blockIdx.x * BX;
+    const int x = x0 + threadIdx.x;
+    const int j0 = blockIdx.y * RS;
+    const int j1 = min(k.Ny, j0 + RS);
+    const bool bot = j0 < L::N, top = j1 > k.Ny - L::N;
+    if (bot) wall_prologue<Q, PREC, BX>(fin, rin, k, 0, x0, s_min[0]);
+    if (top) wall_prologue<Q, PREC, BX>(fin, rin, k, 1, x0, s_min[1]);
+    if (bot || top) __syncthreads();
+    uint32_t seed = 0;
+    if constexpr (Store<PREC>::dev)
+        seed = step_count(fin, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
+    if (x >= k.Nx) return;
+    if (bot || top) {
+        for (int j = j0; j < j1; ++j)
+            step_cell<Q, PREC, false>(fin, fout, rin, rout, k, x, j, s_min[j < L::N ? 0 : 1], seed);
+        return;
+    }
+    C cur[Q];
+    pull<Q, PREC, false>(fin, rin, k, x, j0, nullptr, cur);
+#pragma unroll 1
+    for (int j = j0; j < j1; ++j) {
+        C nxt[Q];
+        if (j + 1 < j1) pull<Q, PREC, false>(fin, rin, k, x, j + 1, nullptr, nxt);
+        collide_store<Q, PREC, false>(cur, fout, rout, k, x, j, seed);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) cur[a] = nxt[a];
+    }
 }
 
 }  // namespace lbm

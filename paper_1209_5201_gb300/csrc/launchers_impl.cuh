@@ -5,7 +5,6 @@
 #include "k_fluxes.cuh"
 #include "k_step_cellwarp.cuh"
 #include "k_step_direct.cuh"
-#include "k_step_pair.cuh"
 #include "k_step_staged.cuh"
 #include "launchers.h"
 
@@ -37,62 +36,38 @@ inline int aux_blocks(long long n) {
     default: return (int)cudaErrorInvalidValue;                 \
     }
 
-// ---- direct kernel variants {BX, MINB, CS, RS} ----------------------------------
-// RS: rows per block
+// ---- direct kernel variants {BX, MINB, CS, RS, PIPE} ----------------------------
+// RS: rows per block; PIPE: software-pipelined row strip (k_step_direct_pipe)
 struct DirectVariants {
-    static constexpr int n = 7;
-    static constexpr int v[n][4] = {{128, 0, 0, 1}, {64, 0, 0, 1},  {128, 8, 0, 1}, {256, 0, 0, 1},
-                                    {128, 0, 1, 1}, {192, 0, 0, 1}, {128, 0, 0, 2}};
+    static constexpr int n = 10;
+    static constexpr int v[n][5] = {{128, 0, 0, 1, 0}, {64, 0, 0, 1, 0},  {128, 8, 0, 1, 0},
+                                    {256, 0, 0, 1, 0}, {128, 0, 1, 1, 0}, {192, 0, 0, 1, 0},
+                                    {128, 0, 0, 2, 0}, {128, 0, 0, 4, 1}, {128, 0, 0, 8, 1},
+                                    {64, 0, 0, 8, 1}};
 };
 
-template <int Q, int PREC, int BX, int MINB, bool CS, int RS>
+template <int Q, int PREC, int BX, int MINB, bool CS, int RS, bool PIPE>
 int launch_direct(SolverImpl &s, int src, int dst) {
     using S = typename Store<PREC>::S;
     const auto &k = Consts<PREC>::get(s);
     dim3 grid((s.p.Nx + BX - 1) / BX, (s.p.Ny + RS - 1) / RS);
-    k_step_direct<Q, PREC, BX, MINB, CS, RS><<<grid, BX, 0, s.stream>>>(
-        (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
-    return (int)cudaGetLastError();
-}
-
-// ---- two-cells-per-thread variants {BX, MINB} (FP32 and BF16DEV storage),
-// numbered after the direct ones -----------------------------------------------
-struct PairVariants {
-    static constexpr int n = 3;
-    static constexpr int v[n][2] = {{64, 0}, {128, 0}, {64, 8}};
-};
-
-template <int Q, int PREC, int BX, int MINB>
-int launch_pair(SolverImpl &s, int src, int dst) {
-    using S = typename Store<PREC>::S;
-    const auto &k = Consts<PREC>::get(s);
-    dim3 grid((s.p.Nx + 2 * BX - 1) / (2 * BX), s.p.Ny);
-    k_step_pair<Q, PREC, BX, MINB><<<grid, BX, 0, s.stream>>>(
-        (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
+    if constexpr (PIPE)
+        k_step_direct_pipe<Q, PREC, BX, MINB, RS><<<grid, BX, 0, s.stream>>>(
+            (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
+    else
+        k_step_direct<Q, PREC, BX, MINB, CS, RS><<<grid, BX, 0, s.stream>>>(
+            (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
     return (int)cudaGetLastError();
 }
 
 template <int PREC>
 int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
     using V = DirectVariants;
-    if constexpr (PREC != LBM_FP64) {
-        using P = PairVariants;
-        switch (variant - V::n) {
-#define LBM_PAIR_CASE(I)                                                                   \
-        case I:                                                                            \
-            LBM_DISPATCH_Q(s.L.Q, return (launch_pair<QQ, PREC, P::v[I][0], P::v[I][1]>(s, src, dst))); \
-            break;
-            LBM_PAIR_CASE(0)
-            LBM_PAIR_CASE(1)
-            LBM_PAIR_CASE(2)
-#undef LBM_PAIR_CASE
-        default: break;
-        }
-    }
 #define LBM_DIRECT_CASE(I)                                                                 \
     case I:                                                                                \
         LBM_DISPATCH_Q(s.L.Q, return (launch_direct<QQ, PREC, V::v[I][0], V::v[I][1],       \
-                                                    (V::v[I][2] != 0), V::v[I][3]>(s, src, dst))); \
+                                                    (V::v[I][2] != 0), V::v[I][3],            \
+                                                    (V::v[I][4] != 0)>(s, src, dst)));        \
         break;
     switch (variant) {
         LBM_DIRECT_CASE(0)
@@ -102,6 +77,9 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
         LBM_DIRECT_CASE(4)
         LBM_DIRECT_CASE(5)
         LBM_DIRECT_CASE(6)
+        LBM_DIRECT_CASE(7)
+        LBM_DIRECT_CASE(8)
+        LBM_DIRECT_CASE(9)
     default: break;
     }
 #undef LBM_DIRECT_CASE
@@ -109,9 +87,7 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
 }
 
 template <int PREC>
-int Launch<PREC>::direct_variants() {
-    return DirectVariants::n + (PREC == LBM_FP64 ? 0 : PairVariants::n);
-}
+int Launch<PREC>::direct_variants() { return DirectVariants::n; }
 
 template <int PREC>
 int Launch<PREC>::step_cellwarp(SolverImpl &s, int src, int dst) {

@@ -99,31 +99,31 @@ template <class S> __device__ __forceinline__ S store_rounded(double v, uint32_t
 template <> __device__ __forceinline__ double store_rounded<double>(double v, uint32_t) { return v; }
 
 // ---- stochastic rounding of FP32 results (batched path) -----------------------
-// f + t rounded to FP32 stochastically, from 23 uniform random bits: a uniform
-// dither of one unit in the last place U of the round-to-nearest sum, in
-// [-U/2, U/2), is added to the small term before the final addition, so the
-// result is the lower or the upper FP32 neighbour of the exact sum with
-// probabilities that make it unbiased (Connolly, Higham & Mary, SIAM J. Sci.
-// Comput. 43 (2021): stochastic rounding, mode 1).  Round-to-nearest leaves
+// f + t rounded to FP32 stochastically, from 32 random bits x: a uniform
+// dither of one unit in the last place U of f, in [-U/2, U/2), is added to the
+// small term before the final addition, so the result is the lower or the
+// upper FP32 neighbour of the exact sum with probabilities that make it
+// unbiased (Connolly, Higham & Mary, SIAM J. Sci. Comput. 43 (2021):
+// stochastic rounding, mode 1).  Where the sum lies in f's binade or a lower
+// one, U is a whole multiple of the sum's grid spacing and the rounding is
+// exactly unbiased; t + dither is itself rounded on t's grid, which keeps it
+// unbiased to within ~ulp(t) / 2 of a unit (exact where |t| << |f|, the case
+// of a long relaxation time, where it matters most).  Round-to-nearest leaves
 // the same round-off at every step of a steady state, a constant forcing
 // that the slowest relaxation time amplifies (up to ~1e-4 U_w in u_x for tall
-// or dense columns); stochastic rounding makes it zero-mean noise.  t + dither
-// is itself rounded on t's grid, which keeps the rounding unbiased to within
-// ~ulp(t) / 2 of a unit: exact where |t| << |f + t|, the case of a long
-// relaxation time, where the amplification is largest.
-__device__ __forceinline__ float add_sr(float f, float t, uint32_t r23) {
-    const float s = f + t;
-    // exponent bits of ulp(s) = 2^(E - 23) for s in [2^E, 2^(E+1)); clamped to
-    // the smallest normal for |s| < 2^-103
-    const uint32_t e = max(__float_as_uint(s) & 0x7f800000u, 24u << 23) - (23u << 23);
+// or dense columns); stochastic rounding makes it zero-mean noise.
+__device__ __forceinline__ float add_sr(float f, float t, uint32_t x) {
+    // exponent bits of ulp(f) = 2^(E - 23) for f in [2^E, 2^(E+1)); clamped
+    // to the smallest normal for |f| < 2^-103 (f = 0 included)
+    const uint32_t e = max(__float_as_uint(f) & 0x7f800000u, 24u << 23) - (23u << 23);
     const float U = __uint_as_float(e);
-    const float m = __uint_as_float(e | r23);          // uniform in [U, 2U)
+    const float m = __uint_as_float(e | (x & 0x007fffffu));   // uniform in [U, 2U)
     return f + (t + fmaf(-1.5f, U, m));
 }
-// 23 random bits of velocity a from the cell's hash (top bits of a product
-// with an odd multiplier that depends on a)
-__device__ __forceinline__ uint32_t sr_bits23(uint32_t hcell, int a) {
-    return (hcell * (0x9E3779B9u * (2u * (uint32_t)a + 1u))) >> 9;
+// 32 random bits of velocity a from the cell's hash: the high word of its
+// product with an odd multiplier that depends on a
+__device__ __forceinline__ uint32_t sr_bits32(uint32_t hcell, int a) {
+    return __umulhi(hcell, 0x9E3779B9u * (2u * (uint32_t)a + 1u));
 }
 
 // Step count of this launch's source buffer; block 0 writes the count of the
@@ -390,25 +390,9 @@ struct Collision {
         oa = relax(fa, O::add(P, R));
         ob = relax(fb, O::sub(P, R));
     }
-    // the same with the FP32 result rounded stochastically (add_sr; one cell)
-    __device__ __forceinline__ float relax_sr(float f, float eq, uint32_t r23) const {
-        return add_sr(f, __fmaf_rn(nom, f, eq), r23);
-    }
-    __device__ __forceinline__ float rest_sr(float f0, uint32_t hcell) const {
-        return relax_sr(f0, __fmul_rn(cw[0], A0[0]), sr_bits23(hcell, 0));
-    }
-    template <int A>
-    __device__ __forceinline__ void pair_sr(float fa, float fb, float &oa, float &ob,
-                                            uint32_t hcell) const {
-        float P, R;
-        eq_pair<A>(P, R);
-        oa = relax_sr(fa, __fadd_rn(P, R), sr_bits23(hcell, A));
-        ob = relax_sr(fb, __fsub_rn(P, R), sr_bits23(hcell, A + 1));
-    }
-
     // Relaxation of one FP32 cell whose increments t_a = omega (rho w g_a - f_a)
     // conserve mass, momentum and (thermal) energy as exactly as FP32 sums
-    // allow, then added to f_a with stochastic rounding.  In exact arithmetic
+    // allow, then added to f_a with stochastic rounding (add_sr).  In exact arithmetic
     // the BGK step conserves them (Sec. II: the equilibrium has the cell's rho,
     // u and T), so the correction below is zero; in FP32 the rounding of rho, u
     // and T and of the lattice constants leaves each collision a small source
@@ -450,8 +434,8 @@ struct Collision {
                 t3 = ta;
                 t4 = tb;
             } else {
-                o[A] = add_sr(f[A], ta, sr_bits23(hcell, A));
-                o[A + 1] = add_sr(f[A + 1], tb, sr_bits23(hcell, A + 1));
+                o[A] = add_sr(f[A], ta, sr_bits32(hcell, A));
+                o[A + 1] = add_sr(f[A + 1], tb, sr_bits32(hcell, A + 1));
             }
         });
         float t0 = __fmaf_rn(nom, f[0], __fmul_rn(cw[0], A0[0]));
@@ -470,11 +454,11 @@ struct Collision {
             M = __fsub_rn(M, E);
         }
         t0 = __fsub_rn(t0, M);
-        o[0] = add_sr(f[0], t0, sr_bits23(hcell, 0));
-        o[1] = add_sr(f[1], t1, sr_bits23(hcell, 1));
-        o[2] = add_sr(f[2], t2, sr_bits23(hcell, 2));
-        o[3] = add_sr(f[3], t3, sr_bits23(hcell, 3));
-        o[4] = add_sr(f[4], t4, sr_bits23(hcell, 4));
+        o[0] = add_sr(f[0], t0, sr_bits32(hcell, 0));
+        o[1] = add_sr(f[1], t1, sr_bits32(hcell, 1));
+        o[2] = add_sr(f[2], t2, sr_bits32(hcell, 2));
+        o[3] = add_sr(f[3], t3, sr_bits32(hcell, 3));
+        o[4] = add_sr(f[4], t4, sr_bits32(hcell, 4));
     }
 };
 

@@ -45,6 +45,11 @@ namespace {
 // per thread on one CTA (~1 s at ~4 us per step and 256 rows)
 constexpr double kLongRowSteps = 2.5e5;
 constexpr long long kAlignElems = 64;        // 256-byte granularity (floats)
+// A request's collision rounds to nearest while its change per check is above
+// kPreciseFrom x tol (far from the steady state the state changes every step,
+// so round-off does not freeze into a bias), then conserving increments with
+// stochastic rounding for the remaining e-folding times to the steady state.
+constexpr double kPreciseFrom = 20.0;
 
 struct Pending {
     uint64_t id;
@@ -137,6 +142,13 @@ struct ServerImpl {
     const LatticeHost &lattice(int kind) const {
         return lat[kind == 17 ? 0 : kind == 25 ? 1 : kind == 26 ? 2 : 3];
     }
+    // chunks per launch of a slot on a cluster of cl CTAs: the configured
+    // (autotuned) value of its class, else the built-in rule
+    int sub_for(int cl) const {
+        for (int c = 0; c < kBatchClasses; ++c)
+            if (kBatchClassCL[c] == cl && cfg.class_sub[c] > 0) return cfg.class_sub[c];
+        return batch_sub_chunks(cl);
+    }
 
     // ---- pool allocator (first fit, coalescing) ---------------------------------
     long long alloc(long long n) {
@@ -193,7 +205,7 @@ struct ServerImpl {
         d.Ny = r.Ny;
         d.cur = 0;
         d.cl = cl;
-        d.sub = batch_sub_chunks(cl);
+        d.sub = sub_for(cl);
         // Steps per chunk launch: cheaper slots run more steps, so that every
         // CTA of a launch takes about as long (cfg.chunk_steps x 333 cost
         // units); the cost model is the velocity count times the rows per
@@ -216,6 +228,8 @@ struct ServerImpl {
         d.max_steps = r.max_steps;
         d.u_ref = std::max(std::fabs(r.u_wall[0]), std::fabs(r.u_wall[1]));
         if (!(d.u_ref > 0)) d.u_ref = 1.0;
+        d.mass0 = (double)r.Ny;                  // rho = 1 at admission
+        d.precise_from = kPreciseFrom * r.tol;
         // incoming terms per wall (Sec. III: at layer l the velocities with
         // e.n < -l); the bottom list takes e_y < 0 at rows 0..|e_y|-1, the top
         // list e_y > 0 at rows Ny-1.. (distance from the wall)
@@ -424,7 +438,7 @@ struct ServerImpl {
             const int from_cl = h_desc[m.from].cl;
             h_desc[m.to] = h_desc[m.from];
             h_desc[m.to].cl = m.cl;
-            h_desc[m.to].sub = batch_sub_chunks(m.cl);
+            h_desc[m.to].sub = sub_for(m.cl);
             h_status[m.to] = h_status[m.from];
             slots[m.to] = slots[m.from];
             used_ctas += m.cl - from_cl;
@@ -692,9 +706,14 @@ int lbm_server_create(const lbm_server_cfg *cfg, void *stream, lbm_server **out)
     try {
         if (!cfg || !out) { set_error("NULL argument"); return LBM_EINVAL; }
         *out = nullptr;
+        bool subs_ok = true;
+        for (int c = 0; c < kBatchClasses; ++c)
+            subs_ok = subs_ok && cfg->class_sub[c] >= 0 && cfg->class_sub[c] <= kMaxSub;
         if (cfg->max_slots < 1 || cfg->max_slots > 4096 || cfg->chunk_steps < 1 ||
-            cfg->mem_budget_bytes < 4096 || cfg->precision != LBM_FP32 || cfg->cluster_rows < 32) {
-            set_error("bad server configuration (slots 1..4096, chunk >= 1, FP32, cluster_rows >= 32)");
+            cfg->mem_budget_bytes < 4096 || cfg->precision != LBM_FP32 || cfg->cluster_rows < 32 ||
+            !subs_ok) {
+            set_error("bad server configuration (slots 1..4096, chunk >= 1, FP32, cluster_rows >= 32, "
+                      "class_sub 0..16)");
             return LBM_EINVAL;
         }
         lbm_server *h = new lbm_server;
@@ -967,3 +986,137 @@ int lbm_batch_solve(const lbm_server_cfg *cfg, void *stream, const lbm_request *
 }
 
 }  // extern "C"
+
+namespace {
+
+// Wall seconds from the first submit to the drain of n identical fixed-step
+// requests (lattice kind, Ny rows, Kn, walls -+0.1, tol 0: never converged)
+// on a server with cfg; *cell_steps gets the lattice updates they ran.
+int time_fixed_steps(const lbm_server_cfg &cfg, void *stream, int kind, int Ny, double Kn, int n,
+                     int64_t steps, double *seconds, double *cell_steps) {
+    lbm_server *h = nullptr;
+    if (int rc = lbm_server_create(&cfg, stream, &h)) return rc;
+    lbm_request r;
+    std::memset(&r, 0, sizeof(r));
+    r.lattice = kind;
+    r.Ny = Ny;
+    r.thermal = kind == LBM_LATTICE_D2Q37 ? 1 : 0;
+    r.eq_order = r.thermal ? 4 : 2;
+    r.Kn = Kn;
+    r.mu_exp = 1.0;
+    r.u_wall[0] = -0.1;
+    r.u_wall[1] = 0.1;
+    r.T_wall[0] = r.T_wall[1] = 1.0;
+    r.tol = 1e-300;
+    r.max_steps = steps;
+    r.accom[0] = r.accom[1] = 1.0;
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = LBM_OK;
+    for (int i = 0; i < n && !rc; ++i) rc = lbm_server_submit(h, &r, nullptr);
+    if (!rc) rc = lbm_server_drain(h, 600.0);
+    *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    std::vector<lbm_result> res(n > 0 ? n : 1);
+    int32_t got = 0;
+    if (!rc) rc = lbm_server_poll(h, res.data(), n, &got);
+    double cs = 0;
+    for (int i = 0; i < got; ++i) cs += (double)res[i].steps * Ny;
+    *cell_steps = cs;
+    lbm_server_destroy(h);
+    return rc;
+}
+
+double median(std::vector<double> v) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const size_t m = v.size() / 2;
+    return v.size() % 2 ? v[m] : 0.5 * (v[m - 1] + v[m]);
+}
+
+}  // namespace
+
+extern "C" int lbm_server_autotune(lbm_server_cfg *cfg, void *stream, lbm_server_tuning *report) {
+    if (!cfg) { set_error("NULL configuration"); return LBM_EINVAL; }
+    const auto t_start = std::chrono::steady_clock::now();
+    lbm_server_tuning rep;
+    std::memset(&rep, 0, sizeof(rep));
+    const int kinds[3] = {LBM_LATTICE_D2Q17, LBM_LATTICE_D2Q25, LBM_LATTICE_D2Q37};
+    const int heights[3] = {256, 1024, 4096};
+    if (int rc = preload_batch_kernels()) {
+        set_error(std::string("batch kernels: ") + cudaGetErrorString((cudaError_t)rc));
+        return LBM_ECUDA;
+    }
+    const int max_cl = batch_max_cluster();
+    // ---- lone columns on every usable cluster size --------------------------
+    // a lone long request (small Kn) gets the largest usable cluster within the
+    // CTA budget: the budget picks the cluster size; long chunks keep the
+    // host's per-launch work out of the step time
+    std::vector<double> ratio[kBatchClasses], rows_best;
+    for (int li = 0; li < 3; ++li) {
+        for (int hi = 0; hi < 3; ++hi) {
+            const int Ny = heights[hi];
+            rep.ny[hi] = Ny;
+            double t1 = 0, tbest = 1e300;
+            for (int c = 0; c < kBatchClasses; ++c) {
+                const int cl = kBatchClassCL[c];
+                if (cl > max_cl || batch_cluster_size(Ny, 32, cl, max_cl) != cl) continue;
+                lbm_server_cfg lc = *cfg;
+                lc.max_slots = cl;
+                lc.cluster_rows = 32;
+                lc.chunk_steps = 1000;
+                lc.mem_budget_bytes = (size_t)64 << 20;
+                for (int k = 0; k < kBatchClasses; ++k) lc.class_sub[k] = 0;
+                const int64_t steps = 4000;
+                double sec = 0, cells = 0;
+                if (int rc = time_fixed_steps(lc, stream, kinds[li], Ny, 1e-3, 1, steps, &sec, &cells))
+                    return rc;
+                const double us = cells > 0 ? sec / (cells / Ny) * 1e6 : 0.0;
+                rep.lone_us[li][hi][c] = us;
+                if (c == 0) t1 = us;
+                if (us > 0 && us < tbest) tbest = us;
+                if (c > 0 && t1 > 0 && us > 0) ratio[c].push_back(t1 / us);
+            }
+            // the smallest cluster within 15 % of the fastest: its rows per CTA
+            for (int c = 0; c < kBatchClasses; ++c) {
+                const double us = rep.lone_us[li][hi][c];
+                if (us > 0 && us <= 1.15 * tbest) {
+                    rows_best.push_back((double)batch_rows_per_cta(Ny, kBatchClassCL[c]));
+                    break;
+                }
+            }
+        }
+    }
+    // ---- chunk length on a full GPU of one-CTA columns ------------------------
+    const int chunks[5] = {25, 50, 100, 200, 400};
+    double best = 0;
+    for (int i = 0; i < 5; ++i) {
+        lbm_server_cfg lc = *cfg;
+        lc.cluster_rows = kMaxNy;
+        lc.chunk_steps = chunks[i];
+        lc.mem_budget_bytes = std::min<size_t>(cfg->mem_budget_bytes, (size_t)1 << 30);
+        double sec = 0, cells = 0;
+        if (int rc = time_fixed_steps(lc, stream, LBM_LATTICE_D2Q25, 128, 0.1, cfg->max_slots, 6000,
+                                      &sec, &cells))
+            return rc;
+        rep.chunk_try[i] = chunks[i];
+        rep.chunk_glups[i] = sec > 0 ? cells / sec / 1e9 : 0.0;
+        best = std::max(best, rep.chunk_glups[i]);
+    }
+    int chunk = chunks[4];
+    for (int i = 0; i < 5; ++i)
+        if (rep.chunk_glups[i] >= 0.95 * best) { chunk = chunks[i]; break; }
+    // ---- the choices ------------------------------------------------------------
+    cfg->chunk_steps = chunk;
+    cfg->class_sub[0] = 1;
+    for (int c = 1; c < kBatchClasses; ++c) {
+        const double m = median(ratio[c]);
+        cfg->class_sub[c] = m > 0 ? std::max(1, std::min(kMaxSub, (int)std::lround(m))) : 0;
+    }
+    if (!rows_best.empty()) {
+        int rows = (int)median(rows_best);
+        rows = std::max(32, std::min(1024, (rows + kResidualChunk - 1) / kResidualChunk * kResidualChunk));
+        cfg->cluster_rows = rows;
+    }
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (report) *report = rep;
+    return LBM_OK;
+}

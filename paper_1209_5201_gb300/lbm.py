@@ -65,7 +65,13 @@ class lbm_result(C.Structure):
 class lbm_server_cfg(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_slots", C.c_int32),
                 ("chunk_steps", C.c_int32), ("precision", C.c_int32), ("use_graph", C.c_int32),
-                ("cluster_rows", C.c_int32)]
+                ("cluster_rows", C.c_int32), ("class_sub", C.c_int32 * 5)]
+
+
+class lbm_server_tuning(C.Structure):
+    _fields_ = [("ny", C.c_int32 * 3), ("lone_us", C.c_double * 5 * 3 * 3),
+                ("chunk_try", C.c_int32 * 5), ("chunk_glups", C.c_double * 5),
+                ("seconds", C.c_double)]
 
 
 class lbm_server_metrics(C.Structure):
@@ -132,6 +138,7 @@ _SIGS = {
     "lbm_server_drain": ([_VP, C.c_double], C.c_int),
     "lbm_server_stats": ([_VP, C.POINTER(lbm_server_metrics)], C.c_int),
     "lbm_server_destroy": ([_VP], C.c_int),
+    "lbm_server_autotune": ([C.POINTER(lbm_server_cfg), _VP, C.POINTER(lbm_server_tuning)], C.c_int),
     "lbm_batch_solve": ([C.POINTER(lbm_server_cfg), _VP, C.POINTER(lbm_request), C.c_int32,
                          C.POINTER(lbm_result), C.c_double], C.c_int),
     "lbm_residual_noalloc": ([_VP, _VP, _VP, _VP, C.c_int64, C.c_double, C.c_int32, _VP, _VP],
@@ -434,6 +441,18 @@ def lbm_server_destroy(h) -> None:
     load().lbm_server_destroy(h)
 
 
+def lbm_server_autotune(cfg: lbm_server_cfg, stream: int = 0):
+    """Tune cfg in place (chunk_steps, cluster_rows, class_sub); returns the
+    measured times as a dict."""
+    rep = lbm_server_tuning()
+    _check(load().lbm_server_autotune(C.byref(cfg), _VP(stream or None), C.byref(rep)),
+           "lbm_server_autotune")
+    return {"ny": list(rep.ny),
+            "lone_us": [[list(rep.lone_us[li][hi]) for hi in range(3)] for li in range(3)],
+            "chunk_try": list(rep.chunk_try), "chunk_glups": list(rep.chunk_glups),
+            "seconds": rep.seconds}
+
+
 def lbm_batch_solve(cfg: lbm_server_cfg, reqs, stream: int = 0, timeout_s: float = 600.0):
     arr = (lbm_request * len(reqs))(*reqs)
     out = (lbm_result * max(1, len(reqs)))()
@@ -531,14 +550,20 @@ class Server:
     thread owns its own CUDA stream."""
 
     def __init__(self, mem_budget_bytes: int = 40 << 30, max_slots: int = 256,
-                 chunk_steps: int = 100, use_graph: bool = True, cluster_rows: int = 256):
+                 chunk_steps: int = 100, use_graph: bool = True, cluster_rows: int = 256,
+                 cfg: "lbm_server_cfg | None" = None):
+        """A server with the given settings, or with `cfg` as a whole (e.g. one
+        lbm_server_autotune filled in)."""
         import torch
-        self.cfg = lbm_server_cfg_default()
-        self.cfg.mem_budget_bytes = int(mem_budget_bytes)
-        self.cfg.max_slots = int(max_slots)
-        self.cfg.chunk_steps = int(chunk_steps)
-        self.cfg.use_graph = int(use_graph)
-        self.cfg.cluster_rows = int(cluster_rows)
+        if cfg is not None:
+            self.cfg = cfg
+        else:
+            self.cfg = lbm_server_cfg_default()
+            self.cfg.mem_budget_bytes = int(mem_budget_bytes)
+            self.cfg.max_slots = int(max_slots)
+            self.cfg.chunk_steps = int(chunk_steps)
+            self.cfg.use_graph = int(use_graph)
+            self.cfg.cluster_rows = int(cluster_rows)
         self.stream = torch.cuda.Stream()
         self.h = lbm_server_create(self.cfg, self.stream.cuda_stream)
 

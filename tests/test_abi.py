@@ -188,3 +188,31 @@ def test_binding_covers_every_declaration_with_its_arity(lbm):
     for name, n in decls.items():
         assert name in lbm._SIGS, name
         assert len(lbm._SIGS[name][0]) == n, (name, n, len(lbm._SIGS[name][0]))
+
+
+def test_struct_layouts_match_the_header(lbm, tmp_path):
+    # every struct the binding mirrors has the header's size and field offsets
+    # (a C program compiled against include/lbm.h prints them)
+    import ctypes
+    import subprocess
+    structs = ["lbm_params", "lbm_stats", "lbm_request", "lbm_result", "lbm_server_cfg",
+               "lbm_server_metrics", "lbm_server_tuning"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void) {"]
+    for st in structs:
+        py = getattr(lbm, st)
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for name, _ in py._fields_:
+            lines.append(f'printf("{st}.{name} %zu\\n", offsetof({st}, {name}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+    for st in structs:
+        py = getattr(lbm, st)
+        assert int(got[st]) == ctypes.sizeof(py), st
+        for name, _ in py._fields_:
+            assert int(got[f"{st}.{name}"]) == getattr(py, name).offset, (st, name)

@@ -333,3 +333,41 @@ def test_cancel_running_and_queued_requests(lbm):
     s.drain(60)
     assert s.poll(4)[0].status == lbm.LBM_OK
     s.close()
+
+
+def test_autotune_fills_the_configuration_and_leaves_results_unchanged(lbm):
+    # the batched-path autotuner times lone columns on every usable cluster
+    # size and full-GPU batches at several chunk lengths, and writes its
+    # choices into the configuration; a server with the tuned cluster rows and
+    # chunks per launch gives the same results, bit for bit, as one with the
+    # built-in rules and the same chunk length
+    import torch
+    cfg = lbm.lbm_server_cfg_default()
+    cfg.mem_budget_bytes = 1 << 28
+    cfg.max_slots = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    rep = lbm.lbm_server_autotune(cfg)
+    assert cfg.chunk_steps in (25, 50, 100, 200, 400)
+    assert 32 <= cfg.cluster_rows <= 1024 and cfg.cluster_rows % 32 == 0
+    assert cfg.class_sub[0] == 1 and all(0 <= v <= 16 for v in cfg.class_sub)
+    assert cfg.class_sub[1] >= 1 and cfg.class_sub[3] >= 1          # 2- and 8-CTA clusters
+    for li in range(3):
+        for hi in range(3):
+            assert rep["lone_us"][li][hi][0] > 0                    # one CTA always usable
+    assert all(g > 0 for g in rep["chunk_glups"]) and rep["seconds"] > 0
+    # results do not depend on the tuned cluster rows or chunks per launch
+    tuned = lbm.Server(cfg=cfg)
+    base = lbm.lbm_server_cfg_default()
+    base.mem_budget_bytes, base.max_slots, base.chunk_steps = 1 << 28, cfg.max_slots, cfg.chunk_steps
+    plain = lbm.Server(cfg=base)
+    items = LONG[1:4] + MIX[:3]
+    out = []
+    for s in (tuned, plain):
+        ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=1e-30, max_steps=3000))
+               for lat, Ny, Kn, Uw, Tw in items]
+        s.drain(300)
+        res = {r.id: r for r in s.poll(64)}
+        out.append([(res[i].steps, res[i].residual, *s.fetch(i, it[1])) for i, it in zip(ids, items)])
+        s.close()
+    for it, a, b in zip(items, *out):
+        assert a[0] == b[0] and a[1] == b[1], it
+        assert all(np.array_equal(x, y) for x, y in zip(a[2:], b[2:])), it

@@ -41,11 +41,12 @@ MUTATIONS = {
         lambda o: pins.test_equilibrium_maxwellian_moments(o, "D2Q37", 3, True)),
     # normaliser of Eq. (11)-(12) counting each outgoing velocity once
     "normaliser_once_per_velocity": (
-        "if (nsgn * L->ey[a] > l) den += gw[a];", "if (nsgn * L->ey[a] > 0 && l == 0) den += gw[a];",
+        "if (nsgn * L->ey[a] - P->vn[wall] > l) den += gw[a];",
+        "if (nsgn * L->ey[a] - P->vn[wall] > 0 && l == 0) den += gw[a];",
         lambda o: pins.test_wall_zero_net_mass_flux_and_bookkeeping(o, "D2Q37")),
     # incoming criterion of Sec. III off by one layer
     "incoming_off_by_one": (
-        "if (nsgn * L->ey[a] < -l)", "if (nsgn * L->ey[a] < -l - 1)",
+        "if (nsgn * L->ey[a] - vn < -l)", "if (nsgn * L->ey[a] - vn < -l - 1)",
         lambda o: pins.test_wall_zero_net_mass_flux_and_bookkeeping(o, "D2Q25")),
     # ghost row of the top wall mirrored the wrong way
     "top_ghost_row": (
@@ -74,8 +75,8 @@ MUTATIONS = {
         lambda o: pins.test_specular_walls_exchange_no_tangential_momentum(o)),
     # wall distribution evaluated at the wrong wall's velocity
     "wall_velocity_swapped": (
-        "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[wall], 0.0, Tw, gw);",
-        "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[1 - wall], 0.0, Tw, gw);",
+        "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[wall], nsgn * P->vn[wall] * L->r, Tw, gw);",
+        "orc_equilibrium(L, P->eq_order, 1.0, P->u_wall[1 - wall], nsgn * P->vn[wall] * L->r, Tw, gw);",
         lambda o: pins.test_couette_antisymmetry(o)),
     # f taken as f~: the Sec. II conversion of the stress moments dropped
     "flux_conversion_dropped": (
