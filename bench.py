@@ -418,22 +418,25 @@ def run_serving(lbm, n=10000, seed=11, rate=200.0, tol=SOLVE_TOL):
             "cpu_baseline": oracle_leg(reqs[:head], results[:head], fields, limit=50)}
 
 
-def run_slots(lbm, n, lattice, Ny, Kn, steps, cluster_rows=256):
+def run_slots(lbm, n, lattice, Ny, Kn, steps, cluster_rows=256, rounding=0):
     """Rate of the batched path at a fixed step count: n identical
     single-column requests (walls -+0.1) that never meet their tolerance,
     each run for `steps` steps (rounded up to whole chunks); wall time from
-    the first submit to the drain."""
+    the first submit to the drain.  rounding: 0 (auto, round-to-nearest for a
+    fixed step count), 1 (stochastic with conserving increments), 2 (nearest)."""
     srv = lbm.Server(mem_budget_bytes=8 << 30, max_slots=resident_ctas(), chunk_steps=100,
                      cluster_rows=cluster_rows)
     t0 = time.perf_counter()
     for _ in range(n):
-        srv.submit(lbm.make_request(lattice, Ny, Kn, 0.1, tol=1e-30, max_steps=steps))
+        srv.submit(lbm.make_request(lattice, Ny, Kn, 0.1, tol=1e-30, max_steps=steps,
+                                    rounding=rounding))
     srv.drain(600)
     wall = time.perf_counter() - t0
     res = srv.poll(n)
     srv.close()
     mean_steps = sum(r.steps for r in res) / len(res)
     return {"slots": n, "lattice": lattice, "Ny": Ny, "Kn": Kn, "cluster_rows": cluster_rows,
+            "rounding": rounding,
             "mean_steps": mean_steps, "wall_s": wall,
             "us_per_step_per_slot": wall / mean_steps * 1e6,
             "GLUPS": n * mean_steps * Ny / wall / 1e9}
@@ -575,6 +578,8 @@ def main():
     ap.add_argument("--Kn", type=float, default=0.005)
     ap.add_argument("--slot-steps", type=int, default=20000)
     ap.add_argument("--cluster-rows", type=int, default=256)
+    ap.add_argument("--rounding", type=int, default=0, choices=[0, 1, 2],
+                    help="slots workload: 0 auto, 1 stochastic, 2 nearest")
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--no-extras", action="store_true",
                     help="grid line only (skip the batched and serving runs)")
@@ -608,7 +613,7 @@ def main():
                 r = run_serving(lbm, n=args.serving_requests)
             else:
                 r = run_slots(lbm, args.slots, args.lattice, args.Ny, args.Kn, args.slot_steps,
-                              args.cluster_rows)
+                              args.cluster_rows, args.rounding)
             print(json.dumps({"workload": args.workload, **r}))
         return 0
     cfg = lbm.Config(lattice="D2Q37", Nx=args.Nx, Ny=args.Ny, eq_order=4, thermal=True,

@@ -185,6 +185,18 @@ int lbm_solver_set_f(lbm_solver *s, const double *f);
 int lbm_solver_macros(lbm_solver *s, double *rho, double *ux, double *uy,
                       double *T);
 
+/* Steady-state estimate of a noisy iteration: advance the solver by nsteps
+ * steps (asynchronous launches, then a synchronisation) and return the time
+ * mean of the Eq. (3) fields over those steps, accumulated in FP64 on the
+ * device (host buffers of Nx*Ny, any may be NULL).  The paper's scheme is
+ * deterministic; with BF16 deviation storage the stored values are rounded
+ * stochastically, so a steady state carries zero-mean noise (about 4e-3 U_w
+ * in u_x on the 64-row Couette column) and the mean over a few thousand steps
+ * is the steady field to about a tenth of that.  Errors: LBM_EINVAL,
+ * LBM_ECUDA, LBM_ETIMEOUT (staged kernel). */
+int lbm_solver_macros_mean(lbm_solver *s, int64_t nsteps, double *rho, double *ux, double *uy,
+                           double *T);
+
 /* Stress and heat flux (Sec. II: f~ = f + dt/(2 tau) (f - f^eq), so
  * f = (f~ + dt/(2 tau) f^eq) / (1 + dt/(2 tau))) of the pre-collision f~ that
  * the next step's streaming and wall fill produce from the current state:
@@ -349,7 +361,19 @@ typedef struct lbm_request {
     int64_t max_steps;    /* give up after this many steps                     */
     uint64_t tag;         /* caller's tag, returned in the result              */
     double accom[2];      /* wall accommodation, as in lbm_params (1: diffuse) */
+    int32_t rounding;     /* LBM_ROUND_*: how the FP32 collision rounds        */
 } lbm_request;
+
+/* lbm_request.rounding.  AUTO: round to nearest while the change per check
+ * is above 5 tol, then increments that conserve mass, momentum (and energy)
+ * added with stochastic rounding, the admission mass restored at the switch
+ * (round-to-nearest at a steady state leaves the same round-off every step,
+ * which the slowest relaxation time amplifies).  STOCHASTIC: the conserving,
+ * stochastically rounded increments from the first step (e.g. for runs to a
+ * fixed step count).  NEAREST: round to nearest throughout. */
+#define LBM_ROUND_AUTO        0
+#define LBM_ROUND_STOCHASTIC  1
+#define LBM_ROUND_NEAREST     2
 
 typedef struct lbm_result {
     uint64_t id, tag;
@@ -447,8 +471,9 @@ typedef struct lbm_server_tuning {
                                    split is not usable or not schedulable)    */
     int32_t chunk_try[5];       /* chunk lengths timed on a full GPU          */
     double chunk_glups[5];      /* lattice updates per second (1e9) of
-                                   max_slots one-CTA D2Q25 columns of 128 rows
-                                   at each chunk length, launches included     */
+                                   max_slots one-CTA D2Q37 columns of 256 rows
+                                   at each chunk length, launches included
+                                   (best of two runs)                          */
     double seconds;             /* wall time of the autotuning                */
 } lbm_server_tuning;
 

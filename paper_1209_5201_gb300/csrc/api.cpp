@@ -630,6 +630,35 @@ int lbm_solver_macros(lbm_solver *h, double *rho, double *ux, double *uy, double
     API_END
 }
 
+int lbm_solver_macros_mean(lbm_solver *h, int64_t nsteps, double *rho, double *ux, double *uy,
+                           double *T) {
+    API_BEGIN
+    NvtxRange nvtx("lbm_solver_macros_mean");
+    if (!h || nsteps < 1) { set_error("NULL solver or nsteps < 1"); return LBM_EINVAL; }
+    SolverImpl &s = h->s;
+    const size_t n = (size_t)s.p.Nx * s.p.Ny;
+    double *d[4] = {s.stage, s.stage + n, s.stage + 2 * n, s.stage + 3 * n};
+    const int kern = effective_kernel(s);
+    for (int64_t i = 0; i < nsteps; ++i) {
+        CU(launch_step_variant(s, s.cur, s.cur ^ 1, kern, s.variant));
+        s.cur ^= 1;
+        ++s.steps;
+        CU(dispatch_prec(s.p.precision, [&](auto P) {
+            return Launch<decltype(P)::value>::macros(s, d[0], d[1], d[2], d[3], i > 0 ? 1 : 0);
+        }));
+    }
+    double *hst[4] = {rho, ux, uy, T};
+    for (int i = 0; i < 4; ++i)
+        if (hst[i]) CU(cudaMemcpyAsync(hst[i], d[i], n * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
+    CU(cudaStreamSynchronize(s.stream));
+    if (int rc = check_device_error(s)) return rc;
+    for (int i = 0; i < 4; ++i)
+        if (hst[i])
+            for (size_t c = 0; c < n; ++c) hst[i][c] /= (double)nsteps;
+    return LBM_OK;
+    API_END
+}
+
 int lbm_solver_fluxes(lbm_solver *h, double *sxx, double *sxy, double *syy, double *qx,
                       double *qy) {
     API_BEGIN

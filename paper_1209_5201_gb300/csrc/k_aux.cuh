@@ -134,10 +134,12 @@ __global__ void k_plane_from_f64(typename Store<PREC>::S *f, const float *rplane
 // Eq. (3) fields of every cell of the stored state; T is the kinetic
 // temperature sum f |c - u|^2 / (2 rho).  Per-cell arithmetic in the storage's
 // compute type (FP32 or FP64), outputs FP64.  Any output may be NULL.
+// acc: add the fields to the outputs instead of writing them (acc == 1), or
+// write them (acc == 0).
 template <int Q, int PREC>
 __global__ void k_macros(const typename Store<PREC>::S *f, const float *rplane,
                          const __grid_constant__ KConsts<typename Store<PREC>::C> k,
-                         double *rho, double *ux, double *uy, double *T) {
+                         double *rho, double *ux, double *uy, double *T, int acc) {
     using L = Lat<Q>;
     using C = typename Store<PREC>::C;
     const long long n = (long long)k.Nx * k.Ny;
@@ -164,10 +166,11 @@ __global__ void k_macros(const typename Store<PREC>::S *f, const float *rplane,
         if constexpr (Store<PREC>::shifted) se += k.e2w;
         // rho D T = sum f |c - u|^2 = r^2 sum e^2 f - rho u^2
         const C e = k.r2 * se - rh * (u * u + v * v);
-        if (rho) rho[c] = (double)rh;
-        if (ux) ux[c] = (double)u;
-        if (uy) uy[c] = (double)v;
-        if (T) T[c] = (double)(e / (C(2) * rh));
+        const double o[4] = {(double)rh, (double)u, (double)v, (double)(e / (C(2) * rh))};
+        double *out[4] = {rho, ux, uy, T};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (out[i]) out[i][c] = acc ? out[i][c] + o[i] : o[i];
         (void)fv;
     }
 }

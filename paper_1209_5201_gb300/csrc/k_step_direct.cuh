@@ -110,15 +110,30 @@ __device__ __forceinline__ void collide_store(const typename Store<PREC>::C (&f)
     const bool image = x < kPadL || x >= k.Nx - kPadL;
     if (!image) {
         S *__restrict__ dst = fout + (j * k.pitch + x + kPadL);
+        if constexpr (Store<PREC>::dev) {
+            // BF16: the rest velocity alone, then each pair (a, a + 1) rounded
+            // by one conversion (the same bits as store_rounded)
+            const float v0 = f_to_dev(o[0], k.w[0], col.rho);
+            const uint32_t d0 = bf16x2_rounded(v0, v0, hcell * 0x9E3779B9u);   // upper: sr_bits(h, 0)
+            unsigned short *d16 = reinterpret_cast<unsigned short *>(dst);
+            d16[k.off_dst[0]] = (unsigned short)(d0 >> 16);
+            PairLoop<1, Q>::run([&](auto ic) {
+                constexpr int A = decltype(ic)::value;
+                const float va = f_to_dev(o[A], k.w[A], col.rho);
+                const float vb = f_to_dev(o[A + 1], k.w[A + 1], col.rho);
+                const uint32_t d = bf16x2_rounded(va, vb, sr_bits_pair(hcell, A));
+                d16[k.off_dst[A]] = (unsigned short)(d >> 16);
+                d16[k.off_dst[A + 1]] = (unsigned short)d;
+            });
+            rout[j * k.pitch + x + kPadL] = (float)col.rho;
+        } else {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            C v = o[a];
-            if constexpr (Store<PREC>::dev) v = f_to_dev(v, k.w[a], col.rho);
-            const S sv = store_rounded<S>(v, sr_bits(hcell, a));
-            if (CS) store_cs<S>(dst + k.off_dst[a], sv);
-            else dst[k.off_dst[a]] = sv;
+            for (int a = 0; a < Q; ++a) {
+                const S sv = store_rounded<S>(o[a], sr_bits(hcell, a));
+                if (CS) store_cs<S>(dst + k.off_dst[a], sv);
+                else dst[k.off_dst[a]] = sv;
+            }
         }
-        if constexpr (Store<PREC>::dev) rout[j * k.pitch + x + kPadL] = (float)col.rho;
     } else {
         const long long roff = (long long)j * k.pitch;
 #pragma unroll
@@ -176,49 +191,6 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
     if (x >= k.Nx) return;
     for (int j = j0; j < j1; ++j)
         step_cell<Q, PREC, CS>(fin, fout, rin, rout, k, x, j, s_min[j < L::N ? 0 : 1], seed);
-}
-
-// Software-pipelined row strip: a block owns BX columns of RS consecutive
-// rows; in a strip clear of both walls every thread issues the loads of its
-// next row before it collides the current one, so the next row's 37 loads
-// are in flight while the ALU works (a strip that touches a wall row steps
-// its rows one by one, as k_step_direct does).
-template <int Q, int PREC, int BX, int MINB, int RS>
-__global__ void __launch_bounds__(BX, MINB)
-k_step_direct_pipe(const typename Store<PREC>::S *__restrict__ fin,
-                   typename Store<PREC>::S *__restrict__ fout, const float *__restrict__ rin,
-                   float *__restrict__ rout,
-                   const __grid_constant__ KConsts<typename Store<PREC>::C> k) {
-    using L = Lat<Q>;
-    using C = typename Store<PREC>::C;
-    __shared__ double s_min[2][BX + 6];
-    const int x0 = blockIdx.x * BX;
-    const int x = x0 + threadIdx.x;
-    const int j0 = blockIdx.y * RS;
-    const int j1 = min(k.Ny, j0 + RS);
-    const bool bot = j0 < L::N, top = j1 > k.Ny - L::N;
-    if (bot) wall_prologue<Q, PREC, BX>(fin, rin, k, 0, x0, s_min[0]);
-    if (top) wall_prologue<Q, PREC, BX>(fin, rin, k, 1, x0, s_min[1]);
-    if (bot || top) __syncthreads();
-    uint32_t seed = 0;
-    if constexpr (Store<PREC>::dev)
-        seed = step_count(fin, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
-    if (x >= k.Nx) return;
-    if (bot || top) {
-        for (int j = j0; j < j1; ++j)
-            step_cell<Q, PREC, false>(fin, fout, rin, rout, k, x, j, s_min[j < L::N ? 0 : 1], seed);
-        return;
-    }
-    C cur[Q];
-    pull<Q, PREC, false>(fin, rin, k, x, j0, nullptr, cur);
-#pragma unroll 1
-    for (int j = j0; j < j1; ++j) {
-        C nxt[Q];
-        if (j + 1 < j1) pull<Q, PREC, false>(fin, rin, k, x, j + 1, nullptr, nxt);
-        collide_store<Q, PREC, false>(cur, fout, rout, k, x, j, seed);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) cur[a] = nxt[a];
-    }
 }
 
 }  // namespace lbm

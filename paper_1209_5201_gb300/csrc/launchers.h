@@ -18,7 +18,9 @@ struct Launch {
                            const double *uy, const double *T);
     static int plane_to_f64(SolverImpl &s, int a, double *out);
     static int plane_from_f64(SolverImpl &s, int a, const double *in);
-    static int macros(SolverImpl &s, double *rho, double *ux, double *uy, double *T);
+    // Eq. (3) fields into FP64 device planes; acc = 1 adds them instead
+    static int macros(SolverImpl &s, double *rho, double *ux, double *uy, double *T,
+                      int acc = 0);
     static int fluxes(SolverImpl &s, double *sxx, double *sxy, double *syy, double *qx,
                       double *qy);
     static int wall_mass(SolverImpl &s, double *m_in);

@@ -36,27 +36,21 @@ inline int aux_blocks(long long n) {
     default: return (int)cudaErrorInvalidValue;                 \
     }
 
-// ---- direct kernel variants {BX, MINB, CS, RS, PIPE} ----------------------------
-// RS: rows per block; PIPE: software-pipelined row strip (k_step_direct_pipe)
+// ---- direct kernel variants {BX, MINB, CS, RS} ----------------------------------
+// RS: rows per block
 struct DirectVariants {
-    static constexpr int n = 10;
-    static constexpr int v[n][5] = {{128, 0, 0, 1, 0}, {64, 0, 0, 1, 0},  {128, 8, 0, 1, 0},
-                                    {256, 0, 0, 1, 0}, {128, 0, 1, 1, 0}, {192, 0, 0, 1, 0},
-                                    {128, 0, 0, 2, 0}, {128, 0, 0, 4, 1}, {128, 0, 0, 8, 1},
-                                    {64, 0, 0, 8, 1}};
+    static constexpr int n = 7;
+    static constexpr int v[n][4] = {{128, 0, 0, 1}, {64, 0, 0, 1},  {128, 8, 0, 1}, {256, 0, 0, 1},
+                                    {128, 0, 1, 1}, {192, 0, 0, 1}, {128, 0, 0, 2}};
 };
 
-template <int Q, int PREC, int BX, int MINB, bool CS, int RS, bool PIPE>
+template <int Q, int PREC, int BX, int MINB, bool CS, int RS>
 int launch_direct(SolverImpl &s, int src, int dst) {
     using S = typename Store<PREC>::S;
     const auto &k = Consts<PREC>::get(s);
     dim3 grid((s.p.Nx + BX - 1) / BX, (s.p.Ny + RS - 1) / RS);
-    if constexpr (PIPE)
-        k_step_direct_pipe<Q, PREC, BX, MINB, RS><<<grid, BX, 0, s.stream>>>(
-            (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
-    else
-        k_step_direct<Q, PREC, BX, MINB, CS, RS><<<grid, BX, 0, s.stream>>>(
-            (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
+    k_step_direct<Q, PREC, BX, MINB, CS, RS><<<grid, BX, 0, s.stream>>>(
+        (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
     return (int)cudaGetLastError();
 }
 
@@ -66,8 +60,7 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
 #define LBM_DIRECT_CASE(I)                                                                 \
     case I:                                                                                \
         LBM_DISPATCH_Q(s.L.Q, return (launch_direct<QQ, PREC, V::v[I][0], V::v[I][1],       \
-                                                    (V::v[I][2] != 0), V::v[I][3],            \
-                                                    (V::v[I][4] != 0)>(s, src, dst)));        \
+                                                    (V::v[I][2] != 0), V::v[I][3]>(s, src, dst))); \
         break;
     switch (variant) {
         LBM_DIRECT_CASE(0)
@@ -77,9 +70,6 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
         LBM_DIRECT_CASE(4)
         LBM_DIRECT_CASE(5)
         LBM_DIRECT_CASE(6)
-        LBM_DIRECT_CASE(7)
-        LBM_DIRECT_CASE(8)
-        LBM_DIRECT_CASE(9)
     default: break;
     }
 #undef LBM_DIRECT_CASE
@@ -225,12 +215,13 @@ int Launch<PREC>::plane_from_f64(SolverImpl &s, int a, const double *in) {
 }
 
 template <int PREC>
-int Launch<PREC>::macros(SolverImpl &s, double *rho, double *ux, double *uy, double *T) {
+int Launch<PREC>::macros(SolverImpl &s, double *rho, double *ux, double *uy, double *T,
+                         int acc) {
     using S = typename Store<PREC>::S;
     const auto &k = Consts<PREC>::get(s);
     const long long n = (long long)s.p.Nx * s.p.Ny;
     LBM_DISPATCH_Q(s.L.Q, (k_macros<QQ, PREC><<<aux_blocks(n), kAuxThreads, 0, s.stream>>>(
-                               (const S *)s.f[s.cur], s.rho[s.cur], k, rho, ux, uy, T)));
+                               (const S *)s.f[s.cur], s.rho[s.cur], k, rho, ux, uy, T, acc)));
     return (int)cudaGetLastError();
 }
 

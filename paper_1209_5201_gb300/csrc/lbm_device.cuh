@@ -97,6 +97,24 @@ template <> __device__ __forceinline__ __nv_bfloat16 store_rounded<__nv_bfloat16
 }
 template <class S> __device__ __forceinline__ S store_rounded(double v, uint32_t);
 template <> __device__ __forceinline__ double store_rounded<double>(double v, uint32_t) { return v; }
+// Two values rounded to BF16 by one hardware stochastic-rounding conversion
+// (cvt.rs.satfinite.bf16x2.f32): va to the upper half with the upper 16 bits
+// of rbits, vb to the lower half with the lower 16.  For finite values below
+// the BF16 maximum it adds those bits below the 16 kept ones and truncates,
+// the same rounding as store_rounded with the same bits (checked on the
+// device bit for bit over 2^20 random pairs), in one instruction for both.
+__device__ __forceinline__ uint32_t bf16x2_rounded(float va, float vb, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va), "f"(vb), "r"(rbits));
+    return d;
+}
+// random bits of the pair (a, a + 1) for bf16x2_rounded: sr_bits(h, a) in the
+// upper half, sr_bits(h, a + 1) in the lower
+__device__ __forceinline__ uint32_t sr_bits_pair(uint32_t hcell, int a) {
+    const uint32_t ha = hcell * (0x9E3779B9u * (2u * (uint32_t)a + 1u));
+    const uint32_t hb = hcell * (0x9E3779B9u * (2u * (uint32_t)a + 3u));
+    return __byte_perm(hb, ha, 0x7632);
+}
 
 // ---- stochastic rounding of FP32 results (batched path) -----------------------
 // f + t rounded to FP32 stochastically, from 32 random bits x: a uniform
@@ -149,13 +167,11 @@ __device__ __forceinline__ int wrap(int v, int n) {
     return m < 0 ? m + n : m;
 }
 
-// ---- explicit arithmetic on one cell (float, double) or two (float2) ---------
+// ---- explicit arithmetic --------------------------------------------------------
 // The collision below is written with explicit fma / mul / add / sub, which
-// the compiler never contracts or reorders, so a kernel that updates one cell
-// per thread (V = float or double) and one that updates two adjacent cells
-// per thread with Blackwell's packed FP32x2 instructions (V = float2: one
-// FFMA2 / FMUL2 / FADD2 does the same operation for both cells) execute the
-// same roundings: their results agree bit for bit.
+// the compiler never contracts or reorders, so every kernel that inlines it
+// (one thread per cell, tile-staged, batched) executes the same roundings and
+// their results agree bit for bit wherever they compute the same cell.
 template <class V> struct Ar;
 template <> struct Ar<float> {
     using S = float;
@@ -163,7 +179,10 @@ template <> struct Ar<float> {
     __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
     __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
     __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
-    __device__ __forceinline__ static float rcp(float a) { return __frcp_rn(a); }
+    // FP32 reciprocal to within 2 ulp (one MUFU.RCP and a multiply): its
+    // error, a relative 1e-7 in 1/rho and in omega, is far below what FP32
+    // storage resolves, and every kernel evaluates the same expression
+    __device__ __forceinline__ static float rcp(float a) { return __fdividef(1.0f, a); }
     __device__ __forceinline__ static float pw(float a, float e) { return powf(a, e); }
     __device__ __forceinline__ static float bc(float c) { return c; }
 };
@@ -176,23 +195,6 @@ template <> struct Ar<double> {
     __device__ __forceinline__ static double rcp(double a) { return __drcp_rn(a); }
     __device__ __forceinline__ static double pw(double a, double e) { return pow(a, e); }
     __device__ __forceinline__ static double bc(double c) { return c; }
-};
-template <> struct Ar<float2> {
-    using S = float;
-    __device__ __forceinline__ static float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-    __device__ __forceinline__ static float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-    __device__ __forceinline__ static float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-    // a - b = fma(b, -1, a), rounded once like __fsub_rn
-    __device__ __forceinline__ static float2 sub(float2 a, float2 b) {
-        return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
-    }
-    __device__ __forceinline__ static float2 rcp(float2 a) {
-        return make_float2(__frcp_rn(a.x), __frcp_rn(a.y));
-    }
-    __device__ __forceinline__ static float2 pw(float2 a, float e) {
-        return make_float2(powf(a.x, e), powf(a.y, e));
-    }
-    __device__ __forceinline__ static float2 bc(float c) { return make_float2(c, c); }
 };
 
 // compile-time loop a = A, A + 1, ..., N - 1
@@ -242,7 +244,7 @@ struct PairLoop {
 // steady state by about that relative amount.  FP64 keeps the form
 // (1 - omega) f~ + omega rho g.
 //
-// V: float or double (one cell), float2 (two cells, packed FP32x2).
+// V: float or double.
 template <int Q, class V, bool SHIFT = false>
 struct Collision {
     using L = Lat<Q>;

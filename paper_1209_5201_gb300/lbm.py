@@ -22,6 +22,7 @@ LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ECUDA, LBM_EBUSY, LBM_ECANCELLED = 5, 6, 7, 8,
 LBM_LATTICE_D2Q17, LBM_LATTICE_D2Q25, LBM_LATTICE_D2Q25B, LBM_LATTICE_D2Q37 = 17, 25, 26, 37
 LBM_FP64, LBM_FP32, LBM_BF16DEV = 0, 1, 2
 LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_STAGED, LBM_KERNEL_CELLWARP = 0, 1, 2, 3
+LBM_ROUND_AUTO, LBM_ROUND_STOCHASTIC, LBM_ROUND_NEAREST = 0, 1, 2
 
 LATTICE_KIND = {"D2Q17": 17, "D2Q25": 25, "D2Q25b": 26, "D2Q37": 37}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16dev": 2}
@@ -52,7 +53,7 @@ class lbm_request(C.Structure):
                 ("thermal", C.c_int32), ("Kn", C.c_double), ("tau", C.c_double),
                 ("mu_exp", C.c_double), ("u_wall", C.c_double * 2), ("T_wall", C.c_double * 2),
                 ("tol", C.c_double), ("max_steps", C.c_int64), ("tag", C.c_uint64),
-                ("accom", C.c_double * 2)]
+                ("accom", C.c_double * 2), ("rounding", C.c_int32)]
 
 
 class lbm_result(C.Structure):
@@ -111,6 +112,7 @@ _SIGS = {
     "lbm_solver_get_f": ([_VP, _DP], C.c_int),
     "lbm_solver_set_f": ([_VP, _DP], C.c_int),
     "lbm_solver_macros": ([_VP, _DP, _DP, _DP, _DP], C.c_int),
+    "lbm_solver_macros_mean": ([_VP, C.c_int64, _DP, _DP, _DP, _DP], C.c_int),
     "lbm_solver_fluxes": ([_VP, _DP, _DP, _DP, _DP, _DP], C.c_int),
     "lbm_solver_state_bytes": ([_VP, C.POINTER(C.c_size_t)], C.c_int),
     "lbm_solver_get_state": ([_VP, _VP, C.c_size_t], C.c_int),
@@ -299,6 +301,11 @@ def lbm_solver_macros(h, rho=None, ux=None, uy=None, T=None) -> None:
     _check(load().lbm_solver_macros(h, _dp(rho), _dp(ux), _dp(uy), _dp(T)), "lbm_solver_macros")
 
 
+def lbm_solver_macros_mean(h, nsteps: int, rho=None, ux=None, uy=None, T=None) -> None:
+    _check(load().lbm_solver_macros_mean(h, int(nsteps), _dp(rho), _dp(ux), _dp(uy), _dp(T)),
+           "lbm_solver_macros_mean")
+
+
 def lbm_solver_fluxes(h, sxx=None, sxy=None, syy=None, qx=None, qy=None) -> None:
     _check(load().lbm_solver_fluxes(h, _dp(sxx), _dp(sxy), _dp(syy), _dp(qx), _dp(qy)),
            "lbm_solver_fluxes")
@@ -477,7 +484,8 @@ def lbm_residual_noalloc(ux, T, ux_prev, T_prev, n: int, T_ref: float, thermal: 
 def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
                  tol: float = 1e-5, max_steps: int = 10_000_000, tag: int = 0,
                  eq_order: int | None = None, thermal: bool | None = None,
-                 tau: float = 0.0, accom: tuple = (1.0, 1.0)) -> lbm_request:
+                 tau: float = 0.0, accom: tuple = (1.0, 1.0),
+                 rounding: int = LBM_ROUND_AUTO) -> lbm_request:
     """A Couette request: walls at -U_w (bottom) and +U_w (top), both at T_w."""
     o, t = (4, True) if lattice == "D2Q37" else (2, False)
     r = lbm_request()
@@ -490,6 +498,7 @@ def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
     r.T_wall[0] = r.T_wall[1] = T_w
     r.tol, r.max_steps, r.tag = tol, max_steps, tag
     r.accom[0], r.accom[1] = accom
+    r.rounding = rounding
     return r
 
 
@@ -637,6 +646,13 @@ class Solver:
         shp = (self.cfg.Ny, self.cfg.Nx)
         out = [np.empty(shp) for _ in range(4)]
         lbm_solver_macros(self.h, *out)
+        return tuple(out)
+
+    def macros_mean(self, nsteps: int):
+        """Time means over the next nsteps steps of (rho, u_x, u_y, T)."""
+        shp = (self.cfg.Ny, self.cfg.Nx)
+        out = [np.empty(shp) for _ in range(4)]
+        lbm_solver_macros_mean(self.h, nsteps, *out)
         return tuple(out)
 
     def fluxes(self):

@@ -84,10 +84,11 @@ LONG = [("D2Q37", 300, 0.004, 0.20, 1.0), ("D2Q25", 700, 0.004, 0.10, 1.0),
         ("D2Q17", 2500, 0.004, 0.15, 1.0)]
 
 
-def fixed_steps(lbm, items, steps, **srv):
+def fixed_steps(lbm, items, steps, rounding=0, **srv):
     """Run every item for `steps` steps (rounded up to whole chunks)."""
     s = lbm.Server(**{**dict(mem_budget_bytes=1 << 28, max_slots=32, chunk_steps=50), **srv})
-    ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=1e-30, max_steps=steps))
+    ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=1e-30, max_steps=steps,
+                                     rounding=rounding))
            for lat, Ny, Kn, Uw, Tw in items]
     s.drain(300)
     res = {r.id: r for r in s.poll(64)}
@@ -96,11 +97,17 @@ def fixed_steps(lbm, items, steps, **srv):
     return out
 
 
-def test_cluster_slots_follow_the_oracle_transient(lbm, oracle):
+@pytest.mark.parametrize("rounding,bound_T", [(1, 1e-5), (2, 2e-5)])
+def test_cluster_slots_follow_the_oracle_transient(lbm, oracle, rounding, bound_T):
     # a fixed number of steps (no convergence stop): every row of the state,
     # including the rows next to the cluster's CTA boundaries, against the
-    # oracle after the same steps
-    for (lat, Ny, Kn, Uw, Tw), (r, rho, ux, uy, T) in zip(LONG, fixed_steps(lbm, LONG, 1500)):
+    # oracle after the same steps.  With stochastic rounding and conserving
+    # increments (rounding 1) within 1e-5 in u_x / U_w and T; rounded to
+    # nearest throughout (rounding 2), the FP32 transient's T drifts further
+    # (measured 1.2e-5 after 1500 steps of the 300-row D2Q37 column at Kn
+    # 0.004), bound 2e-5 for T
+    for (lat, Ny, Kn, Uw, Tw), (r, rho, ux, uy, T) in zip(
+            LONG, fixed_steps(lbm, LONG, 1500, rounding=rounding)):
         o, t = (4, True) if lat == "D2Q37" else (2, False)
         p = oracle.Problem(lattice=lat, Nx=1, Ny=Ny, eq_order=o, thermal=t, Kn=Kn,
                            u_wall=(-Uw, Uw), T_wall=(Tw, Tw))
@@ -109,7 +116,7 @@ def test_cluster_slots_follow_the_oracle_transient(lbm, oracle):
         _, oux, _, oT = oracle.macros(p, f)
         assert np.max(np.abs(ux - oux[:, 0])) / Uw < 1e-5, (lat, Ny, r.steps)
         if t:
-            assert np.max(np.abs(T - oT[:, 0])) < 1e-5, (lat, Ny)
+            assert np.max(np.abs(T - oT[:, 0])) < bound_T, (lat, Ny)
 
 
 @pytest.mark.parametrize("how", ["no clusters", "one CTA of budget"])

@@ -4,7 +4,8 @@ deviation storage, each run to its steady-state tolerance (1e-8 FP64, 1e-6
 otherwise), against the FP64 oracle's steady state (residual 1e-10).
 L-inf errors in rho, u_x / U_w and the kinetic temperature, with the
 one-thread-per-cell kernel and with the one-warp-per-cell kernel (the
-automatic choice on a grid this small)."""
+automatic choice on a grid this small), of the final state and of the time
+mean over the next 4000 steps (lbm_solver_macros_mean)."""
 import numpy as np
 import pytest
 
@@ -14,16 +15,23 @@ pytestmark = pytest.mark.gpu
 
 # BF16 keeps 8 significant bits of d = f - w rho (|d| up to ~0.3 w here).
 # With round-to-nearest the steady state carried that round-off as a bias
-# amplified by the relaxation time (4.4e-2 U_w in u_x); the step kernels now
+# amplified by the relaxation time (4.4e-2 U_w in u_x); the step kernels
 # round stochastically, so the steady state carries zero-mean noise instead:
 # over two random streams and both kernels, measured 3.7e-3 .. 5.3e-3 U_w in
-# u_x, 2.5e-4 .. 6.6e-4 in rho, 1.3e-4 .. 2.3e-4 in T; bounds about 3x the
-# largest.  The noise keeps the residual near 4e-3, so the 1e-6 target is not
-# reached (ENOTCONVERGED is expected).
+# u_x, 2.5e-4 .. 6.6e-4 in rho, 1.3e-4 .. 2.3e-4 in T for the final state
+# (bounds 1.5x the largest); the noise keeps the residual near 4e-3, so the
+# 1e-6 target is not reached (ENOTCONVERGED is expected: the noise floor).
+# The time mean over 4000 steps is the steady field to within the bound of
+# the BF16 variant, 5e-3 in u_x / U_w and in rho.
 BOUNDS = {          # rho, u_x / U_w, T
     "fp64": (1e-9, 1e-7, 1e-9),
     "fp32": (2e-6, 5e-6, 2e-6),
-    "bf16dev": (2e-3, 1.5e-2, 1e-3),
+    "bf16dev": (1e-3, 8e-3, 4e-4),
+}
+MEAN_BOUNDS = {
+    "fp64": (1e-9, 1e-7, 1e-9),
+    "fp32": (2e-6, 5e-6, 2e-6),
+    "bf16dev": (5e-3, 5e-3, 4e-4),
 }
 KERNELS = {"thread": 1, "warp": 3}
 TOL = {"fp64": 1e-8, "fp32": 1e-6, "bf16dev": 1e-6}
@@ -45,10 +53,14 @@ def sweep(lbm, oracle, kernel):
         s.init()
         st, steps, res = s.run_to_residual(TOL[prec], 2_000_000, 100)
         rho, ux, uy, T = s.macros()
+        mrho, mux, _, mT = s.macros_mean(4000)
         out[prec] = dict(status=st, steps=steps, res=res,
                          err_rho=float(np.max(np.abs(rho - orho))),
                          err_u=float(np.max(np.abs(ux - oux)) / Uw),
-                         err_T=float(np.max(np.abs(T - oT))))
+                         err_T=float(np.max(np.abs(T - oT))),
+                         mean_err_rho=float(np.max(np.abs(mrho - orho))),
+                         mean_err_u=float(np.max(np.abs(mux - oux)) / Uw),
+                         mean_err_T=float(np.max(np.abs(mT - oT))))
         s.close()
     return out
 
@@ -63,6 +75,8 @@ def test_precision_sweep_against_oracle_steady_state(lbm_mod, oracle, kname):
     res = sweep(lbm_mod, oracle, KERNELS[kname])
     report("precision_sweep" + ("" if kname == "thread" else "_cellwarp"), res)
     for prec, r in res.items():
-        b = BOUNDS[prec]
+        b, m = BOUNDS[prec], MEAN_BOUNDS[prec]
         assert r["err_rho"] < b[0] and r["err_u"] < b[1] and r["err_T"] < b[2], (prec, r)
+        assert r["mean_err_rho"] < m[0] and r["mean_err_u"] < m[1] and r["mean_err_T"] < m[2], \
+            (prec, r)
     assert res["fp64"]["status"] == lbm_mod.LBM_OK and res["fp32"]["status"] == lbm_mod.LBM_OK
