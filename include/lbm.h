@@ -362,7 +362,22 @@ typedef struct lbm_request {
     uint64_t tag;         /* caller's tag, returned in the result              */
     double accom[2];      /* wall accommodation, as in lbm_params (1: diffuse) */
     int32_t rounding;     /* LBM_ROUND_*: how the FP32 collision rounds        */
+    int32_t init;         /* LBM_INIT_*: the state the solve starts from       */
 } lbm_request;
+
+/* lbm_request.init.  REST: rho = 1, u = 0, T = 1 (T_w for a thermal lattice
+ * at rest is not imposed: T = 1).  NS: the local equilibrium at rho = 1 of the
+ * Navier-Stokes slip solution of the paper's Couette problem (Sec. IV,
+ * Eq. (13)-(14)): u_x(y) = (u_b + u_t)/2 + (u_t - u_b)(y - 1/2)/(1 + 2 lambda)
+ * with the slip length lambda = Kn (2 - a)/a (a the mean accommodation), and
+ * for a thermal lattice T(y) = T_b + (T_t - T_b) y + the viscous heating
+ * 2 Pr U^2 y (1 - y)/(C_p (1 + 2 lambda)^2) plus the temperature jump
+ * [8 gamma/(gamma + 1)] lambda U^2/(2 C_p (1 + 2 lambda)^2), U = (u_t - u_b)/2,
+ * C_p = 2, gamma = 2, Pr = 1.  The steady state does not depend on the start
+ * (the column's mass is the same); a start close to it takes fewer steps,
+ * most of all in the dense, tall columns that dominate the latency tail. */
+#define LBM_INIT_REST  0
+#define LBM_INIT_NS    1
 
 /* lbm_request.rounding.  AUTO: round to nearest while the change per check
  * is above 5 tol, then increments that conserve mass, momentum (and energy)
@@ -483,13 +498,14 @@ typedef struct lbm_server_tuning {
  *  - one lone column of each lattice at heights 256, 1024 and 4096 on each
  *    usable cluster size (long runs, so launch overhead is negligible), and
  *  - max_slots one-CTA columns at chunk lengths 25, 50, 100, 200, 400,
- * then writes into *cfg: class_sub[c] = the median over lattices and heights
- * of the step time on one CTA over that on a cluster of class c (how many
+ * then writes into *cfg: class_sub[c] = the step time of a lone D2Q37
+ * column of CL x 256 rows (the tallest a CL-CTA cluster serves at 256 rows
+ * per CTA) on one CTA over that on the class's cluster of CL CTAs (how many
  * chunks a cluster slot runs while a one-CTA slot runs one, 1..16);
  * cluster_rows = the median over lattices and heights of the rows per CTA
  * of the smallest cluster within 15 % of the fastest (32 .. 1024); and
- * chunk_steps = the shortest chunk within 5 % of the best full-GPU rate
- * (shorter chunks admit and retire requests sooner).  Takes a few seconds;
+ * chunk_steps = the longest chunk within 5 % of the best full-GPU rate
+ * (fewer launches, each a host round trip).  Takes about half a minute;
  * the device must be otherwise idle for the times to mean anything.  `stream`
  * as for lbm_server_create; `report` (may be NULL) receives the times.
  * Results of a solve do not depend on cluster_rows or class_sub; chunk_steps

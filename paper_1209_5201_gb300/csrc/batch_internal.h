@@ -41,6 +41,9 @@ struct SlotDesc {
     double mass0;             // the column's mass at admission (sum of rho)
     double precise_from;      // change per check below which the slot switches
                               // to stochastic rounding and conserving increments
+    // initial state: u_x(y) = u0 + u1 (y - 1/2), T(y) = T0 + T1 y + T2 y (1 - y)
+    // at rho = 1 (y = (j + 1/2) / Ny); rest: u0 = u1 = T1 = T2 = 0, T0 = 1
+    double init_u0, init_u1, init_T0, init_T1, init_T2;
     // incoming terms of Eq. (12)'s numerator, built on the host: wall w (0
     // bottom, 1 top), term l < nterm is velocity term_a[w][l] at distance
     // term_row[w][l] from the wall

@@ -1,6 +1,7 @@
 // Batched chunk kernel launch unit (one CTA per slot) and its per-slot
 // initialisation and read-out kernels.
 #include "batch_internal.h"
+#include "k_aux.cuh"
 #include "k_batch.cuh"
 
 namespace lbm {
@@ -90,17 +91,25 @@ k_batch_chunk(SlotDesc *__restrict__ desc, SlotStatus *__restrict__ status,
         desc[slot].cur = (int)((sd.cur + (long long)done * sd.chunk_steps) & 1);
 }
 
-// Rest equilibrium f~* = rho0 w_a of newly admitted slots, stored as the
-// deviation (rho0 - 1) w_a; previous-check fields u_x = 0, T = 1.
+// Initial state of newly admitted slots: the equilibrium f~* = rho0 g^eq(u, T)
+// of Eq. (4) with u_x(y), T(y) from the descriptor (rest: u = 0, T = 1; the
+// Sec. IV slip solution), stored as deviations from w_a; the previous-check
+// fields are the initial u_x and T.
 template <int Q>
 __device__ void init_slot(const SlotDesc &d, float *pool, float rho0) {
     float *f = pool + d.f_off + (d.cur ? (long long)Q * d.Ny : 0);
+    const bool thermal = d.k.thermal != 0;
     for (int j = threadIdx.x; j < d.Ny; j += blockDim.x) {
+        const double y = (j + 0.5) / d.Ny;
+        const float u = (float)(d.init_u0 + d.init_u1 * (y - 0.5));
+        const float T = thermal ? (float)(d.init_T0 + d.init_T1 * y + d.init_T2 * y * (1.0 - y)) : 1.0f;
+        float o[Q];
+        equilibrium_all<Q, float, true>(rho0, rho0 - 1.0f, u, 0.0f, T, d.k, o);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) f[(long long)a * d.Ny + j] = (rho0 - 1.0f) * d.k.w[a];
+        for (int a = 0; a < Q; ++a) f[(long long)a * d.Ny + j] = o[a];
         float *pu = pool + d.prev_off;
-        pu[j] = 0.0f;
-        pu[d.Ny + j] = 1.0f;
+        pu[j] = u;
+        pu[d.Ny + j] = T;
     }
 }
 

@@ -231,6 +231,25 @@ struct ServerImpl {
         d.u_ref = std::max(std::fabs(r.u_wall[0]), std::fabs(r.u_wall[1]));
         if (!(d.u_ref > 0)) d.u_ref = 1.0;
         d.mass0 = (double)r.Ny;                  // rho = 1 at admission
+        d.init_u0 = d.init_u1 = d.init_T1 = d.init_T2 = 0.0;
+        d.init_T0 = 1.0;
+        if (r.init == LBM_INIT_NS) {
+            // Sec. IV slip solution: slip length Kn (2 - a)/a per wall (a the
+            // mean accommodation), viscous heating and jump of Eq. (14)
+            const double a = 0.5 * (r.accom[0] + r.accom[1]);
+            const double kn = r.tau > 0 ? r.tau * std::sqrt(M_PI / 2.0) : r.Kn;
+            const double lam = a > 0 ? kn * (2.0 - a) / a : 1e30;
+            const double U = 0.5 * (r.u_wall[1] - r.u_wall[0]);
+            d.init_u0 = 0.5 * (r.u_wall[0] + r.u_wall[1]);
+            d.init_u1 = lam < 1e29 ? 2.0 * U / (1.0 + 2.0 * lam) : 0.0;
+            if (r.thermal) {
+                const double Cp = 2.0, gam = 2.0, Pr = 1.0, den = std::pow(1.0 + 2.0 * lam, 2);
+                const double Us = lam < 1e29 ? U * U : 0.0;
+                d.init_T0 = r.T_wall[0] + 8.0 * gam / (gam + 1.0) * lam * Us / (2.0 * Cp * den);
+                d.init_T1 = r.T_wall[1] - r.T_wall[0];
+                d.init_T2 = 2.0 * Pr * Us / (Cp * den);
+            }
+        }
         d.precise_from = r.rounding == LBM_ROUND_AUTO ? kPreciseFrom * r.tol : -1.0;
         // incoming terms per wall (Sec. III: at layer l the velocities with
         // e.n < -l); the bottom list takes e_y < 0 at rows 0..|e_y|-1, the top
@@ -699,6 +718,10 @@ static int check_request(const lbm_request *r) {
         set_error("rounding must be LBM_ROUND_AUTO, _STOCHASTIC or _NEAREST");
         return LBM_EINVAL;
     }
+    if (r->init != LBM_INIT_REST && r->init != LBM_INIT_NS) {
+        set_error("init must be LBM_INIT_REST or LBM_INIT_NS");
+        return LBM_EINVAL;
+    }
     return LBM_OK;
 }
 
@@ -1058,30 +1081,30 @@ extern "C" int lbm_server_autotune(lbm_server_cfg *cfg, void *stream, lbm_server
     // a lone long request (small Kn) gets the largest usable cluster within the
     // CTA budget: the budget picks the cluster size; long chunks keep the
     // host's per-launch work out of the step time
-    std::vector<double> ratio[kBatchClasses], rows_best;
+    auto lone_us = [&](int kind, int Ny, int cl, double *us) -> int {
+        *us = 0.0;
+        if (cl > max_cl || batch_cluster_size(Ny, 32, cl, max_cl) != cl) return LBM_OK;
+        lbm_server_cfg lc = *cfg;
+        lc.max_slots = cl;
+        lc.cluster_rows = 32;
+        lc.chunk_steps = 1000;
+        lc.mem_budget_bytes = (size_t)64 << 20;
+        for (int k = 0; k < kBatchClasses; ++k) lc.class_sub[k] = 0;
+        double sec = 0, cells = 0;
+        if (int rc = time_fixed_steps(lc, stream, kind, Ny, 1e-3, 1, 4000, &sec, &cells)) return rc;
+        *us = cells > 0 ? sec / (cells / Ny) * 1e6 : 0.0;
+        return LBM_OK;
+    };
+    std::vector<double> rows_best;
     for (int li = 0; li < 3; ++li) {
         for (int hi = 0; hi < 3; ++hi) {
             const int Ny = heights[hi];
             rep.ny[hi] = Ny;
-            double t1 = 0, tbest = 1e300;
+            double tbest = 1e300;
             for (int c = 0; c < kBatchClasses; ++c) {
-                const int cl = kBatchClassCL[c];
-                if (cl > max_cl || batch_cluster_size(Ny, 32, cl, max_cl) != cl) continue;
-                lbm_server_cfg lc = *cfg;
-                lc.max_slots = cl;
-                lc.cluster_rows = 32;
-                lc.chunk_steps = 1000;
-                lc.mem_budget_bytes = (size_t)64 << 20;
-                for (int k = 0; k < kBatchClasses; ++k) lc.class_sub[k] = 0;
-                const int64_t steps = 4000;
-                double sec = 0, cells = 0;
-                if (int rc = time_fixed_steps(lc, stream, kinds[li], Ny, 1e-3, 1, steps, &sec, &cells))
-                    return rc;
-                const double us = cells > 0 ? sec / (cells / Ny) * 1e6 : 0.0;
-                rep.lone_us[li][hi][c] = us;
-                if (c == 0) t1 = us;
+                if (int rc = lone_us(kinds[li], Ny, kBatchClassCL[c], &rep.lone_us[li][hi][c])) return rc;
+                const double us = rep.lone_us[li][hi][c];
                 if (us > 0 && us < tbest) tbest = us;
-                if (c > 0 && t1 > 0 && us > 0) ratio[c].push_back(t1 / us);
             }
             // the smallest cluster within 15 % of the fastest: its rows per CTA
             for (int c = 0; c < kBatchClasses; ++c) {
@@ -1092,6 +1115,18 @@ extern "C" int lbm_server_autotune(lbm_server_cfg *cfg, void *stream, lbm_server
                 }
             }
         }
+    }
+    // chunks per launch of class c: the factor by which its cluster shortens
+    // a step, at the height the class serves (CL x 256 rows, the tallest a
+    // CL-CTA cluster takes at 256 rows per CTA): D2Q37 there on one CTA over
+    // on the cluster
+    double ratio[kBatchClasses] = {1, 0, 0, 0, 0};
+    for (int c = 1; c < kBatchClasses; ++c) {
+        const int cl = kBatchClassCL[c], Ny = std::min(kMaxNy, 256 * cl);
+        double t1 = 0, tc = 0;
+        if (int rc = lone_us(LBM_LATTICE_D2Q37, Ny, 1, &t1)) return rc;
+        if (int rc = lone_us(LBM_LATTICE_D2Q37, Ny, cl, &tc)) return rc;
+        ratio[c] = (t1 > 0 && tc > 0) ? t1 / tc : 0.0;
     }
     // ---- chunk length on a full GPU of one-CTA columns ------------------------
     // (D2Q37, 256 rows: the heaviest one-CTA column; best of two runs each)
@@ -1112,16 +1147,16 @@ extern "C" int lbm_server_autotune(lbm_server_cfg *cfg, void *stream, lbm_server
         }
         best = std::max(best, rep.chunk_glups[i]);
     }
-    int chunk = chunks[4];
+    // the longest chunk within 5 % of the best rate: fewer launches (each
+    // costs the host a round trip) at about the same rate
+    int chunk = chunks[0];
     for (int i = 0; i < 5; ++i)
-        if (rep.chunk_glups[i] >= 0.95 * best) { chunk = chunks[i]; break; }
+        if (rep.chunk_glups[i] >= 0.95 * best) chunk = chunks[i];
     // ---- the choices ------------------------------------------------------------
     cfg->chunk_steps = chunk;
     cfg->class_sub[0] = 1;
-    for (int c = 1; c < kBatchClasses; ++c) {
-        const double m = median(ratio[c]);
-        cfg->class_sub[c] = m > 0 ? std::max(1, std::min(kMaxSub, (int)std::lround(m))) : 0;
-    }
+    for (int c = 1; c < kBatchClasses; ++c)
+        cfg->class_sub[c] = ratio[c] > 0 ? std::max(1, std::min(kMaxSub, (int)std::lround(ratio[c]))) : 0;
     if (!rows_best.empty()) {
         int rows = (int)median(rows_best);
         rows = std::max(32, std::min(1024, (rows + kResidualChunk - 1) / kResidualChunk * kResidualChunk));

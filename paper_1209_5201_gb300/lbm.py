@@ -23,6 +23,7 @@ LBM_LATTICE_D2Q17, LBM_LATTICE_D2Q25, LBM_LATTICE_D2Q25B, LBM_LATTICE_D2Q37 = 17
 LBM_FP64, LBM_FP32, LBM_BF16DEV = 0, 1, 2
 LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_STAGED, LBM_KERNEL_CELLWARP = 0, 1, 2, 3
 LBM_ROUND_AUTO, LBM_ROUND_STOCHASTIC, LBM_ROUND_NEAREST = 0, 1, 2
+LBM_INIT_REST, LBM_INIT_NS = 0, 1
 
 LATTICE_KIND = {"D2Q17": 17, "D2Q25": 25, "D2Q25b": 26, "D2Q37": 37}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16dev": 2}
@@ -53,7 +54,7 @@ class lbm_request(C.Structure):
                 ("thermal", C.c_int32), ("Kn", C.c_double), ("tau", C.c_double),
                 ("mu_exp", C.c_double), ("u_wall", C.c_double * 2), ("T_wall", C.c_double * 2),
                 ("tol", C.c_double), ("max_steps", C.c_int64), ("tag", C.c_uint64),
-                ("accom", C.c_double * 2), ("rounding", C.c_int32)]
+                ("accom", C.c_double * 2), ("rounding", C.c_int32), ("init", C.c_int32)]
 
 
 class lbm_result(C.Structure):
@@ -485,7 +486,7 @@ def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
                  tol: float = 1e-5, max_steps: int = 10_000_000, tag: int = 0,
                  eq_order: int | None = None, thermal: bool | None = None,
                  tau: float = 0.0, accom: tuple = (1.0, 1.0),
-                 rounding: int = LBM_ROUND_AUTO) -> lbm_request:
+                 rounding: int = LBM_ROUND_AUTO, init: int = LBM_INIT_REST) -> lbm_request:
     """A Couette request: walls at -U_w (bottom) and +U_w (top), both at T_w."""
     o, t = (4, True) if lattice == "D2Q37" else (2, False)
     r = lbm_request()
@@ -499,6 +500,7 @@ def make_request(lattice: str, Ny: int, Kn: float, U_w: float, T_w: float = 1.0,
     r.tol, r.max_steps, r.tag = tol, max_steps, tag
     r.accom[0], r.accom[1] = accom
     r.rounding = rounding
+    r.init = init
     return r
 
 

@@ -378,3 +378,31 @@ def test_autotune_fills_the_configuration_and_leaves_results_unchanged(lbm):
     for it, a, b in zip(items, *out):
         assert a[0] == b[0] and a[1] == b[1], it
         assert all(np.array_equal(x, y) for x, y in zip(a[2:], b[2:])), it
+
+
+def test_ns_start_reaches_the_same_steady_state_in_fewer_steps(lbm, oracle):
+    # a request may start from the Navier-Stokes slip solution of the paper's
+    # Couette problem instead of rest: the same steady state (within 1e-5 of
+    # the oracle's, which starts from rest) in fewer steps for dense columns
+    items = [("D2Q25", 400, 0.01, 0.20, 1.0), ("D2Q37", 300, 0.02, 0.25, 1.05),
+             ("D2Q17", 200, 0.1, 0.15, 1.0)]
+    steps = {}
+    for init in (lbm.LBM_INIT_REST, lbm.LBM_INIT_NS):
+        s = lbm.Server(mem_budget_bytes=1 << 28, max_slots=16, chunk_steps=50)
+        ids = [s.submit(lbm.make_request(lat, Ny, Kn, Uw, Tw, tol=5e-6, init=init))
+               for lat, Ny, Kn, Uw, Tw in items]
+        s.drain(300)
+        res = {r.id: r for r in s.poll(8)}
+        for rid, (lat, Ny, Kn, Uw, Tw) in zip(ids, items):
+            r = res[rid]
+            assert r.status == lbm.LBM_OK, (init, lat, Ny)
+            _, ux, _, T = s.fetch(rid, Ny)
+            oux, oT = oracle_steady(oracle, lat, Ny, Kn, Uw, Tw)
+            assert np.max(np.abs(ux - oux)) / Uw < 1e-5, (init, lat, Ny)
+            if lat == "D2Q37":
+                assert np.max(np.abs(T - oT)) < 1e-5, (init, lat, Ny)
+            assert abs(r.mass - Ny) < 1e-5 * Ny
+            steps[(init, lat)] = r.steps
+        s.close()
+    for lat in ("D2Q25", "D2Q37"):                  # the dense ones
+        assert steps[(lbm.LBM_INIT_NS, lat)] < 0.8 * steps[(lbm.LBM_INIT_REST, lat)], steps
