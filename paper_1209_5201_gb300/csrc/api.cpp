@@ -195,8 +195,10 @@ void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int p
         k.w[a] = (C)L.w[a];
         k.wsh[L.shell[a]] = (C)L.w[a];
         k.c2sh[L.shell[a]] = (C)(L.r * L.r * (L.ex[a] * L.ex[a] + L.ey[a] * L.ey[a]));
-        k.off_src[a] = (int)((long long)a * k.plane - (long long)L.ey[a] * pitch - L.ex[a]);
-        k.off_dst[a] = (int)((long long)a * k.plane);
+        const long long es = (long long)storage_elem_bytes(p.precision);
+        k.b_src[a] = es * ((long long)a * k.plane - (long long)L.ey[a] * pitch - L.ex[a]);
+        k.b_dst[a] = es * ((long long)a * k.plane);
+        k.b_rho[a] = 4LL * (-(long long)L.ey[a] * pitch - L.ex[a]);
     }
     double e2w = 0;
     for (int a = 0; a < L.Q; ++a) e2w += (double)(C)L.w[a] * (L.ex[a] * L.ex[a] + L.ey[a] * L.ey[a]);

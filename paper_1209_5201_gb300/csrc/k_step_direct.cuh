@@ -59,7 +59,7 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
                                      const double *s_min, typename Store<PREC>::C (&f)[Q]) {
     using L = Lat<Q>;
     using C = typename Store<PREC>::C;
-    // the cell's own index; velocity a reads at cell + off_src[a]
+    // the cell's own index; velocity a reads b_src[a] bytes from it
     const int cell = j * k.pitch + x + kPadL;
     const typename Store<PREC>::S *__restrict__ src = fin + cell;
 #pragma unroll
@@ -72,20 +72,11 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
             f[a] = wall_mix<PREC>(s_min[threadIdx.x + 3 - L::ex(a)], k.wcoef[wall][a], k.w[a],
                                   k.accom[wall], spec);
         } else {
-            C v = to_c(src[k.off_src[a]]);
-            if constexpr (Store<PREC>::dev)
-                v = dev_to_f(v, k.w[a], rin[cell - L::ey(a) * k.pitch - L::ex(a)]);
+            C v = to_c(ld_b(src, k.b_src[a]));
+            if constexpr (Store<PREC>::dev) v = dev_to_f(v, k.w[a], ld_b(rin + cell, k.b_rho[a]));
             f[a] = v;
         }
     }
-}
-
-// Streaming (evict-first) store of one population.
-template <class S>
-__device__ __forceinline__ void store_cs(S *p, S v) { __stcs(p, v); }
-template <>
-__device__ __forceinline__ void store_cs<__nv_bfloat16>(__nv_bfloat16 *p, __nv_bfloat16 v) {
-    __stcs((unsigned short *)p, __bfloat16_as_ushort(v));
 }
 
 // Collide the pulled values f of cell (x, j) and store the result.
@@ -116,22 +107,21 @@ __device__ __forceinline__ void collide_store(const typename Store<PREC>::C (&f)
             const float v0 = f_to_dev(o[0], k.w[0], col.rho);
             const uint32_t d0 = bf16x2_rounded(v0, v0, hcell * 0x9E3779B9u);   // upper: sr_bits(h, 0)
             unsigned short *d16 = reinterpret_cast<unsigned short *>(dst);
-            d16[k.off_dst[0]] = (unsigned short)(d0 >> 16);
+            st_b<false>(d16, k.b_dst[0], (unsigned short)(d0 >> 16));
             PairLoop<1, Q>::run([&](auto ic) {
                 constexpr int A = decltype(ic)::value;
                 const float va = f_to_dev(o[A], k.w[A], col.rho);
                 const float vb = f_to_dev(o[A + 1], k.w[A + 1], col.rho);
                 const uint32_t d = bf16x2_rounded(va, vb, sr_bits_pair(hcell, A));
-                d16[k.off_dst[A]] = (unsigned short)(d >> 16);
-                d16[k.off_dst[A + 1]] = (unsigned short)d;
+                st_b<false>(d16, k.b_dst[A], (unsigned short)(d >> 16));
+                st_b<false>(d16, k.b_dst[A + 1], (unsigned short)d);
             });
             rout[j * k.pitch + x + kPadL] = (float)col.rho;
         } else {
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const S sv = store_rounded<S>(o[a], sr_bits(hcell, a));
-                if (CS) store_cs<S>(dst + k.off_dst[a], sv);
-                else dst[k.off_dst[a]] = sv;
+                st_b<CS>(dst, k.b_dst[a], sv);
             }
         }
     } else {

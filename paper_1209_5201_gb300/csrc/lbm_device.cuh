@@ -65,6 +65,62 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16>(float
 template <class S> __device__ __forceinline__ S from_c(double v);
 template <> __device__ __forceinline__ double from_c<double>(double v) { return v; }
 
+// ---- addressing of the shifted streams ------------------------------------------
+// A global access at byte offset b (signed) from the 64-bit base p, the
+// offset a per-velocity constant of the solve: the address is one 64-bit add
+// of a warp-uniform constant.  The loads use the read-only path (the source
+// buffer is not written during a step) and ask L2 to fetch the 256-byte
+// block around each 128-byte request: the next warp's shifted segment of the
+// same plane row then hits L2 (about 1 % on the 4096 x 2048 step).
+template <class S> __device__ __forceinline__ S ld_b(const S *p, long long b);
+template <> __device__ __forceinline__ float ld_b<float>(const float *p, long long b) {
+    float v;
+    asm("{\n\t.reg .u64 a;\n\tadd.s64 a, %2, %1;\n\tld.global.nc.L2::256B.f32 %0, [a];\n\t}"
+        : "=f"(v) : "l"(b), "l"(p));
+    return v;
+}
+template <> __device__ __forceinline__ double ld_b<double>(const double *p, long long b) {
+    double v;
+    asm("{\n\t.reg .u64 a;\n\tadd.s64 a, %2, %1;\n\tld.global.nc.L2::256B.f64 %0, [a];\n\t}"
+        : "=d"(v) : "l"(b), "l"(p));
+    return v;
+}
+template <> __device__ __forceinline__ __nv_bfloat16 ld_b<__nv_bfloat16>(const __nv_bfloat16 *p,
+                                                                       long long b) {
+    unsigned short v;
+    asm("{\n\t.reg .u64 a;\n\tadd.s64 a, %2, %1;\n\tld.global.nc.L2::256B.b16 %0, [a];\n\t}"
+        : "=h"(v) : "l"(b), "l"(p));
+    return __ushort_as_bfloat16(v);
+}
+// stores; CS: streaming (evict-first) hint
+template <bool CS>
+__device__ __forceinline__ void st_b(float *p, long long b, float v) {
+    if constexpr (CS)
+        asm volatile("{\n\t.reg .u64 a;\n\tadd.s64 a, %1, %0;\n\tst.global.cs.f32 [a], %2;\n\t}"
+                     :: "l"(b), "l"(p), "f"(v) : "memory");
+    else
+        asm volatile("{\n\t.reg .u64 a;\n\tadd.s64 a, %1, %0;\n\tst.global.f32 [a], %2;\n\t}"
+                     :: "l"(b), "l"(p), "f"(v) : "memory");
+}
+template <bool CS>
+__device__ __forceinline__ void st_b(double *p, long long b, double v) {
+    if constexpr (CS)
+        asm volatile("{\n\t.reg .u64 a;\n\tadd.s64 a, %1, %0;\n\tst.global.cs.f64 [a], %2;\n\t}"
+                     :: "l"(b), "l"(p), "d"(v) : "memory");
+    else
+        asm volatile("{\n\t.reg .u64 a;\n\tadd.s64 a, %1, %0;\n\tst.global.f64 [a], %2;\n\t}"
+                     :: "l"(b), "l"(p), "d"(v) : "memory");
+}
+template <bool CS>
+__device__ __forceinline__ void st_b(unsigned short *p, long long b, unsigned short v) {
+    if constexpr (CS)
+        asm volatile("{\n\t.reg .u64 a;\n\tadd.s64 a, %1, %0;\n\tst.global.cs.b16 [a], %2;\n\t}"
+                     :: "l"(b), "l"(p), "h"(v) : "memory");
+    else
+        asm volatile("{\n\t.reg .u64 a;\n\tadd.s64 a, %1, %0;\n\tst.global.b16 [a], %2;\n\t}"
+                     :: "l"(b), "l"(p), "h"(v) : "memory");
+}
+
 // ---- stochastic rounding of the BF16 store -----------------------------------
 // 16 pseudo-random bits per (step, cell, velocity): one counter-based integer
 // hash per cell ("lowbias32", C. Wellons, hash-prospector, 2018) of the cell's

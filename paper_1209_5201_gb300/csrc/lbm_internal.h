@@ -59,8 +59,10 @@ struct KConsts {
     C e2w;                    // sum_a |e_a|^2 w_a (= D / r^2 up to rounding)
     C th0;                    // r^2 e2w - D, formed in FP64: theta = T - 1 of the
                               // shifted storage without cancellation against D
-    int off_src[kMaxQ];       // a * plane - e_ay * pitch - e_ax: pull source offset
-    int off_dst[kMaxQ];       // a * plane: store offset
+    // byte offsets of the step kernel's accesses from the cell's own element
+    long long b_src[kMaxQ];   // (a * plane - e_ay * pitch - e_ax) elements: pull source
+    long long b_dst[kMaxQ];   // a * plane elements: store
+    long long b_rho[kMaxQ];   // (-e_ay * pitch - e_ax) FP32 elements: source density (BF16DEV)
     int mirror[kMaxQ];        // velocity with (e_x, -e_y): specular partner
     double accom[2];          // wall accommodation (1: diffuse)
     double wcoef[2][kMaxQ];   // g^w_a / D_w (0 unless a leaves the wall)
