@@ -105,7 +105,7 @@ __device__ __forceinline__ void collide_store(const typename Store<PREC>::C (&f)
             // BF16: the rest velocity alone, then each pair (a, a + 1) rounded
             // by one conversion (the same bits as store_rounded)
             const float v0 = f_to_dev(o[0], k.w[0], col.rho);
-            const uint32_t d0 = bf16x2_rounded(v0, v0, hcell * 0x9E3779B9u);   // upper: sr_bits(h, 0)
+            const uint32_t d0 = bf16x2_rounded(v0, v0, sr_word(hcell, 0));   // upper: sr_bits(h, 0)
             unsigned short *d16 = reinterpret_cast<unsigned short *>(dst);
             st_b<false>(d16, k.b_dst[0], (unsigned short)(d0 >> 16));
             PairLoop<1, Q>::run([&](auto ic) {

@@ -136,8 +136,23 @@ __device__ __forceinline__ uint32_t sr_cell(uint32_t step, uint32_t cell) {
     x ^= x >> 16;
     return x;
 }
+// 32 random bits of the velocity pair led by odd A (and of the rest
+// velocity, A = 0): the cell hash times an odd multiplier that depends on A,
+// modulo 2^32.  An odd multiplier permutes the 32-bit words, so the product
+// is uniform when the hash is; its lower half is a permutation of the hash's
+// lower 16 bits and, for each of those, its upper half runs uniformly over
+// the hash's upper 16 bits, so the two halves are uniform and independent.
+// (The high word of the 64-bit product is not uniform: it stays below the
+// multiplier, and its upper bits would round down more often than up.)
+__device__ __forceinline__ uint32_t sr_word(uint32_t hcell, int A) {
+    return hcell * (0x9E3779B9u * (2u * (uint32_t)A + 1u));
+}
+// 16 random bits of velocity a: the upper half of its pair's word for the
+// rest velocity and the odd member a of a pair (a, a + 1), the lower half for
+// the even member
 __device__ __forceinline__ uint32_t sr_bits(uint32_t hcell, int a) {
-    return (hcell * (0x9E3779B9u * (2u * (uint32_t)a + 1u))) >> 16;
+    if (a == 0 || (a & 1)) return sr_word(hcell, a) >> 16;
+    return sr_word(hcell, a - 1) & 0xffffu;
 }
 // The value to store: BF16 keeps the top 16 bits of the FP32 pattern; adding
 // 16 random bits below them first rounds up with probability equal to the
@@ -165,12 +180,8 @@ __device__ __forceinline__ uint32_t bf16x2_rounded(float va, float vb, uint32_t 
     return d;
 }
 // random bits of the pair (a, a + 1) for bf16x2_rounded: sr_bits(h, a) in the
-// upper half, sr_bits(h, a + 1) in the lower
-__device__ __forceinline__ uint32_t sr_bits_pair(uint32_t hcell, int a) {
-    const uint32_t ha = hcell * (0x9E3779B9u * (2u * (uint32_t)a + 1u));
-    const uint32_t hb = hcell * (0x9E3779B9u * (2u * (uint32_t)a + 3u));
-    return __byte_perm(hb, ha, 0x7632);
-}
+// upper half, sr_bits(h, a + 1) in the lower (one multiply for both)
+__device__ __forceinline__ uint32_t sr_bits_pair(uint32_t hcell, int a) { return sr_word(hcell, a); }
 
 // ---- stochastic rounding of FP32 results (batched path) -----------------------
 // f + t rounded to FP32 stochastically, from 32 random bits x: a uniform
