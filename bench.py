@@ -675,17 +675,26 @@ def main():
     # ---- end to end through the public API with host buffers --------------------
     # per job: init from a pinned host density field, the K steps, then the four
     # macroscopic fields back into pinned host memory
+    # (one untimed pass first, then the median of three timed passes: the
+    # first host-buffer round trip of a process pays one-off host costs)
     rho_h = torch.from_numpy(inputs.rho_field(cfg.Nx, cfg.Ny, 1e-3, seed=7)).pin_memory()
     outs = [torch.empty((cfg.Ny, cfg.Nx), dtype=torch.float64).pin_memory() for _ in range(4)]
-    barrier()
-    t0 = time.perf_counter()
-    lbm.lbm_solver_init_fields(s.h, rho_h.numpy())
-    s.step(args.steps)
-    lbm.lbm_solver_macros(s.h, *[o.numpy() for o in outs])
-    e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    passes = []
+    for rep in range(4):
+        barrier()
+        t0 = time.perf_counter()
+        lbm.lbm_solver_init_fields(s.h, rho_h.numpy())
+        s.step(args.steps)
+        lbm.lbm_solver_macros(s.h, *[o.numpy() for o in outs])
+        dt = reduce_max(time.perf_counter() - t0, dist, "cuda")
+        if rep > 0:
+            passes.append(dt)
+    e2e_s = statistics.median(passes)
     e2e = {"value": job_rate(world, cells, args.steps, e2e_s), "unit": "MLUPS",
            "h2d_bytes_per_step": cells * 8 / args.steps,
-           "d2h_bytes_per_step": 4 * cells * 8 / args.steps}
+           "d2h_bytes_per_step": 4 * cells * 8 / args.steps,
+           "passes": "median of 3 timed passes after 1 untimed",
+           "pass_ms": [round(1e3 * p, 3) for p in passes]}
     s.close()
 
     if rank != 0:

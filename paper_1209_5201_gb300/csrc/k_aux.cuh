@@ -230,20 +230,36 @@ template <int Q, int PREC>
 __global__ void k_mass_partials(const typename Store<PREC>::S *f, const float *rplane,
                                 const __grid_constant__ KConsts<typename Store<PREC>::C> k,
                                 double *partials) {
-    const long long n = (long long)k.Nx * k.Ny;
+    // rows j = blockIdx.x, + gridDim.x, ...; the block's threads stride over x
+    // (no division per cell).  FP32 / BF16DEV storage: a cell's sum of stored
+    // deviations is formed in FP32 (they are small, so its rounding is far
+    // below FP32 resolution of the cell's mass) and added to an FP64 total;
+    // FP64 storage sums in FP64.
     double acc[1] = {0.0};
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
-        const long long ro = (long long)j * k.pitch + x + kPadL;
-        double s = Store<PREC>::shifted ? 1.0 : 0.0;     // sum of the weights
+    double wsum = 0.0;
+    if constexpr (Store<PREC>::dev) {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            auto v = to_c(f[(long long)a * k.plane + ro]);
-            if constexpr (Store<PREC>::dev) v += k.w[a] * rplane[ro];
-            s += (double)v;
+        for (int a = 0; a < Q; ++a) wsum += (double)k.w[a];
+    }
+    for (int j = blockIdx.x; j < k.Ny; j += gridDim.x) {
+        const typename Store<PREC>::S *row = f + (long long)j * k.pitch + kPadL;
+        for (int x = threadIdx.x; x < k.Nx; x += blockDim.x) {
+            if constexpr (PREC == LBM_FP64) {
+                double s = 0.0;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) s += row[(long long)a * k.plane + x];
+                acc[0] += s;
+            } else {
+                float sd = 0.0f;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) sd += to_c(row[(long long)a * k.plane + x]);
+                double s = (double)sd;
+                if constexpr (Store<PREC>::shifted) s += 1.0;    // sum of the weights
+                if constexpr (Store<PREC>::dev)
+                    s += wsum * (double)rplane[(long long)j * k.pitch + kPadL + x];
+                acc[0] += s;
+            }
         }
-        acc[0] += s;
     }
     block_sum<1>(acc, partials + blockIdx.x);
 }

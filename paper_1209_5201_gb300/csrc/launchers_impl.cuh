@@ -39,9 +39,9 @@ inline int aux_blocks(long long n) {
 // ---- direct kernel variants {BX, MINB, CS, RS} ----------------------------------
 // RS: rows per block
 struct DirectVariants {
-    static constexpr int n = 7;
-    static constexpr int v[n][4] = {{128, 0, 0, 1}, {64, 0, 0, 1},  {128, 8, 0, 1}, {256, 0, 0, 1},
-                                    {128, 0, 1, 1}, {192, 0, 0, 1}, {128, 0, 0, 2}};
+    static constexpr int n = 8;
+    static constexpr int v[n][4] = {{128, 0, 0, 1}, {64, 0, 0, 1},  {128, 6, 0, 1}, {256, 0, 0, 1},
+                                    {128, 0, 1, 1}, {192, 0, 0, 1}, {128, 0, 0, 2}, {128, 5, 0, 1}};
 };
 
 template <int Q, int PREC, int BX, int MINB, bool CS, int RS>
@@ -70,6 +70,7 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
         LBM_DIRECT_CASE(4)
         LBM_DIRECT_CASE(5)
         LBM_DIRECT_CASE(6)
+        LBM_DIRECT_CASE(7)
     default: break;
     }
 #undef LBM_DIRECT_CASE
