@@ -632,7 +632,10 @@ def main():
     s.init()
     nd, ns = s.variant_count(1), s.variant_count(2)
     for kv in ([] if args.no_variants else [(1, v) for v in range(nd)] + [(2, v) for v in range(ns)]):
-        s.set_kernel(*kv)
+        try:
+            s.set_kernel(*kv)
+        except lbm.LBMError:
+            continue               # the staged kernel on a grid of several x-tiles
         s.step(3)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)

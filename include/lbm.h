@@ -252,9 +252,12 @@ int lbm_solver_stats(lbm_solver *s, lbm_stats *st);
  * kernel whose producer warp stages each velocity's shifted source window
  * (tile plus the +-3-cell halo, rounded to 16 bytes in x) into shared memory
  * with TMA; `variant` picks one of the compiled tile shapes, 0 <= variant <
- * nvariants.  AUTO uses DIRECT variant 0 until set_kernel or autotune picks
- * another.  Both compute the
- * same step (Eq. (5) with Eq. (12)).  Errors: LBM_EINVAL. */
+ * nvariants; it runs grids stored as one x-tile only (Nx + 8 columns within
+ * the tile pitch: 1056 elements for FP32 and FP64, 1088 for BF16DEV; wider
+ * grids are stored as several x-tiles of that pitch).  AUTO uses DIRECT
+ * variant 0 until set_kernel or autotune picks another.  Both compute the
+ * same step (Eq. (5) with Eq. (12)).  Errors: LBM_EINVAL (also STAGED on a
+ * grid of several x-tiles). */
 int lbm_solver_set_kernel(lbm_solver *s, int32_t kernel, int32_t variant);
 
 /* Limit, in nanoseconds of the GPU's global timer, of each bounded wait of

@@ -22,11 +22,36 @@ size_t storage_elem_bytes(int precision) {
     return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
 }
 
-int padded_pitch(int Nx, int precision) {
-    // row = kPadL images | Nx columns | kPadL images, rounded to 128 bytes
+int padded_pitch(int Nx, int precision) { return tile_layout(Nx, precision).pitch; }
+
+TileLayout tile_layout(int Nx, int precision) {
+    // one tile with a compact segment (kPadL | Nx columns | kPadL, rounded to
+    // 128 bytes) for narrow grids; the smallest pitch class holding the row
+    // once that is at most twice the row; past the widest class of the
+    // precision, the fewest tiles of it, the columns spread evenly (every tile
+    // but the last holds tw, the last the rest)
     const int per128 = (int)(128 / storage_elem_bytes(precision));
     const int n = Nx + 2 * kPadL;
-    return (n + per128 - 1) / per128 * per128;
+    TileLayout t;
+    t.nt = 1;
+    t.tw = Nx;
+    if (2 * n <= pitch_class(precision, 0)) {
+        t.pitch = (n + per128 - 1) / per128 * per128;
+        return t;
+    }
+    const int wide = widest_pitch_class(precision);
+    for (int c = 0; c <= wide; ++c)
+        if (n <= pitch_class(precision, c)) {
+            t.pitch = pitch_class(precision, c);
+            return t;
+        }
+    const int tp = pitch_class(precision, wide);
+    const int cols = tp - 2 * kPadL;
+    t.pitch = tp;
+    t.nt = (Nx + cols - 1) / cols;
+    t.tw = (Nx + t.nt - 1) / t.nt;
+    if (Nx - (t.nt - 1) * t.tw < 2 * kPadL) ++t.nt, t.tw = (Nx + t.nt - 1) / t.nt;
+    return t;
 }
 
 namespace {
@@ -40,10 +65,11 @@ struct Layout {
 
 Layout layout_of(const LatticeHost &L, const lbm_params &p) {
     Layout lo;
-    const size_t pitch = (size_t)padded_pitch(p.Nx, p.precision);
+    const TileLayout tl = tile_layout(p.Nx, p.precision);
+    const size_t row = (size_t)tl.nt * tl.pitch;     // elements of one row of one velocity
     const size_t cells = (size_t)p.Nx * p.Ny;
-    lo.f_bytes = align_up((size_t)L.Q * p.Ny * pitch * storage_elem_bytes(p.precision));
-    lo.rho_bytes = p.precision == LBM_BF16DEV ? align_up((size_t)p.Ny * pitch * 4) : 0;
+    lo.f_bytes = align_up((size_t)L.Q * p.Ny * row * storage_elem_bytes(p.precision));
+    lo.rho_bytes = p.precision == LBM_BF16DEV ? align_up((size_t)p.Ny * row * 4) : 0;
     lo.stage_bytes = align_up(5 * cells * 8);
     lo.prev_bytes = align_up(2 * cells * 8);
     lo.red_bytes = align_up((1024 * 8 + 64) * 8);
@@ -56,7 +82,12 @@ int check_params(const LatticeHost &L, const lbm_params &p) {
         set_error("need Nx >= 1 and Ny >= 2 * ghost depth");
         return LBM_EINVAL;
     }
-    if ((long long)L.Q * p.Ny * padded_pitch(p.Nx, p.precision) > (1LL << 31) - 1) {
+    if (p.Nx > (1 << 24)) {
+        set_error("grid too large (Nx)");
+        return LBM_EINVAL;
+    }
+    const TileLayout tl = tile_layout(p.Nx, p.precision);
+    if ((long long)L.Q * p.Ny * tl.nt * tl.pitch > (1LL << 31) - 1) {
         set_error("grid too large (Q * Ny * padded row must fit in 31 bits)");
         return LBM_EINVAL;
     }
@@ -179,8 +210,13 @@ void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int p
     std::memset(&k, 0, sizeof(k));
     k.Nx = p.Nx;
     k.Ny = p.Ny;
+    k.Q = L.Q;
+    const TileLayout tl = tile_layout(p.Nx, p.precision);
     k.pitch = pitch;
-    k.plane = (long long)p.Ny * pitch;
+    k.nt = tl.nt;
+    k.tw = tl.tw;
+    k.tile_elems = (long long)p.Ny * L.Q * pitch;
+    k.tile_rho = (long long)p.Ny * pitch;
     k.wait_ns = kDefaultWaitNs;
     k.thermal = p.thermal;
     k.eq_order = p.eq_order;
@@ -196,8 +232,8 @@ void fill_consts(KConsts<C> &k, const LatticeHost &L, const lbm_params &p, int p
         k.wsh[L.shell[a]] = (C)L.w[a];
         k.c2sh[L.shell[a]] = (C)(L.r * L.r * (L.ex[a] * L.ex[a] + L.ey[a] * L.ey[a]));
         const long long es = (long long)storage_elem_bytes(p.precision);
-        k.b_src[a] = es * ((long long)a * k.plane - (long long)L.ey[a] * pitch - L.ex[a]);
-        k.b_dst[a] = es * ((long long)a * k.plane);
+        k.b_src[a] = es * ((long long)(a - L.ey[a] * L.Q) * pitch - L.ex[a]);
+        k.b_dst[a] = es * ((long long)a * pitch);
         k.b_rho[a] = 4LL * (-(long long)L.ey[a] * pitch - L.ex[a]);
     }
     double e2w = 0;
@@ -404,6 +440,7 @@ int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
     s.p = *p;
     s.stream = (cudaStream_t)stream;
     s.pitch = padded_pitch(p->Nx, p->precision);
+    s.nt = tile_layout(p->Nx, p->precision).nt;
     s.elem = storage_elem_bytes(p->precision);
     s.owns_mem = device_mem == nullptr;
     s.dbytes = lo.total;
@@ -603,7 +640,7 @@ int lbm_solver_set_f(lbm_solver *h, const double *f) {
             CU(cudaMemcpyAsync(s.stage, f + a * n, n * sizeof(double), cudaMemcpyHostToDevice, s.stream));
             CU(launch_accumulate(s.stream, acc, s.stage, (long long)n, a == 0));
         }
-        CU(launch_rho_plane(s.stream, s.rho[s.cur], acc, s.p.Nx, s.p.Ny, s.pitch));
+        CU(launch_rho_plane(s.stream, s.rho[s.cur], acc, s.kf));
     }
     for (int a = 0; a < s.L.Q; ++a) {
         CU(cudaMemcpyAsync(s.stage, f + a * n, n * sizeof(double), cudaMemcpyHostToDevice, s.stream));
@@ -683,8 +720,8 @@ int lbm_solver_fluxes(lbm_solver *h, double *sxx, double *sxy, double *syy, doub
 int lbm_solver_state_bytes(lbm_solver *h, size_t *bytes) {
     if (!h || !bytes) { set_error("NULL argument"); return LBM_EINVAL; }
     const SolverImpl &s = h->s;
-    const size_t fb = (size_t)s.L.Q * s.p.Ny * s.pitch * s.elem;
-    const size_t rb = s.rho[0] ? (size_t)s.p.Ny * s.pitch * 4 : 0;
+    const size_t fb = (size_t)s.L.Q * s.p.Ny * s.nt * s.pitch * s.elem;
+    const size_t rb = s.rho[0] ? (size_t)s.p.Ny * s.nt * s.pitch * 4 : 0;
     *bytes = 64 + fb + rb;
     return LBM_OK;
 }
@@ -711,9 +748,9 @@ int lbm_solver_get_state(lbm_solver *h, void *buf, size_t bytes) {
     char *b = (char *)buf;
     std::memset(b, 0, 64);
     std::memcpy(b, &hd, sizeof(hd));
-    const size_t fb = (size_t)s.L.Q * s.p.Ny * s.pitch * s.elem;
+    const size_t fb = (size_t)s.L.Q * s.p.Ny * s.nt * s.pitch * s.elem;
     CU(cudaMemcpyAsync(b + 64, s.f[s.cur], fb, cudaMemcpyDeviceToHost, s.stream));
-    if (s.rho[0]) CU(cudaMemcpyAsync(b + 64 + fb, s.rho[s.cur], (size_t)s.p.Ny * s.pitch * 4, cudaMemcpyDeviceToHost, s.stream));
+    if (s.rho[0]) CU(cudaMemcpyAsync(b + 64 + fb, s.rho[s.cur], (size_t)s.p.Ny * s.nt * s.pitch * 4, cudaMemcpyDeviceToHost, s.stream));
     CU(cudaStreamSynchronize(s.stream));
     return LBM_OK;
     API_END
@@ -732,9 +769,9 @@ int lbm_solver_set_state(lbm_solver *h, const void *buf, size_t bytes) {
         return LBM_EINVAL;
     }
     const char *b = (const char *)buf;
-    const size_t fb = (size_t)s.L.Q * s.p.Ny * s.pitch * s.elem;
+    const size_t fb = (size_t)s.L.Q * s.p.Ny * s.nt * s.pitch * s.elem;
     CU(cudaMemcpyAsync(s.f[s.cur], b + 64, fb, cudaMemcpyHostToDevice, s.stream));
-    if (s.rho[0]) CU(cudaMemcpyAsync(s.rho[s.cur], b + 64 + fb, (size_t)s.p.Ny * s.pitch * 4, cudaMemcpyHostToDevice, s.stream));
+    if (s.rho[0]) CU(cudaMemcpyAsync(s.rho[s.cur], b + 64 + fb, (size_t)s.p.Ny * s.nt * s.pitch * 4, cudaMemcpyHostToDevice, s.stream));
     CU(cudaStreamSynchronize(s.stream));
     s.steps = hd.steps;
     s.mass0 = hd.mass0;
@@ -850,6 +887,10 @@ int lbm_solver_set_kernel(lbm_solver *h, int32_t kernel, int32_t variant) {
                    : kernel == LBM_KERNEL_CELLWARP ? 1
                                                    : direct_variant_count(s.p.precision);
     if (variant < 0 || variant >= nv) { set_error("bad variant"); return LBM_EINVAL; }
+    if (kernel == LBM_KERNEL_STAGED && s.nt != 1) {
+        set_error("the staged kernel runs grids stored as one x-tile only (Nx + 8 <= tile pitch)");
+        return LBM_EINVAL;
+    }
     s.p.kernel = kernel;
     s.variant = variant;
     return LBM_OK;

@@ -114,7 +114,8 @@ int autotune_solver(SolverImpl &s, int trial) {
         if ((rc = time_candidate(s, LBM_KERNEL_DIRECT, v, trial, &ms))) return rc;
         if (ms < best.ms) best = Choice{LBM_KERNEL_DIRECT, v, ms};
     }
-    const int nv = staged_variant_count(s.p.precision);
+    // the staged kernel: grids stored as one x-tile only
+    const int nv = s.nt == 1 ? staged_variant_count(s.p.precision) : 0;
     for (int v = 0; v < nv; ++v) {
         if ((rc = time_candidate(s, LBM_KERNEL_STAGED, v, trial, &ms))) return rc;
         if (ms < best.ms) best = Choice{LBM_KERNEL_STAGED, v, ms};

@@ -47,14 +47,13 @@ __device__ __forceinline__ void store_cell(typename Store<PREC>::S *f, float *rp
                                            typename Store<PREC>::C rho) {
     using S = typename Store<PREC>::S;
     using C = typename Store<PREC>::C;
-    const long long roff = (long long)j * k.pitch;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         C v = o[a];
         if constexpr (Store<PREC>::dev) v -= k.w[a] * rho;
-        store_with_images<S>(f + (long long)a * k.plane + roff, x, k.Nx, from_c<S>(v));
+        store_pop<S>(f, k, a, j, x, from_c<S>(v));
     }
-    if constexpr (Store<PREC>::dev) store_with_images<float>(rplane + roff, x, k.Nx, (float)rho);
+    if constexpr (Store<PREC>::dev) store_rho(rplane, k, j, x, (float)rho);
 }
 
 // f~* = rho0 (1 + amp (2U - 1)) g^eq(0, 1) = rho w_a.
@@ -103,9 +102,9 @@ __global__ void k_plane_to_f64(const typename Store<PREC>::S *f, const float *rp
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
-        const long long r = (long long)j * k.pitch + x + kPadL;
-        double v = (double)to_c(f[(long long)a * k.plane + r]);
-        if constexpr (Store<PREC>::dev) v = (double)(to_c(f[(long long)a * k.plane + r]) + k.w[a] * rplane[r]);
+        const long long r = col_index(k, j, x) + (long long)a * k.pitch;
+        double v = (double)to_c(f[r]);
+        if constexpr (Store<PREC>::dev) v = (double)(to_c(f[r]) + k.w[a] * rplane[rho_index(k, j, x)]);
         if constexpr (Store<PREC>::shifted) v += (double)k.w[a];
         out[c] = v;
     }
@@ -124,10 +123,9 @@ __global__ void k_plane_from_f64(typename Store<PREC>::S *f, const float *rplane
          c += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
         C v = (C)in[c];
-        if constexpr (Store<PREC>::dev) v -= k.w[a] * rplane[(long long)j * k.pitch + x + kPadL];
+        if constexpr (Store<PREC>::dev) v -= k.w[a] * rplane[rho_index(k, j, x)];
         if constexpr (Store<PREC>::shifted) v = (C)(in[c] - (double)k.w[a]);
-        store_with_images<S>(f + (long long)a * k.plane + (long long)j * k.pitch, x, k.Nx,
-                             from_c<S>(v));
+        store_pop<S>(f, k, a, j, x, from_c<S>(v));
     }
 }
 
@@ -147,13 +145,14 @@ __global__ void k_macros(const typename Store<PREC>::S *f, const float *rplane,
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
-        const long long ro = (long long)j * k.pitch + x + kPadL;
+        const long long ro = col_index(k, j, x);
+        const long long rr = rho_index(k, j, x);
         C fv[Q];
         C s0 = 0, sx = 0, sy = 0, se = 0;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            C v = to_c(f[(long long)a * k.plane + ro]);
-            if constexpr (Store<PREC>::dev) v += k.w[a] * rplane[ro];
+            C v = to_c(f[ro + (long long)a * k.pitch]);
+            if constexpr (Store<PREC>::dev) v += k.w[a] * rplane[rr];
             fv[a] = v;
             s0 += v;
             sx += C(L::ex(a)) * v;
@@ -189,13 +188,13 @@ __global__ void k_wall_mass(const typename Store<PREC>::S *f, const float *rplan
         for (int b = 0; b < Q; ++b) {
             const int eyb = L::ey(b);
             if (wall == 0 ? !(eyb < 0) : !(eyb > 0)) continue;
-            const int xs = wrap(xw - L::ex(b), k.Nx) + kPadL;
+            const int xs = wrap(xw - L::ex(b), k.Nx);
             const int depth = eyb < 0 ? -eyb : eyb;
             for (int kk = 0; kk < depth; ++kk) {
                 const int row = wall == 0 ? kk : k.Ny - 1 - kk;
-                double v = (double)to_c(f[(long long)b * k.plane + (long long)row * k.pitch + xs]);
+                double v = (double)to_c(f[col_index(k, row, xs) + (long long)b * k.pitch]);
                 if constexpr (Store<PREC>::dev)
-                    v += (double)k.w[b] * (double)rplane[(long long)row * k.pitch + xs];
+                    v += (double)k.w[b] * (double)rplane[rho_index(k, row, xs)];
                 if constexpr (Store<PREC>::shifted) v += (double)k.w[b];
                 m += v;
             }
@@ -242,21 +241,20 @@ __global__ void k_mass_partials(const typename Store<PREC>::S *f, const float *r
         for (int a = 0; a < Q; ++a) wsum += (double)k.w[a];
     }
     for (int j = blockIdx.x; j < k.Ny; j += gridDim.x) {
-        const typename Store<PREC>::S *row = f + (long long)j * k.pitch + kPadL;
         for (int x = threadIdx.x; x < k.Nx; x += blockDim.x) {
+            const typename Store<PREC>::S *cell = f + col_index(k, j, x);
             if constexpr (PREC == LBM_FP64) {
                 double s = 0.0;
 #pragma unroll
-                for (int a = 0; a < Q; ++a) s += row[(long long)a * k.plane + x];
+                for (int a = 0; a < Q; ++a) s += cell[(long long)a * k.pitch];
                 acc[0] += s;
             } else {
                 float sd = 0.0f;
 #pragma unroll
-                for (int a = 0; a < Q; ++a) sd += to_c(row[(long long)a * k.plane + x]);
+                for (int a = 0; a < Q; ++a) sd += to_c(cell[(long long)a * k.pitch]);
                 double s = (double)sd;
                 if constexpr (Store<PREC>::shifted) s += 1.0;    // sum of the weights
-                if constexpr (Store<PREC>::dev)
-                    s += wsum * (double)rplane[(long long)j * k.pitch + kPadL + x];
+                if constexpr (Store<PREC>::dev) s += wsum * (double)rplane[rho_index(k, j, x)];
                 acc[0] += s;
             }
         }

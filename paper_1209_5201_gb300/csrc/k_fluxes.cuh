@@ -31,14 +31,17 @@ k_fluxes(const typename Store<PREC>::S *__restrict__ fin, const float *__restric
     const int x = x0 + threadIdx.x;
     const bool bot = j < L::N, top = j >= k.Ny - L::N;
     if (bot || top) {
-        wall_prologue<Q, PREC, kFluxThreads>(fin, rin, k, bot ? 0 : 1, x0, s_min);
+        wall_prologue<Q, PREC, kFluxThreads>(fin, rin, k, bot ? 0 : 1, x0,
+                                             min(kFluxThreads, k.Nx - x0) + 6, s_min);
         __syncthreads();
     }
     if (x >= k.Nx) return;
 
     C fc[Q];
-    if (bot || top) pull<Q, PREC, true>(fin, rin, k, x, j, s_min, fc);
-    else pull<Q, PREC, false>(fin, rin, k, x, j, s_min, fc);
+    const typename Store<PREC>::S *src = fin + col_index(k, j, x);
+    const float *rsrc = Store<PREC>::dev ? rin + rho_index(k, j, x) : nullptr;
+    if (bot || top) pull<Q, PREC, true, 0>(fin, rin, src, rsrc, k, x, j, s_min, fc);
+    else pull<Q, PREC, false, 0>(fin, rin, src, rsrc, k, x, j, s_min, fc);
 
     double f[Q];
     double rho = 0.0, jx = 0.0, jy = 0.0;

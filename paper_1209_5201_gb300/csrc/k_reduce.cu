@@ -17,13 +17,13 @@ __global__ void k_accumulate(double *acc, const double *in, long long n, int fir
         acc[c] = first ? in[c] : acc[c] + in[c];
 }
 
-__global__ void k_rho_plane_from_f64(float *rplane, const double *acc, int Nx, int Ny,
-                                     int pitch) {
-    const long long n = (long long)Nx * Ny;
+__global__ void k_rho_plane_from_f64(float *rplane, const double *acc,
+                                     const __grid_constant__ KConsts<float> k) {
+    const long long n = (long long)k.Nx * k.Ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(c / Nx), x = (int)(c % Nx);
-        store_with_images<float>(rplane + (long long)j * pitch, x, Nx, (float)acc[c]);
+        const int j = (int)(c / k.Nx), x = (int)(c % k.Nx);
+        store_rho(rplane, k, j, x, (float)acc[c]);
     }
 }
 
@@ -63,10 +63,9 @@ int launch_accumulate(cudaStream_t st, double *acc, const double *in, long long 
     return (int)cudaGetLastError();
 }
 
-int launch_rho_plane(cudaStream_t st, float *rplane, const double *acc, int Nx, int Ny,
-                     int pitch) {
-    k_rho_plane_from_f64<<<reduction_blocks((long long)Nx * Ny), kAuxThreads, 0, st>>>(
-        rplane, acc, Nx, Ny, pitch);
+int launch_rho_plane(cudaStream_t st, float *rplane, const double *acc, const KConsts<float> &k) {
+    k_rho_plane_from_f64<<<reduction_blocks((long long)k.Nx * k.Ny), kAuxThreads, 0, st>>>(
+        rplane, acc, k);
     return (int)cudaGetLastError();
 }
 

@@ -67,12 +67,11 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
     const uint32_t hcell = Store<PREC>::dev ? sr_cell(seed, (uint32_t)blockIdx.x) : 0u;
     const bool bot = j < L::N, top = j >= k.Ny - L::N;
 
-    // value of population a at padded column xp of row `row`, in the
+    // value of population a at column xc (0 <= xc < Nx) of row `row`, in the
     // collision's form
-    auto load = [&](int a, int row, int xp) -> C {
-        const long long idx = (long long)row * k.pitch + xp;
-        C v = to_c(fin[(long long)a * k.plane + idx]);
-        if constexpr (Store<PREC>::dev) v = dev_to_f(v, k.w[a], rin[idx]);
+    auto load = [&](int a, int row, int xc) -> C {
+        C v = to_c(fin[col_index(k, row, xc) + (long long)a * k.pitch]);
+        if constexpr (Store<PREC>::dev) v = dev_to_f(v, k.w[a], rin[rho_index(k, row, xc)]);
         return v;
     };
 
@@ -88,7 +87,7 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
                 if (lane < s_nt) {
                     const int b = s_tb[wall][lane], kk = s_tk[wall][lane];
                     const int row = wall == 0 ? kk : k.Ny - 1 - kk;
-                    double v = (double)load(b, row, wrap(xw - s_ex[b], k.Nx) + kPadL);
+                    double v = (double)load(b, row, wrap(xw - s_ex[b], k.Nx));
                     if constexpr (SHIFT) v += (double)k.w[b];
                     m = v;
                 }
@@ -108,7 +107,7 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
             const C spec = k.accom[wall] != 1.0 ? specular_source<PREC>(fin, rin, k, a, ex, x, j) : C(0);
             return wall_mix<PREC>(s_min[3 - ex], k.wcoef[wall][a], k.w[a], k.accom[wall], spec);
         }
-        return load(a, sj, x - ex + kPadL);
+        return load(a, sj, wrap(x - ex, k.Nx));
     };
     const int a0 = lane, a1 = lane + 32;
     const C f0 = a0 < Q ? pull(a0) : C(0);
@@ -187,13 +186,12 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
         const C O = sv * (A1v[i] + col.A3 * s2);
         C v = col.relax(f, cwv[i] * (E + O));
         if constexpr (Store<PREC>::dev) v = f_to_dev(v, k.w[a], col.rho);
-        store_with_images<S>(fout + (long long)a * k.plane + (long long)j * k.pitch, x, k.Nx,
-                             store_rounded<S>(v, sr_bits(hcell, a)));
+        store_pop<S>(fout, k, a, j, x, store_rounded<S>(v, sr_bits(hcell, a)));
     };
     if (a0 < Q) relax_store(a0, 0, f0);
     if (a1 < Q) relax_store(a1, 1, f1);
     if constexpr (Store<PREC>::dev)
-        if (lane == 0) store_with_images<float>(rout + (long long)j * k.pitch, x, k.Nx, (float)col.rho);
+        if (lane == 0) store_rho(rout, k, j, x, (float)col.rho);
 }
 
 }  // namespace lbm

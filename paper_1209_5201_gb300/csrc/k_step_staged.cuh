@@ -3,9 +3,10 @@
 //
 // Tile: TX columns x TY rows of fluid cells.  For velocity a the tile pulls
 // the source window shifted by (-e_ax, -e_ay): rows j0 - e_ay .. +TY and
-// columns x0 - 4 .. x0 + TX + 4 of plane a, i.e. the tile plus the x-halo
-// rounded to 16 bytes.  One elected producer thread stages the Q windows of a
-// tile with 3-D TMA boxes (x, y, a) into a ring of STAGES shared-memory
+// columns x0 - 4 .. x0 + TX + 4 of velocity a, i.e. the tile plus the x-halo
+// rounded to 16 bytes.  Grids stored as one x-tile only (their row segments
+// hold every column; see KConsts).  One elected producer thread stages the Q
+// windows of a tile with 3-D TMA boxes (x, a, y) into a ring of STAGES shared-memory
 // buffers; rows outside [0, Ny) arrive zero-filled and are replaced by the
 // diffuse-wall fill.  Consumer warps read their cell's Q values from shared
 // memory (conflict-free, consecutive lanes on consecutive columns), release
@@ -170,7 +171,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                 mbar_arrive_expect_tx(&full[s], Cfg::kTxBytes);
 #pragma unroll
                 for (int a = 0; a < Q; ++a)
-                    tma_load_3d(st + a * Cfg::kPlaneStride, &tm_f, &full[s], x0, j0 - L::ey(a), a);
+                    tma_load_3d(st + a * Cfg::kPlaneStride, &tm_f, &full[s], x0, a, j0 - L::ey(a));
                 if constexpr (Cfg::kDev)
                     tma_load_2d(st + Q * Cfg::kPlaneStride, &tm_r, &full[s], x0, j0 - 3);
             }
@@ -216,14 +217,14 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                     for (int b = 0; b < Q; ++b) {
                         const int eyb = L::ey(b);
                         if (w == 0 ? !(eyb < 0) : !(eyb > 0)) continue;
-                        const int xs = wrap(xw - L::ex(b), k.Nx) + kPadL;
+                        const int xs = wrap(xw - L::ex(b), k.Nx);
                         const int depth = eyb < 0 ? -eyb : eyb;
                         for (int kk = 0; kk < depth; ++kk) {
                             const int row = w == 0 ? kk : k.Ny - 1 - kk;
-                            double v = (double)to_c(fin[(long long)b * k.plane +
-                                                        (long long)row * k.pitch + xs]);
+                            double v = (double)to_c(
+                                fin[col_index(k, row, xs) + (long long)b * k.pitch]);
                             if constexpr (Cfg::kDev)
-                                v += (double)k.w[b] * (double)rin[(long long)row * k.pitch + xs];
+                                v += (double)k.w[b] * (double)rin[rho_index(k, row, xs)];
                             if constexpr (Store<PREC>::shifted) v += (double)k.w[b];
                             m += v;
                         }
@@ -287,17 +288,14 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                 constexpr int A = decltype(ic)::value;
                 col.template pair<A>(fv[q][A], fv[q][A + 1], o[A], o[A + 1]);
             });
-            const long long roff = (long long)j * k.pitch;
             const uint32_t hcell = Cfg::kDev ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 C v = o[a];
                 if constexpr (Cfg::kDev) v = f_to_dev(v, k.w[a], col.rho);
-                store_with_images<S>(fout + (long long)a * k.plane + roff, x, k.Nx,
-                                     store_rounded<S>(v, sr_bits(hcell, a)));
+                store_pop<S>(fout, k, a, j, x, store_rounded<S>(v, sr_bits(hcell, a)));
             }
-            if constexpr (Cfg::kDev)
-                store_with_images<float>(rout + roff, x, k.Nx, (float)col.rho);
+            if constexpr (Cfg::kDev) store_rho(rout, k, j, x, (float)col.rho);
         }
         if (*(volatile int *)stop) break;
     }

@@ -29,7 +29,7 @@ struct Launch {
 
 // Precision-independent kernels (k_reduce.cu).
 int launch_accumulate(cudaStream_t st, double *acc, const double *in, long long n, int first);
-int launch_rho_plane(cudaStream_t st, float *rplane, const double *acc, int Nx, int Ny, int pitch);
+int launch_rho_plane(cudaStream_t st, float *rplane, const double *acc, const KConsts<float> &k);
 int launch_final_sum(cudaStream_t st, const double *partials, int nblocks, int nv, double *out);
 int launch_residual_partials(cudaStream_t st, const double *ux, const double *T, double *uxp,
                              double *Tp, long long n, double Tref, double *partials,

@@ -40,7 +40,7 @@ inline int aux_blocks(long long n) {
 // RS: rows per block
 struct DirectVariants {
     static constexpr int n = 8;
-    static constexpr int v[n][4] = {{128, 0, 0, 1}, {64, 0, 0, 1},  {128, 6, 0, 1}, {256, 0, 0, 1},
+    static constexpr int v[n][4] = {{128, 0, 0, 1}, {128, 7, 0, 1}, {128, 6, 0, 1}, {256, 0, 0, 1},
                                     {128, 0, 1, 1}, {192, 0, 0, 1}, {128, 0, 0, 2}, {128, 5, 0, 1}};
 };
 
@@ -48,20 +48,43 @@ template <int Q, int PREC, int BX, int MINB, bool CS, int RS>
 int launch_direct(SolverImpl &s, int src, int dst) {
     using S = typename Store<PREC>::S;
     const auto &k = Consts<PREC>::get(s);
-    dim3 grid((s.p.Nx + BX - 1) / BX, (s.p.Ny + RS - 1) / RS);
-    k_step_direct<Q, PREC, BX, MINB, CS, RS><<<grid, BX, 0, s.stream>>>(
+    // blocks of BX columns never straddle two x-tiles
+    dim3 grid(k.nt * ((k.tw + BX - 1) / BX), (s.p.Ny + RS - 1) / RS);
+    // a pitch class: offsets as instruction immediates (compiled for the
+    // 37-velocity lattice; the others take the offsets from the constants)
+    if constexpr (Q == 37 && BX == 128 && RS == 1) {
+        constexpr int P0 = pitch_class(PREC, 0), P1 = pitch_class(PREC, 1),
+                      P2 = pitch_class(PREC, 2);
+        if (k.pitch == P0) {
+            k_step_direct<Q, PREC, BX, MINB, CS, RS, P0><<<grid, BX, 0, s.stream>>>(
+                (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
+            return (int)cudaGetLastError();
+        }
+        if (k.pitch == P1) {
+            k_step_direct<Q, PREC, BX, MINB, CS, RS, P1><<<grid, BX, 0, s.stream>>>(
+                (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
+            return (int)cudaGetLastError();
+        }
+        if (k.pitch == P2) {
+            k_step_direct<Q, PREC, BX, MINB, CS, RS, P2><<<grid, BX, 0, s.stream>>>(
+                (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
+            return (int)cudaGetLastError();
+        }
+    }
+    k_step_direct<Q, PREC, BX, MINB, CS, RS, 0><<<grid, BX, 0, s.stream>>>(
         (const S *)s.f[src], (S *)s.f[dst], s.rho[src], s.rho[dst], k);
     return (int)cudaGetLastError();
 }
 
-template <int PREC>
-int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
+// One lattice's direct-kernel variants (the 37-velocity ones, with their
+// pitch-class instantiations, compile in a translation unit of their own).
+template <int PREC, int Q>
+int step_q(SolverImpl &s, int src, int dst, int variant) {
     using V = DirectVariants;
-#define LBM_DIRECT_CASE(I)                                                                 \
-    case I:                                                                                \
-        LBM_DISPATCH_Q(s.L.Q, return (launch_direct<QQ, PREC, V::v[I][0], V::v[I][1],       \
-                                                    (V::v[I][2] != 0), V::v[I][3]>(s, src, dst))); \
-        break;
+#define LBM_DIRECT_CASE(I)                                                                  \
+    case I:                                                                                 \
+        return launch_direct<Q, PREC, V::v[I][0], V::v[I][1], (V::v[I][2] != 0), V::v[I][3]>( \
+            s, src, dst);
     switch (variant) {
         LBM_DIRECT_CASE(0)
         LBM_DIRECT_CASE(1)
@@ -74,6 +97,17 @@ int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
     default: break;
     }
 #undef LBM_DIRECT_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+template <int PREC>
+int Launch<PREC>::step(SolverImpl &s, int src, int dst, int variant) {
+    switch (s.L.Q) {
+    case 17: return step_q<PREC, 17>(s, src, dst, variant);
+    case 25: return step_q<PREC, 25>(s, src, dst, variant);
+    case 37: return step_q<PREC, 37>(s, src, dst, variant);
+    default: break;
+    }
     return (int)cudaErrorInvalidValue;
 }
 
@@ -138,6 +172,7 @@ int launch_staged(SolverImpl &s, int src, int dst) {
         if (e != cudaSuccess) return (int)e;
         attr_set[dev] = true;
     }
+    if (s.nt != 1) return (int)cudaErrorNotSupported;    // one x-tile grids only
     if (encode_tensor_maps(s, TX, TY)) return (int)cudaErrorInvalidValue;
     const int ntiles = ((s.p.Nx + TX - 1) / TX) * ((s.p.Ny + TY - 1) / TY);
     const int grid = ntiles < s.sm_count ? ntiles : s.sm_count;

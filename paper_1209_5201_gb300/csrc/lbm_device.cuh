@@ -92,6 +92,48 @@ template <> __device__ __forceinline__ __nv_bfloat16 ld_b<__nv_bfloat16>(const _
         : "=h"(v) : "l"(b), "l"(p));
     return __ushort_as_bfloat16(v);
 }
+// The same with a compile-time byte offset B (|B| < 2^23), folded into the
+// access instruction: no address arithmetic per access.
+template <class S, long long B> __device__ __forceinline__ S ld_i(const S *p);
+template <class S, long long B> struct LdI;
+template <long long B> struct LdI<float, B> {
+    __device__ __forceinline__ static float go(const float *p) {
+        float v;
+        asm("ld.global.nc.L2::256B.f32 %0, [%1+%2];" : "=f"(v) : "l"(p), "n"(B));
+        return v;
+    }
+};
+template <long long B> struct LdI<double, B> {
+    __device__ __forceinline__ static double go(const double *p) {
+        double v;
+        asm("ld.global.nc.L2::256B.f64 %0, [%1+%2];" : "=d"(v) : "l"(p), "n"(B));
+        return v;
+    }
+};
+template <long long B> struct LdI<__nv_bfloat16, B> {
+    __device__ __forceinline__ static __nv_bfloat16 go(const __nv_bfloat16 *p) {
+        unsigned short v;
+        asm("ld.global.nc.L2::256B.b16 %0, [%1+%2];" : "=h"(v) : "l"(p), "n"(B));
+        return __ushort_as_bfloat16(v);
+    }
+};
+template <class S, long long B> __device__ __forceinline__ S ld_i(const S *p) { return LdI<S, B>::go(p); }
+template <long long B, bool CS>
+__device__ __forceinline__ void st_i(float *p, float v) {
+    if constexpr (CS) asm volatile("st.global.cs.f32 [%0+%1], %2;" :: "l"(p), "n"(B), "f"(v) : "memory");
+    else asm volatile("st.global.f32 [%0+%1], %2;" :: "l"(p), "n"(B), "f"(v) : "memory");
+}
+template <long long B, bool CS>
+__device__ __forceinline__ void st_i(double *p, double v) {
+    if constexpr (CS) asm volatile("st.global.cs.f64 [%0+%1], %2;" :: "l"(p), "n"(B), "d"(v) : "memory");
+    else asm volatile("st.global.f64 [%0+%1], %2;" :: "l"(p), "n"(B), "d"(v) : "memory");
+}
+template <long long B, bool CS>
+__device__ __forceinline__ void st_i(unsigned short *p, unsigned short v) {
+    if constexpr (CS) asm volatile("st.global.cs.b16 [%0+%1], %2;" :: "l"(p), "n"(B), "h"(v) : "memory");
+    else asm volatile("st.global.b16 [%0+%1], %2;" :: "l"(p), "n"(B), "h"(v) : "memory");
+}
+
 // stores; CS: streaming (evict-first) hint
 template <bool CS>
 __device__ __forceinline__ void st_b(float *p, long long b, float v) {
@@ -232,6 +274,20 @@ __device__ __forceinline__ float f_to_dev(float f, float w, float rho) { return 
 __device__ __forceinline__ int wrap(int v, int n) {
     int m = v % n;
     return m < 0 ? m + n : m;
+}
+
+// ---- tiled storage (layout in KConsts) ----------------------------------------
+// Element of velocity 0 of column x (0 <= x < Nx), row j, in a state buffer;
+// velocity a sits a pitch further.  The density of (j, x) in the density plane.
+template <class K>
+__device__ __forceinline__ long long col_index(const K &k, int j, int x) {
+    const int t = k.nt == 1 ? 0 : x / k.tw;
+    return t * k.tile_elems + (long long)j * k.Q * k.pitch + (x - t * k.tw) + kPadL;
+}
+template <class K>
+__device__ __forceinline__ long long rho_index(const K &k, int j, int x) {
+    const int t = k.nt == 1 ? 0 : x / k.tw;
+    return t * k.tile_rho + (long long)j * k.pitch + (x - t * k.tw) + kPadL;
 }
 
 // ---- explicit arithmetic --------------------------------------------------------
@@ -562,9 +618,9 @@ __device__ __forceinline__ typename Store<PREC>::C
 specular_source(const typename Store<PREC>::S *__restrict__ fin, const float *__restrict__ rin,
                 const KConsts<typename Store<PREC>::C> &k, int a, int ex, int x, int j) {
     const int b = k.mirror[a];
-    const long long ro = (long long)j * k.pitch + wrap(x - 2 * ex, k.Nx) + kPadL;
-    auto v = to_c(fin[(long long)b * k.plane + ro]);
-    if constexpr (Store<PREC>::dev) v = dev_to_f(v, k.w[b], rin[ro]);
+    const int xs = wrap(x - 2 * ex, k.Nx);
+    auto v = to_c(fin[col_index(k, j, xs) + (long long)b * k.pitch]);
+    if constexpr (Store<PREC>::dev) v = dev_to_f(v, k.w[b], rin[rho_index(k, j, xs)]);
     return v;
 }
 
@@ -577,6 +633,44 @@ __device__ __forceinline__ void store_with_images(S *__restrict__ row, int x, in
         for (int q = x - Nx; q >= -kPadL; q -= Nx) row[q + kPadL] = v;
         for (int q = x + Nx; q < Nx + kPadL; q += Nx) row[q + kPadL] = v;
     }
+}
+
+// The copies of column x (tile t, tile column xl of a tile of w columns) held
+// in halos: with one tile its periodic images, else the slot in the previous
+// tile's right halo (xl < kPadL) or the next tile's left halo (xl >= w -
+// kPadL).  seg0: this row's segment of the velocity in tile 0; ts: tile stride.
+template <class S, class K>
+__device__ __forceinline__ void store_halo_copies(S *__restrict__ seg0, long long ts, const K &k,
+                                                  int t, int xl, int w, S v) {
+    if (k.nt == 1) {
+        for (int q = xl - k.Nx; q >= -kPadL; q -= k.Nx) seg0[q + kPadL] = v;
+        for (int q = xl + k.Nx; q < k.Nx + kPadL; q += k.Nx) seg0[q + kPadL] = v;
+        return;
+    }
+    if (xl < kPadL) {
+        const int tl = t == 0 ? k.nt - 1 : t - 1;
+        seg0[tl * ts + tile_width(k, tl) + kPadL + xl] = v;
+    }
+    if (xl >= w - kPadL) {
+        const int tr = t == k.nt - 1 ? 0 : t + 1;
+        seg0[tr * ts + xl - w + kPadL] = v;
+    }
+}
+// Population a of (j, x), its own slot and its halo copies.
+template <class S, class K>
+__device__ __forceinline__ void store_pop(S *__restrict__ f, const K &k, int a, int j, int x, S v) {
+    const int t = k.nt == 1 ? 0 : x / k.tw, xl = x - t * k.tw;
+    S *seg0 = f + ((long long)j * k.Q + a) * k.pitch;
+    seg0[t * k.tile_elems + xl + kPadL] = v;
+    store_halo_copies<S>(seg0, k.tile_elems, k, t, xl, tile_width(k, t), v);
+}
+// Density of (j, x) (BF16DEV), its own slot and its halo copies.
+template <class K>
+__device__ __forceinline__ void store_rho(float *__restrict__ r, const K &k, int j, int x, float v) {
+    const int t = k.nt == 1 ? 0 : x / k.tw, xl = x - t * k.tw;
+    float *seg0 = r + (long long)j * k.pitch;
+    seg0[t * k.tile_rho + xl + kPadL] = v;
+    store_halo_copies<float>(seg0, k.tile_rho, k, t, xl, tile_width(k, t), v);
 }
 
 }  // namespace lbm

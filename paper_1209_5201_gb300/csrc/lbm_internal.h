@@ -21,6 +21,27 @@ constexpr int kMaxShells = 8;
 constexpr int kPadL = 4;          // periodic image columns kept left of x = 0
 constexpr long long kCellwarpAutoCells = 4096;   // LBM_KERNEL_AUTO: one warp per cell up to here
 constexpr unsigned long long kDefaultWaitNs = 2000000000ull;   // bounded device waits: 2 s
+// Segment pitches (elements, 128-byte multiples) for which the step kernel
+// has instantiations with the pitch a compile-time constant: a grid of Nx +
+// 2 kPadL > kPitchClass[p][0] / 2 columns is stored with the smallest class
+// that holds its row (one x-tile; at most half of the segment is padding),
+// or, past the widest class of its precision, as x-tiles of that class; a
+// narrower grid keeps a compact pitch.  The widest class was measured per
+// precision (D2Q37 at 4096 x 2048: FP32 0.376 / 0.393 / 0.406 ms per step
+// with one, two and four x-tiles; BF16DEV 0.390 / 0.334 / 0.346 ms).
+constexpr int kPitchClasses = 3;
+inline constexpr int pitch_class(int precision, int c) {
+    return precision == LBM_BF16DEV ? (c == 0 ? 1088 : c == 1 ? 2112 : 4224)
+                                    : (c == 0 ? 1056 : c == 1 ? 2112 : 4224);
+}
+inline constexpr int widest_pitch_class(int precision) {
+    return precision == LBM_BF16DEV ? 1 : 2;
+}
+// Columns of tile t (all tiles hold tw but the last, which holds the rest).
+template <class K>
+__host__ __device__ __forceinline__ int tile_width(const K &k, int t) {
+    return t < k.nt - 1 ? k.tw : k.Nx - (k.nt - 1) * k.tw;
+}
 
 struct LatticeHost {
     int kind;
@@ -42,10 +63,23 @@ double lattice_isotropy_error(const LatticeHost &L, int degree);
 // Per-solve constants handed to every kernel by value.  C is the compute type
 // (float or double); wall coefficients stay FP64 (the wall mass flux is
 // normalised in FP64).
+// Single-domain storage: the columns are split into nt x-tiles; tile t holds
+// columns [t tw, min((t + 1) tw, Nx)) and stores, row by row and within a row
+// velocity by velocity, a segment of `pitch` elements: kPadL halo columns (the
+// previous tile's last kPadL columns, periodic in x), the tile's columns,
+// kPadL halo columns (the next tile's first ones), padding to 128 bytes.
+// Element (a, j, x) of a state buffer sits at t * tile_elems + (j Q + a) pitch
+// + x - t tw + kPadL; the BF16DEV density of (j, x) at t * tile_rho + j pitch +
+// x - t tw + kPadL.  One tile (nt = 1) holds every column, its halos being the
+// periodic images; wide grids use tiles of a fixed pitch (pitch_class), so the
+// step kernel's Q shifted accesses are compile-time offsets from one base.
 template <class C>
 struct KConsts {
-    int Nx, Ny, pitch;
-    long long plane;          // elements per velocity plane = Ny * pitch
+    int Nx, Ny, Q;
+    int pitch;                // elements per (tile, row, velocity) segment
+    int nt, tw;               // number of x-tiles, columns per tile (the last: the rest)
+    long long tile_elems;     // Ny * Q * pitch: one tile of a state buffer
+    long long tile_rho;       // Ny * pitch: one tile of the density plane
     int thermal, eq_order;
     int const_tau;            // 1: tau_lat is used as is
     int mu_is_one;            // mu = T: tau independent of T
@@ -60,9 +94,10 @@ struct KConsts {
     C th0;                    // r^2 e2w - D, formed in FP64: theta = T - 1 of the
                               // shifted storage without cancellation against D
     // byte offsets of the step kernel's accesses from the cell's own element
-    long long b_src[kMaxQ];   // (a * plane - e_ay * pitch - e_ax) elements: pull source
-    long long b_dst[kMaxQ];   // a * plane elements: store
-    long long b_rho[kMaxQ];   // (-e_ay * pitch - e_ax) FP32 elements: source density (BF16DEV)
+    // (a = 0) in its tile
+    long long b_src[kMaxQ];   // ((a - e_ay Q) pitch - e_ax) elements: pull source
+    long long b_dst[kMaxQ];   // a pitch elements: store
+    long long b_rho[kMaxQ];   // (-e_ay pitch - e_ax) FP32 elements: source density (BF16DEV)
     int mirror[kMaxQ];        // velocity with (e_x, -e_y): specular partner
     double accom[2];          // wall accommodation (1: diffuse)
     double wcoef[2][kMaxQ];   // g^w_a / D_w (0 unless a leaves the wall)
@@ -95,7 +130,8 @@ struct SolverImpl {
     size_t red_elems;
     double *pinned;           // host pinned results of reductions (16 doubles)
     int cur;                  // buffer holding the current state
-    int pitch;
+    int pitch;                // segment pitch of the x-tiles (KConsts::pitch)
+    int nt;                   // number of x-tiles
     size_t elem;              // storage bytes per population
     int64_t steps;
     double mass0;
@@ -120,6 +156,11 @@ constexpr int kGraphSteps = 64;   // steps per replayed graph (even: parity kept
 
 // Encode tm_f / tm_r for boxes of (TX + 2 kPadL) x TY (density: TY + 6 rows).
 int encode_tensor_maps(SolverImpl &s, int TX, int TY);
+// The x-tiling of a grid: pitch, number of tiles, columns per tile.
+struct TileLayout {
+    int pitch, nt, tw;
+};
+TileLayout tile_layout(int Nx, int precision);
 int staged_variant_count(int precision);
 int direct_variant_count(int precision);
 int launch_step_variant(SolverImpl &s, int src, int dst, int kernel, int variant);

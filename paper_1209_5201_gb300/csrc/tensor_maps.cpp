@@ -38,9 +38,10 @@ int encode_tensor_maps(SolverImpl &s, int TX, int TY) {
     const cuuint64_t es = (cuuint64_t)s.elem;
     const cuuint32_t W = (cuuint32_t)(TX + 2 * kPadL);
     for (int b = 0; b < 2; ++b) {
-        cuuint64_t dims[3] = {(cuuint64_t)s.pitch, (cuuint64_t)s.p.Ny, (cuuint64_t)s.L.Q};
-        cuuint64_t strides[2] = {(cuuint64_t)s.pitch * es, (cuuint64_t)s.pitch * s.p.Ny * es};
-        cuuint32_t box[3] = {W, (cuuint32_t)TY, 1};
+        // one x-tile: element (a, j, p) at (j Q + a) pitch + p; dims (p, a, j)
+        cuuint64_t dims[3] = {(cuuint64_t)s.pitch, (cuuint64_t)s.L.Q, (cuuint64_t)s.p.Ny};
+        cuuint64_t strides[2] = {(cuuint64_t)s.pitch * es, (cuuint64_t)s.pitch * s.L.Q * es};
+        cuuint32_t box[3] = {W, 1, (cuuint32_t)TY};
         cuuint32_t estr[3] = {1, 1, 1};
         CUresult r = enc(&s.tm_f[b], dt, 3, s.f[b], dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -1,0 +1,7 @@
+// The direct step kernel's variants of the LBM_FP32 storage format for the
+// 37-velocity lattice, with their pitch-class instantiations.
+#include "launchers_impl.cuh"
+
+namespace lbm {
+template int step_q<LBM_FP32, 37>(SolverImpl &, int, int, int);
+}  // namespace lbm

@@ -99,15 +99,17 @@ def test_params_default_and_checks(lbm):
         bad.Kn = float("nan")
         with pytest.raises(lbm.LBMError):
             lbm.lbm_solver_required_bytes(h, bad)
-        # the large-grid workload: two FP32 state buffers of 37 x 2048 x pitch
+        # the large-grid workload: two FP32 state buffers of 37 x 2048 rows of 4
+        # x-tiles of 1056 elements, FP64 staging planes, reduction scratch
         p = lbm.lbm_params_default()
         p.Nx, p.Ny, p.precision = 4096, 2048, lbm.LBM_FP32
         n = lbm.lbm_solver_required_bytes(h, p)
-        assert 2 * 37 * 2048 * 4096 * 4 < n < 2 * 37 * 2048 * 4224 * 4 + 7 * 4096 * 2048 * 8
-        # the largest buffer the kernels' 32-bit offsets address, and one past it
-        p.Nx, p.Ny = 8192, 7000
+        assert 2 * 37 * 2048 * 4224 * 4 < n < 2 * 37 * 2048 * 4224 * 4 + 7 * 4096 * 2048 * 8 + (1 << 20)
+        # the largest buffer the kernels' 32-bit offsets address (8 tiles of
+        # 1056: 37 * 6870 * 8448 < 2^31 elements), and one past it
+        p.Nx, p.Ny = 8192, 6870
         lbm.lbm_solver_required_bytes(h, p)
-        p.Ny = 7100
+        p.Ny = 6871
         with pytest.raises(lbm.LBMError) as ei:
             lbm.lbm_solver_required_bytes(h, p)
         assert ei.value.status == lbm.LBM_EINVAL

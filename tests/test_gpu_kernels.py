@@ -118,6 +118,76 @@ def test_edge_sizes_all_variants(lbm, oracle, Nx, Ny):
         assert rel_err(f, ref) < 1e-12, (kv, Nx, Ny)
 
 
+def direct_kernels(lbm, precision):
+    return [kv for kv in kernels(lbm, precision) if kv[0] == lbm.LBM_KERNEL_DIRECT]
+
+
+# Rows of Nx + 8 > 528 elements are stored with a pitch class (1056 / 2112 /
+# 4224 elements; BF16 1088 / 2112), for which the 37-velocity step has
+# instantiations with the pitch a compile-time constant; past the widest class
+# (FP32 and FP64 4224, BF16 2112) a grid is stored as x-tiles of it, each with
+# halos of its neighbours' columns.  700 columns: one tile of pitch 1056; 1101:
+# one tile of pitch 2112; 4301: two tiles of 2151 and 2150 columns.
+@pytest.mark.parametrize("precision,Nx,tol", [("fp64", 700, 1e-12), ("fp32", 1101, 1e-5),
+                                              ("fp64", 4301, 1e-12), ("fp32", 4301, 1e-5)])
+def test_pitch_class_grids_every_direct_variant_matches_oracle(lbm, oracle, precision, Nx, tol):
+    Ny, n = 10, 30
+    kw = dict(Kn=0.05, u_wall=(-0.3, 0.3), T_wall=(1.02, 0.98))
+    ref = first = None
+    for kv in direct_kernels(lbm, precision):
+        f, p, perm, rho = run_variant(lbm, oracle, "D2Q37", Nx, Ny, precision, kv, n, **kw)
+        if ref is None:
+            fo = oracle.init_fields(p, rho)
+            oracle.run(p, fo, n)
+            ref = oracle.collide(p, fo)[perm]
+            first = f
+        assert rel_err(f, ref) < tol, kv
+        assert np.array_equal(f, first), kv
+
+
+def test_tiled_grid_bf16_variants_agree_and_staged_is_refused(lbm, oracle):
+    # 2201 columns in BF16: two x-tiles of 1101 and 1100 columns (pitch 2112)
+    outs = [run_variant(lbm, oracle, "D2Q37", 2201, 9, "bf16dev", kv, 20, Kn=0.05,
+                        u_wall=(-0.3, 0.3))[0] for kv in direct_kernels(lbm, "bf16dev")]
+    for f in outs[1:]:
+        assert np.array_equal(f, outs[0])
+    s = lbm.Solver(lbm.Config(lattice="D2Q37", Nx=2201, Ny=9, eq_order=4, thermal=True,
+                              precision="bf16dev"))
+    with pytest.raises(lbm.LBMError) as ei:
+        s.set_kernel(lbm.LBM_KERNEL_STAGED, 0)
+    assert ei.value.status == lbm.LBM_EINVAL
+    s.close()
+
+
+def test_three_tiles_other_lattice_and_accommodation(lbm, oracle):
+    # D2Q17 on 8500 columns: three x-tiles (2834, 2834, 2832 columns), the
+    # step with its pitch from the constants; partly specular walls, whose
+    # mirrored source lies up to 6 columns away, across tile boundaries
+    Nx, Ny, n = 8500, 8, 20
+    accom = (0.6, 0.8)
+    kw = dict(lattice="D2Q17", Nx=Nx, Ny=Ny, eq_order=2, thermal=False, Kn=0.07,
+              u_wall=(-0.2, 0.15))
+    p = oracle.Problem(**kw, accom=accom)
+    rho = inputs.rho_field(Nx, Ny, 1e-2, seed=5)
+    fo = oracle.init_fields(p, rho)
+    oracle.run(p, fo, n)
+    pos = {tuple(v): i for i, v in enumerate(p.lat.e.tolist())}
+    first = None
+    for kv in direct_kernels(lbm, "fp64"):
+        s = lbm.Solver(lbm.Config(**kw, precision="fp64", accom=accom))
+        s.set_kernel(*kv)
+        s.init_fields(rho)
+        s.step(n)
+        s.sync()
+        f = s.get_f()
+        perm = np.array([pos[tuple(v)] for v in s.lat.e.tolist()])
+        s.close()
+        assert rel_err(f, oracle.collide(p, fo)[perm]) < 1e-12, kv
+        if first is None:
+            first = f
+        assert np.array_equal(f, first), kv
+
+
 def test_autotune_picks_a_compiled_kernel_and_reinitialises(lbm, oracle):
     cfg = lbm.Config(lattice="D2Q37", Nx=512, Ny=64, eq_order=4, thermal=True,
                      precision="fp32", noise_amp=1e-3)
@@ -165,11 +235,11 @@ def test_full_size_workload_sampled_columns(lbm, oracle):
 
 
 def test_largest_grid_the_offsets_address(lbm, oracle):
-    # D2Q37 FP32 at 8192 x 7000: a state buffer just under 2^31 elements, so
-    # the velocity-plane offsets of the step kernel reach their largest
-    # values; no density noise, so every column equals the oracle's
-    # single-column solve of the same height
-    Nx, Ny, n = 8192, 7000, 8
+    # D2Q37 FP32 at 8192 x 6870 (two x-tiles of 4096 columns): a state buffer
+    # just under 2^31 elements, so the tile offsets of the step kernel reach
+    # their largest values; no density noise, so every column equals the
+    # oracle's single-column solve of the same height
+    Nx, Ny, n = 8192, 6870, 8
     cfg = lbm.Config(lattice="D2Q37", Nx=Nx, Ny=Ny, eq_order=4, thermal=True, Kn=0.05,
                      u_wall=(-0.3, 0.3), precision="fp32", kernel=lbm.LBM_KERNEL_DIRECT)
     s = lbm.Solver(cfg)
