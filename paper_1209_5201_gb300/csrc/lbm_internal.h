@@ -24,19 +24,18 @@ constexpr unsigned long long kDefaultWaitNs = 2000000000ull;   // bounded device
 // Segment pitches (elements, 128-byte multiples) for which the step kernel
 // has instantiations with the pitch a compile-time constant: a grid of Nx +
 // 2 kPadL > kPitchClass[p][0] / 2 columns is stored with the smallest class
-// that holds its row (one x-tile; at most half of the segment is padding),
-// or, past the widest class of its precision, as x-tiles of that class; a
-// narrower grid keeps a compact pitch.  The widest class was measured per
-// precision (D2Q37 at 4096 x 2048: FP32 0.376 / 0.393 / 0.406 ms per step
-// with one, two and four x-tiles; BF16DEV 0.390 / 0.334 / 0.346 ms).
+// that holds its row (one x-tile; at most half of the segment is padding,
+// which no kernel touches), or, past the widest class, as x-tiles of it; a
+// narrower grid keeps a compact pitch.  Wider tiles measured faster (D2Q37 at
+// 4096 x 2048: FP32 one tile of 4224 0.378 ms per step against four of 1056
+// 0.406 ms; BF16DEV one tile 0.325 ms against two of 2112 0.337 ms): fewer
+// separate row segments are streamed at once.
 constexpr int kPitchClasses = 3;
 inline constexpr int pitch_class(int precision, int c) {
     return precision == LBM_BF16DEV ? (c == 0 ? 1088 : c == 1 ? 2112 : 4224)
                                     : (c == 0 ? 1056 : c == 1 ? 2112 : 4224);
 }
-inline constexpr int widest_pitch_class(int precision) {
-    return precision == LBM_BF16DEV ? 1 : 2;
-}
+inline constexpr int widest_pitch_class(int) { return kPitchClasses - 1; }
 // Columns of tile t (all tiles hold tw but the last, which holds the rest).
 template <class K>
 __host__ __device__ __forceinline__ int tile_width(const K &k, int t) {

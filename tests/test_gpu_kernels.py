@@ -123,10 +123,10 @@ def direct_kernels(lbm, precision):
 
 
 # Rows of Nx + 8 > 528 elements are stored with a pitch class (1056 / 2112 /
-# 4224 elements; BF16 1088 / 2112), for which the 37-velocity step has
+# 4224 elements; BF16 1088 / 2112 / 4224), for which the 37-velocity step has
 # instantiations with the pitch a compile-time constant; past the widest class
-# (FP32 and FP64 4224, BF16 2112) a grid is stored as x-tiles of it, each with
-# halos of its neighbours' columns.  700 columns: one tile of pitch 1056; 1101:
+# (4224) a grid is stored as x-tiles of it, each with halos of its
+# neighbours' columns.  700 columns: one tile of pitch 1056; 1101:
 # one tile of pitch 2112; 4301: two tiles of 2151 and 2150 columns.
 @pytest.mark.parametrize("precision,Nx,tol", [("fp64", 700, 1e-12), ("fp32", 1101, 1e-5),
                                               ("fp64", 4301, 1e-12), ("fp32", 4301, 1e-5)])
@@ -146,12 +146,12 @@ def test_pitch_class_grids_every_direct_variant_matches_oracle(lbm, oracle, prec
 
 
 def test_tiled_grid_bf16_variants_agree_and_staged_is_refused(lbm, oracle):
-    # 2201 columns in BF16: two x-tiles of 1101 and 1100 columns (pitch 2112)
-    outs = [run_variant(lbm, oracle, "D2Q37", 2201, 9, "bf16dev", kv, 20, Kn=0.05,
+    # 4301 columns in BF16: two x-tiles of 2151 and 2150 columns (pitch 4224)
+    outs = [run_variant(lbm, oracle, "D2Q37", 4301, 9, "bf16dev", kv, 20, Kn=0.05,
                         u_wall=(-0.3, 0.3))[0] for kv in direct_kernels(lbm, "bf16dev")]
     for f in outs[1:]:
         assert np.array_equal(f, outs[0])
-    s = lbm.Solver(lbm.Config(lattice="D2Q37", Nx=2201, Ny=9, eq_order=4, thermal=True,
+    s = lbm.Solver(lbm.Config(lattice="D2Q37", Nx=4301, Ny=9, eq_order=4, thermal=True,
                               precision="bf16dev"))
     with pytest.raises(lbm.LBMError) as ei:
         s.set_kernel(lbm.LBM_KERNEL_STAGED, 0)
