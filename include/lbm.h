@@ -152,7 +152,10 @@ int lbm_solver_required_bytes(const lbm_lattice *lat, const lbm_params *p,
  * passes a torch allocation); if NULL the library allocates (and frees) its
  * own with cudaMallocAsync on `stream`.  The lattice may be destroyed after
  * this call.  Errors: LBM_EINVAL (parameters; Ny < 2 N, eq_order, precision,
- * or Q x Ny x padded row >= 2^31 elements per state buffer), LBM_ENOMEM,
+ * or Q x Ny x stored row >= 2^31 elements per state buffer, a stored row
+ * being the grid's x-tiles' segments: Nx + 8 rounded up to 128 bytes, or to a
+ * pitch class of 1056 / 2112 / 4224 elements, 1088 / 2112 / 4224 for
+ * BF16DEV, or tiles of 4224), LBM_ENOMEM,
  * LBM_ECUDA. */
 int lbm_solver_create(const lbm_lattice *lat, const lbm_params *p, void *stream,
                       void *device_mem, size_t device_bytes, lbm_solver **out);
