@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(lattice="D2Q37", Nx=4096, Ny=2048, eq_order=4, thermal=True, Kn=0.05,
                 u_wall=(-0.3, 0.3), T_wall=(1.0, 1.0), noise_amp=1e-3, seed=7)
-BYTES_PER_LU = {"fp32": 8 * 37, "fp64": 16 * 37, "bf16dev": 4 * 37 + 8}
-DTYPE = {"fp32": "f32", "fp64": "f64", "bf16dev": "bf16-storage/f32"}
+BYTES_PER_LU = {"fp32": 8 * 37, "fp64": 16 * 37, "bf16dev": 4 * 37 + 8, "bf16shift": 4 * 37}
+DTYPE = {"fp32": "f32", "fp64": "f64", "bf16dev": "bf16-storage/f32", "bf16shift": "bf16-storage/f32"}
 
 
 def reduce_max(value: float, dist=None, device="cpu") -> float:
@@ -563,7 +563,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev", "bf16shift"])
     ap.add_argument("--kernel", type=int, default=-1,
                     help="-1: autotune; 1: direct; 2: staged (with --variant)")
     ap.add_argument("--variant", type=int, default=0)

@@ -104,6 +104,14 @@ int lbm_lattice_verify(const lbm_lattice *lat, int degree, double *max_err);
                             the stored d stochastically (unbiased, from a
                             counter-based hash of step, cell and velocity), so
                             results are reproducible run to run             */
+#define LBM_BF16SHIFT 3  /* BF16 storage of d_a = f~*_a - w_a rho_0 (rho_0 = 1,
+                            the reference density of the non-dimensional
+                            variables, Sec. IV), FP32 arithmetic on the
+                            deviations (the collision of LBM_FP32), the same
+                            stochastic rounding of the stored d as
+                            LBM_BF16DEV; no density plane: 4 Q bytes per cell
+                            and step move through HBM.  Kernels: DIRECT and
+                            CELLWARP (STAGED is LBM_EINVAL)                  */
 
 #define LBM_KERNEL_AUTO     0   /* library picks                             */
 #define LBM_KERNEL_DIRECT   1   /* one-pass pull kernel, global loads         */
@@ -122,7 +130,7 @@ typedef struct lbm_params {
     double mu_exp;       /* viscosity law exponent, default 1                  */
     double u_wall[2];    /* x-velocity of bottom and top wall                  */
     double T_wall[2];    /* wall temperatures; isothermal runs use 1           */
-    int32_t precision;   /* LBM_FP64 / LBM_FP32 / LBM_BF16DEV                  */
+    int32_t precision;   /* LBM_FP64 / LBM_FP32 / LBM_BF16DEV / LBM_BF16SHIFT  */
     int32_t kernel;      /* LBM_KERNEL_*                                       */
     double rho0;         /* initial density of lbm_solver_init                 */
     double noise_amp;    /* initial rho = rho0 (1 + noise_amp (2U - 1))        */

@@ -92,7 +92,7 @@ int check_params(const LatticeHost &L, const lbm_params &p) {
         return LBM_EINVAL;
     }
     if (p.eq_order < 2 || p.eq_order > 4) { set_error("eq_order must be 2, 3 or 4"); return LBM_EINVAL; }
-    if (p.precision < LBM_FP64 || p.precision > LBM_BF16DEV) { set_error("bad precision"); return LBM_EINVAL; }
+    if (p.precision < LBM_FP64 || p.precision > LBM_BF16SHIFT) { set_error("bad precision"); return LBM_EINVAL; }
     if (!(p.tau > 0) && !(p.Kn > 0)) { set_error("need Kn > 0 or tau > 0"); return LBM_EINVAL; }
     if (!std::isfinite(p.Kn) || !std::isfinite(p.tau) || !std::isfinite(p.mu_exp) ||
         !std::isfinite(p.u_wall[0]) || !std::isfinite(p.u_wall[1]) ||
@@ -104,6 +104,10 @@ int check_params(const LatticeHost &L, const lbm_params &p) {
     if (p.thermal && (p.T_wall[0] <= 0 || p.T_wall[1] <= 0)) { set_error("T_wall must be > 0"); return LBM_EINVAL; }
     if (!(p.rho0 > 0)) { set_error("rho0 must be > 0"); return LBM_EINVAL; }
     if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_CELLWARP) { set_error("bad kernel"); return LBM_EINVAL; }
+    if (p.kernel == LBM_KERNEL_STAGED && p.precision == LBM_BF16SHIFT) {
+        set_error("the staged kernel is not built for LBM_BF16SHIFT");
+        return LBM_EINVAL;
+    }
     if (!(p.accom[0] >= 0 && p.accom[0] <= 1 && p.accom[1] >= 0 && p.accom[1] <= 1)) {
         set_error("accom must lie in [0, 1]");
         return LBM_EINVAL;
@@ -144,6 +148,7 @@ int dispatch_prec(int prec, F &&fn) {
     switch (prec) {
     case LBM_FP64: return fn(std::integral_constant<int, LBM_FP64>{});
     case LBM_FP32: return fn(std::integral_constant<int, LBM_FP32>{});
+    case LBM_BF16SHIFT: return fn(std::integral_constant<int, LBM_BF16SHIFT>{});
     default: return fn(std::integral_constant<int, LBM_BF16DEV>{});
     }
 }

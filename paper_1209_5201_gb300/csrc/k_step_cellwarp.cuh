@@ -63,8 +63,8 @@ k_step_cellwarp(const typename Store<PREC>::S *__restrict__ fin,
     const int j = blockIdx.x / k.Nx, x = blockIdx.x - j * k.Nx;
     // BF16: step count of the stochastic rounding (block 0 advances it)
     uint32_t seed = 0;
-    if constexpr (Store<PREC>::dev) seed = step_count(fin, k, blockIdx.x == 0 && lane == 0);
-    const uint32_t hcell = Store<PREC>::dev ? sr_cell(seed, (uint32_t)blockIdx.x) : 0u;
+    if constexpr (Store<PREC>::sr) seed = step_count(fin, k, blockIdx.x == 0 && lane == 0);
+    const uint32_t hcell = Store<PREC>::sr ? sr_cell(seed, (uint32_t)blockIdx.x) : 0u;
     const bool bot = j < L::N, top = j >= k.Ny - L::N;
 
     // value of population a at column xc (0 <= xc < Nx) of row `row`, in the

@@ -125,7 +125,7 @@ __device__ __forceinline__ void collide_store(const typename Store<PREC>::C (&f)
                                               int xl, int w, int x, int j, uint32_t seed) {
     using S = typename Store<PREC>::S;
     using C = typename Store<PREC>::C;
-    const uint32_t hcell = Store<PREC>::dev ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
+    const uint32_t hcell = Store<PREC>::sr ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
     Collision<Q, C, Store<PREC>::shifted> col;
     col.setup(f, k);
     C o[Q];
@@ -136,16 +136,21 @@ __device__ __forceinline__ void collide_store(const typename Store<PREC>::C (&f)
     });
 
     S v[Q];
-    if constexpr (Store<PREC>::dev) {
+    if constexpr (Store<PREC>::sr) {
         // BF16: the rest velocity alone, then each pair (a, a + 1) rounded by
-        // one conversion (the same bits as store_rounded)
-        const float v0 = f_to_dev(o[0], k.w[0], col.rho);
+        // one conversion (the same bits as store_rounded); BF16DEV first
+        // takes w_a rho off, BF16SHIFT's collision output is the deviation
+        const auto dv = [&](float oa, float wa) {
+            if constexpr (Store<PREC>::dev) return f_to_dev(oa, wa, col.rho);
+            else return oa;
+        };
+        const float v0 = dv(o[0], k.w[0]);
         const uint32_t d0 = bf16x2_rounded(v0, v0, sr_word(hcell, 0));   // upper: sr_bits(h, 0)
         v[0] = __ushort_as_bfloat16((unsigned short)(d0 >> 16));
         PairLoop<1, Q>::run([&](auto ic) {
             constexpr int A = decltype(ic)::value;
-            const float va = f_to_dev(o[A], k.w[A], col.rho);
-            const float vb = f_to_dev(o[A + 1], k.w[A + 1], col.rho);
+            const float va = dv(o[A], k.w[A]);
+            const float vb = dv(o[A + 1], k.w[A + 1]);
             const uint32_t d = bf16x2_rounded(va, vb, sr_bits_pair(hcell, A));
             v[A] = __ushort_as_bfloat16((unsigned short)(d >> 16));
             v[A + 1] = __ushort_as_bfloat16((unsigned short)d);
@@ -221,7 +226,7 @@ k_step_direct(const typename Store<PREC>::S *__restrict__ fin,
     if (bot || top) __syncthreads();
     // BF16: step count of the stochastic rounding (block 0 advances it)
     uint32_t seed = 0;
-    if constexpr (Store<PREC>::dev)
+    if constexpr (Store<PREC>::sr)
         seed = step_count(fin, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
     if (xl >= w) return;
     const long long pitch = PC > 0 ? PC : k.pitch;

@@ -141,7 +141,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
     const bool producer = warp == Cfg::kConsumerWarps;
     // BF16: step count of the stochastic rounding (block 0 advances it)
     uint32_t seed = 0;
-    if constexpr (Cfg::kDev) seed = step_count(fin, k, blockIdx.x == 0 && threadIdx.x == 0);
+    if constexpr (Store<PREC>::sr) seed = step_count(fin, k, blockIdx.x == 0 && threadIdx.x == 0);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -288,7 +288,7 @@ k_step_staged(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ 
                 constexpr int A = decltype(ic)::value;
                 col.template pair<A>(fv[q][A], fv[q][A + 1], o[A], o[A + 1]);
             });
-            const uint32_t hcell = Cfg::kDev ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
+            const uint32_t hcell = Store<PREC>::sr ? sr_cell(seed, (uint32_t)j * (uint32_t)k.Nx + (uint32_t)x) : 0u;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 C v = o[a];

@@ -21,6 +21,9 @@ template <> struct Consts<LBM_FP32> {
 template <> struct Consts<LBM_BF16DEV> {
     static const KConsts<float> &get(const SolverImpl &s) { return s.kf; }
 };
+template <> struct Consts<LBM_BF16SHIFT> {
+    static const KConsts<float> &get(const SolverImpl &s) { return s.kf; }
+};
 
 inline int aux_blocks(long long n) {
     long long b = (n + kAuxThreads - 1) / kAuxThreads;
@@ -156,6 +159,11 @@ template <> struct Variants<LBM_FP64> {
 template <> struct Variants<LBM_BF16DEV> {
     static constexpr int n = 2;
     static constexpr int v[n][4] = {{128, 2, 4, 1}, {128, 4, 3, 1}};
+};
+// not built for BF16SHIFT (the direct kernel is the fast path of wide grids)
+template <> struct Variants<LBM_BF16SHIFT> {
+    static constexpr int n = 0;
+    static constexpr int v[1][4] = {{0, 0, 0, 0}};
 };
 
 template <int Q, int PREC, int TX, int TY, int ST, int CPT>

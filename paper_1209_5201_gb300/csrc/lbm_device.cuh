@@ -40,17 +40,24 @@ template <int PREC> struct Store;
 // shifted: stored d_a = f~*_a - w_a (the rest weights as rounded to the
 //          compute type); the collision runs on the deviations, so FP32
 //          round-off scales with |d| instead of |f|.
+// sr:      BF16 storage; the step kernels round the stored values
+//          stochastically (FP32 and FP64 values are stored as computed).
 template <> struct Store<LBM_FP64> {
     using S = double; using C = double;
-    static constexpr bool dev = false, shifted = false;
+    static constexpr bool dev = false, shifted = false, sr = false;
 };
 template <> struct Store<LBM_FP32> {
     using S = float; using C = float;
-    static constexpr bool dev = false, shifted = true;
+    static constexpr bool dev = false, shifted = true, sr = false;
 };
 template <> struct Store<LBM_BF16DEV> {
     using S = __nv_bfloat16; using C = float;
-    static constexpr bool dev = true, shifted = false;
+    static constexpr bool dev = true, shifted = false, sr = true;
+};
+// the FP32 format's deviations d_a = f~*_a - w_a held in BF16
+template <> struct Store<LBM_BF16SHIFT> {
+    using S = __nv_bfloat16; using C = float;
+    static constexpr bool dev = false, shifted = true, sr = true;
 };
 
 __device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }

@@ -32,8 +32,9 @@ constexpr unsigned long long kDefaultWaitNs = 2000000000ull;   // bounded device
 // separate row segments are streamed at once.
 constexpr int kPitchClasses = 3;
 inline constexpr int pitch_class(int precision, int c) {
-    return precision == LBM_BF16DEV ? (c == 0 ? 1088 : c == 1 ? 2112 : 4224)
-                                    : (c == 0 ? 1056 : c == 1 ? 2112 : 4224);
+    return precision == LBM_BF16DEV || precision == LBM_BF16SHIFT
+               ? (c == 0 ? 1088 : c == 1 ? 2112 : 4224)
+               : (c == 0 ? 1056 : c == 1 ? 2112 : 4224);
 }
 inline constexpr int widest_pitch_class(int) { return kPitchClasses - 1; }
 // Columns of tile t (all tiles hold tw but the last, which holds the rest).

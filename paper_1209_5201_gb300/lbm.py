@@ -20,13 +20,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm_gb300.so")
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_EBUDGET, LBM_ENOTCONVERGED = 0, 1, 2, 3, 4
 LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ECUDA, LBM_EBUSY, LBM_ECANCELLED = 5, 6, 7, 8, 9
 LBM_LATTICE_D2Q17, LBM_LATTICE_D2Q25, LBM_LATTICE_D2Q25B, LBM_LATTICE_D2Q37 = 17, 25, 26, 37
-LBM_FP64, LBM_FP32, LBM_BF16DEV = 0, 1, 2
+LBM_FP64, LBM_FP32, LBM_BF16DEV, LBM_BF16SHIFT = 0, 1, 2, 3
 LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_STAGED, LBM_KERNEL_CELLWARP = 0, 1, 2, 3
 LBM_ROUND_AUTO, LBM_ROUND_STOCHASTIC, LBM_ROUND_NEAREST = 0, 1, 2
 LBM_INIT_REST, LBM_INIT_NS = 0, 1
 
 LATTICE_KIND = {"D2Q17": 17, "D2Q25": 25, "D2Q25b": 26, "D2Q37": 37}
-PRECISION = {"fp64": 0, "fp32": 1, "bf16dev": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16dev": 2, "bf16shift": 3}
 
 
 class LBMError(RuntimeError):

@@ -51,10 +51,12 @@ def test_fp64_accommodation(lbm, oracle, accom):
 
 # FP32 and BF16 storage against the FP64 oracle after 40 steps.  FP32: the
 # bound of the one-thread kernels (1e-5).  BF16 keeps 8 significant bits of
-# d = f - w rho and the step kernels round it stochastically: each store errs
+# d = f - w rho (BF16SHIFT: d = f - w) and the step kernels round it
+# stochastically: each store errs
 # by up to one BF16 ulp (2^-7 of |d|, zero-mean), and over 40 steps the errors
 # add like a random walk; measured 7.7e-3 relative per population, bound 1.5e-2.
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16dev", 1.5e-2)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16dev", 1.5e-2),
+                                           ("bf16shift", 1.5e-2)])
 def test_reduced_precision(lbm, oracle, precision, tol):
     err, _ = run(lbm, oracle, "D2Q37", 9, 14, precision, 40)
     assert err < tol, (precision, err)

@@ -49,7 +49,7 @@ def test_fp64_fluxes_match_oracle(lbm, oracle, lattice, Nx, Ny, accom):
         assert _close(g, r, 1e-10), (name, float(np.max(np.abs(g - r))), float(np.max(np.abs(r))))
 
 
-@pytest.mark.parametrize("precision,rel", [("fp32", 2e-3), ("bf16dev", 0.1)])
+@pytest.mark.parametrize("precision,rel", [("fp32", 2e-3), ("bf16dev", 0.1), ("bf16shift", 0.1)])
 def test_reduced_precision_steady_shear_stress(lbm, oracle, precision, rel):
     # steady isothermal Couette: the uniform bulk shear stress against the
     # oracle's steady state (the FP32 / BF16 round-off floors of the state)

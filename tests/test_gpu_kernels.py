@@ -75,14 +75,15 @@ def test_every_variant_matches_oracle_isothermal(lbm, oracle, lattice):
         assert rel_err(f, ref) < 1e-12, kv
 
 
-def test_bf16_variants_agree_bitwise(lbm, oracle):
-    outs = [run_variant(lbm, oracle, "D2Q37", 200, 18, "bf16dev", kv, 40, Kn=0.05,
-                        u_wall=(-0.3, 0.3))[0] for kv in kernels(lbm, "bf16dev")]
+@pytest.mark.parametrize("precision", ["bf16dev", "bf16shift"])
+def test_bf16_variants_agree_bitwise(lbm, oracle, precision):
+    outs = [run_variant(lbm, oracle, "D2Q37", 200, 18, precision, kv, 40, Kn=0.05,
+                        u_wall=(-0.3, 0.3))[0] for kv in kernels(lbm, precision)]
     for f in outs[1:]:
         assert np.array_equal(f, outs[0])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16dev"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16dev", "bf16shift"])
 @pytest.mark.parametrize("Nx,Ny", [(1, 6), (3, 7), (9, 6), (33, 6), (257, 13), (300, 8)])
 def test_edge_sizes_fp32_bf16_variants_agree(lbm, oracle, precision, Nx, Ny):
     # FP32 and BF16 storage: every direct and staged variant gives the same
@@ -145,14 +146,15 @@ def test_pitch_class_grids_every_direct_variant_matches_oracle(lbm, oracle, prec
         assert np.array_equal(f, first), kv
 
 
-def test_tiled_grid_bf16_variants_agree_and_staged_is_refused(lbm, oracle):
+@pytest.mark.parametrize("precision", ["bf16dev", "bf16shift"])
+def test_tiled_grid_bf16_variants_agree_and_staged_is_refused(lbm, oracle, precision):
     # 4301 columns in BF16: two x-tiles of 2151 and 2150 columns (pitch 4224)
-    outs = [run_variant(lbm, oracle, "D2Q37", 4301, 9, "bf16dev", kv, 20, Kn=0.05,
-                        u_wall=(-0.3, 0.3))[0] for kv in direct_kernels(lbm, "bf16dev")]
+    outs = [run_variant(lbm, oracle, "D2Q37", 4301, 9, precision, kv, 20, Kn=0.05,
+                        u_wall=(-0.3, 0.3))[0] for kv in direct_kernels(lbm, precision)]
     for f in outs[1:]:
         assert np.array_equal(f, outs[0])
     s = lbm.Solver(lbm.Config(lattice="D2Q37", Nx=4301, Ny=9, eq_order=4, thermal=True,
-                              precision="bf16dev"))
+                              precision=precision))
     with pytest.raises(lbm.LBMError) as ei:
         s.set_kernel(lbm.LBM_KERNEL_STAGED, 0)
     assert ei.value.status == lbm.LBM_EINVAL

@@ -23,18 +23,27 @@ pytestmark = pytest.mark.gpu
 # 1e-6 target is not reached (ENOTCONVERGED is expected: the noise floor).
 # The time mean over 4000 steps is the steady field to within the bound of
 # the BF16 variant, 5e-3 in u_x / U_w and in rho.
+# BF16SHIFT keeps 8 significant bits of d = f - w (the FP32 format's
+# deviations; here rho stays within 1e-3 of 1, so |d| is about that of
+# BF16DEV) with the same stochastic rounding and no density plane: measured
+# on both kernels 2.3e-3 .. 2.5e-3 U_w in u_x, 4.4e-4 .. 4.5e-4 in rho,
+# 1.4e-4 .. 1.5e-4 in T for the final state (bounds 2x the largest, one
+# random stream measured), residual noise near 2.6e-3, and the time mean
+# within 3.4e-4 in rho and u_x / U_w and 2.6e-6 in T (bounds 1e-3, 1e-3, 1e-5).
 BOUNDS = {          # rho, u_x / U_w, T
     "fp64": (1e-9, 1e-7, 1e-9),
     "fp32": (2e-6, 5e-6, 2e-6),
     "bf16dev": (1e-3, 8e-3, 4e-4),
+    "bf16shift": (9e-4, 5e-3, 3e-4),
 }
 MEAN_BOUNDS = {
     "fp64": (1e-9, 1e-7, 1e-9),
     "fp32": (2e-6, 5e-6, 2e-6),
     "bf16dev": (5e-3, 5e-3, 4e-4),
+    "bf16shift": (1e-3, 1e-3, 1e-5),
 }
 KERNELS = {"thread": 1, "warp": 3}
-TOL = {"fp64": 1e-8, "fp32": 1e-6, "bf16dev": 1e-6}
+TOL = {"fp64": 1e-8, "fp32": 1e-6, "bf16dev": 1e-6, "bf16shift": 1e-6}
 
 
 def sweep(lbm, oracle, kernel):
@@ -47,7 +56,7 @@ def sweep(lbm, oracle, kernel):
     # conserve energy, so the kinetic T is compared on the collided oracle state
     orho, oux, _, oT = oracle.macros_kinetic(p, oracle.collide(p, f))
     out = {}
-    for prec in ("fp64", "fp32", "bf16dev"):
+    for prec in ("fp64", "fp32", "bf16dev", "bf16shift"):
         s = lbm.Solver(lbm.Config(lattice="D2Q25", Nx=1, Ny=64, Kn=0.1, u_wall=(-Uw, Uw),
                                   precision=prec, kernel=kernel))
         s.init()
