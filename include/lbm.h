@@ -106,7 +106,7 @@ int lbm_lattice_verify(const lbm_lattice *lat, int degree, double *max_err);
                             results are reproducible run to run             */
 #define LBM_BF16SHIFT 3  /* BF16 storage of d_a = f~*_a - w_a rho_0 (rho_0 = 1,
                             the reference density of the non-dimensional
-                            variables, Sec. IV), FP32 arithmetic on the
+                            variables, Sec. II), FP32 arithmetic on the
                             deviations (the collision of LBM_FP32), the same
                             stochastic rounding of the stored d as
                             LBM_BF16DEV; no density plane: 4 Q bytes per cell
