@@ -368,7 +368,7 @@ def run_batched(lbm, n=256, seed=7, tol=SOLVE_TOL, baseline_every=16):
             "baseline_sample": f"every {baseline_every}th instance ({len(sample)}), each timed "
                                "to completion: alone through the same server, and on the "
                                "single-domain FP32 solver (AUTO kernel) for the same steps",
-            "max_err_est": max((r.err_est for r in results if r.status == 0), default=None),
+            **err_est_summary(results),
             "cta_budget": ctas, "autotune": tuned[1],
             "accuracy": "solves stop at an extrapolated L-inf distance tol of u_x/U_w (and T) "
                         "to the steady state; cpu_baseline.max_err_vs_oracle is the measured "
@@ -382,6 +382,17 @@ def run_batched(lbm, n=256, seed=7, tol=SOLVE_TOL, baseline_every=16):
             # over the makespan (the pool is L2-resident: an L2 rate)
             "achieved_GBps": sum(r.steps * it.Ny * 8 * Q_OF[it.lattice]
                                  for r, it in zip(results, insts)) / makespan / 1e9}
+
+
+def err_est_summary(results):
+    """Largest extrapolated distance to the steady state (units of U) over the
+    requests that stopped by the extrapolation rule, and how many stopped at
+    the round-off floor instead (their change no longer contracts, so the
+    server reports no extrapolation for them: err_est = 1e30)."""
+    est = [r.err_est for r in results if r.status == 0]
+    extrap = [e for e in est if e < 1e29]
+    return {"max_err_est": max(extrap, default=None),
+            "converged_at_noise_floor": len(est) - len(extrap)}
 
 
 def run_serving(lbm, n=10000, seed=11, rate=200.0, tol=SOLVE_TOL):
@@ -417,7 +428,7 @@ def run_serving(lbm, n=10000, seed=11, rate=200.0, tol=SOLVE_TOL):
             "server_cfg": {"chunk_steps": cfg.chunk_steps, "cluster_rows": cfg.cluster_rows,
                            "class_sub": list(cfg.class_sub)},
             "cell_steps": int(cell_steps), "GLUPS": cell_steps / wall / 1e9,
-            "max_err_est": max((r.err_est for r in results if r.status == 0), default=None),
+            **err_est_summary(results),
             "cpu_baseline": oracle_leg(reqs[:head], results[:head], fields, limit=50)}
 
 
@@ -443,6 +454,44 @@ def run_slots(lbm, n, lattice, Ny, Kn, steps, cluster_rows=256, rounding=0):
             "mean_steps": mean_steps, "wall_s": wall,
             "us_per_step_per_slot": wall / mean_steps * 1e6,
             "GLUPS": n * mean_steps * Ny / wall / 1e9}
+
+
+def run_precision(lbm, prec: str, steps: int, warmup: int):
+    """The grid workload (D2Q37 4096 x 2048) with another storage format: the
+    autotuned kernel's step time by CUDA events on the solver's stream over
+    `steps` steps after `warmup`, and its roofline at that format's
+    algorithmic bytes per lattice update."""
+    import torch
+
+    cfg = lbm.Config(lattice="D2Q37", Nx=WORKLOAD["Nx"], Ny=WORKLOAD["Ny"], eq_order=4,
+                     thermal=True, Kn=WORKLOAD["Kn"], u_wall=WORKLOAD["u_wall"],
+                     T_wall=WORKLOAD["T_wall"], precision=prec,
+                     noise_amp=WORKLOAD["noise_amp"], seed=WORKLOAD["seed"])
+    stream = torch.cuda.Stream()
+    s = lbm.Solver(cfg, stream=stream)
+    kern, var, _ = s.autotune(10)
+    s.init()
+    s.step(warmup)
+    s.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    s.close()
+    cells = cfg.Nx * cfg.Ny
+    ms_step = e0.elapsed_time(e1) / steps
+    peak, peak_kind = measured_peaks()
+    bpl = BYTES_PER_LU[prec]
+    achieved = bpl * cells / (ms_step * 1e-3) / 1e9
+    return {"workload": workload_name(prec, cfg.Nx, cfg.Ny), "dtype": DTYPE[prec],
+            "value": job_rate(1, cells, steps, ms_step * steps * 1e-3), "unit": "MLUPS",
+            "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
+            "kernel": kernel_name(kern, var, prec),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "traffic": step_traffic(f"{prec}:{kern}:{var}:{cfg.Nx}x{cfg.Ny}"),
+                         "peak_kind": f"{peak_kind} (copy burst)", "bytes_per_lu": bpl}}
 
 
 def run_column_fp64(lbm, steps=20000):
@@ -731,6 +780,10 @@ def main():
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.precision)
     if not args.no_extras and world == 1:
+        if args.precision == "fp32":
+            # the two BF16 storage formats on the same grid
+            out["precisions"] = {p: run_precision(lbm, p, max(args.steps, 500), args.warmup)
+                                 for p in ("bf16shift", "bf16dev")}
         out["column_fp64"] = run_column_fp64(lbm)
         out["batched"] = run_batched(lbm)
         out["serving"] = run_serving(lbm, n=args.serving_requests)

@@ -412,7 +412,8 @@ typedef struct lbm_result {
     int64_t steps;
     double residual;      /* last change over one check (units of tol)        */
     double err_est;       /* extrapolated distance to the steady state (units
-                             of tol)                                         */
+                             of tol); 1e30 when the request stopped at the
+                             round-off floor (no contraction to extrapolate) */
     double mass;          /* sum of rho over the column at the last check     */
     double t_submit, t_admit, t_done;   /* seconds since server creation      */
 } lbm_result;
