@@ -117,6 +117,34 @@ def test_params_default_and_checks(lbm):
         lbm.lbm_lattice_destroy(h)
 
 
+def test_bf16_formats_memory_and_checks(lbm):
+    # BF16SHIFT stores the FP32 format's deviations d = f - w in BF16 and has
+    # no density plane: its requirement is BF16DEV's less the two FP32 planes
+    # (one row of 4224 padded elements per row and buffer at 4096 x 2048); the
+    # staged kernel is not built for it, and no precision follows it
+    h = lbm.lbm_lattice_create(37)
+    try:
+        p = lbm.lbm_params_default()
+        p.Nx, p.Ny, p.eq_order, p.thermal = 4096, 2048, 4, 1
+        p.precision = lbm.LBM_BF16DEV
+        dev = lbm.lbm_solver_required_bytes(h, p)
+        p.precision = lbm.LBM_BF16SHIFT
+        shift = lbm.lbm_solver_required_bytes(h, p)
+        assert dev - shift == 2 * 2048 * 4224 * 4
+        p.precision = lbm.LBM_FP32
+        assert lbm.lbm_solver_required_bytes(h, p) - shift == 2 * 37 * 2048 * 4224 * 2
+        p.precision, p.kernel = lbm.LBM_BF16SHIFT, lbm.LBM_KERNEL_STAGED
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_solver_required_bytes(h, p)
+        assert ei.value.status == lbm.LBM_EINVAL
+        p.precision, p.kernel = lbm.LBM_BF16SHIFT + 1, lbm.LBM_KERNEL_AUTO
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_solver_required_bytes(h, p)
+        assert ei.value.status == lbm.LBM_EINVAL
+    finally:
+        lbm.lbm_lattice_destroy(h)
+
+
 def test_status_strings(lbm):
     assert lbm.lbm_status_string(0) == "ok"
     assert lbm.lbm_status_string(4) == "not converged"
