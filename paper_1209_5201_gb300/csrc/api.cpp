@@ -891,6 +891,10 @@ int lbm_solver_set_kernel(lbm_solver *h, int32_t kernel, int32_t variant) {
     const int nv = kernel == LBM_KERNEL_STAGED     ? staged_variant_count(s.p.precision)
                    : kernel == LBM_KERNEL_CELLWARP ? 1
                                                    : direct_variant_count(s.p.precision);
+    if (kernel == LBM_KERNEL_STAGED && nv == 0) {
+        set_error("the staged kernel is not built for this precision");
+        return LBM_EINVAL;
+    }
     if (variant < 0 || variant >= nv) { set_error("bad variant"); return LBM_EINVAL; }
     if (kernel == LBM_KERNEL_STAGED && s.nt != 1) {
         set_error("the staged kernel runs grids stored as one x-tile only (Nx + 8 <= tile pitch)");
