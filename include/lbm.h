@@ -412,8 +412,10 @@ typedef struct lbm_result {
     int64_t steps;
     double residual;      /* last change over one check (units of tol)        */
     double err_est;       /* extrapolated distance to the steady state (units
-                             of tol); 1e30 when the request stopped at the
-                             round-off floor (no contraction to extrapolate) */
+                             of tol) at the last check: at most tol when the
+                             request stopped by extrapolation; 1e30 while the
+                             change does not contract (a stop at the
+                             round-off floor)                                */
     double mass;          /* sum of rho over the column at the last check     */
     double t_submit, t_admit, t_done;   /* seconds since server creation      */
 } lbm_result;
