@@ -246,3 +246,17 @@ def test_struct_layouts_match_the_header(lbm, tmp_path):
         assert int(got[st]) == ctypes.sizeof(py), st
         for name, _ in py._fields_:
             assert int(got[f"{st}.{name}"]) == getattr(py, name).offset, (st, name)
+
+
+def test_binding_constants_match_the_header(lbm):
+    # every integer constant include/lbm.h defines (status codes, lattices,
+    # storage formats, kernels, rounding and start modes) has the same value in
+    # the binding
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    consts = {m.group(1): int(m.group(2))
+              for m in re.finditer(r"^#define\s+(LBM_\w+)\s+(-?\d+)\b", src, flags=re.M)}
+    assert len(consts) >= 27 and "LBM_BF16SHIFT" in consts
+    for name, v in consts.items():
+        assert getattr(lbm, name) == v, name
+    assert lbm.PRECISION == {"fp64": lbm.LBM_FP64, "fp32": lbm.LBM_FP32,
+                             "bf16dev": lbm.LBM_BF16DEV, "bf16shift": lbm.LBM_BF16SHIFT}
